@@ -1,0 +1,154 @@
+/*
+ * nufft45.h -- non-iterative inverse nonuniform FFTs of types 4 and 5 in one
+ * dimension (J. Selva, "Non-iterative Type 4 and 5 Nonuniform FFT Methods in
+ * the One-Dimensional Case"), with the type-1 and type-2 transforms they are
+ * built from.  CUDA library for GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * Nodes.  P = N nodes x_p in radians (any real value; wrapped to [0, 2 pi)).
+ *   The library uses t_p = x_p / (2 pi) mod 1, carried exactly as the 64-bit
+ *   fraction T_p = trunc(t_p 2^64).  Sec. II assumes 0 <= t_p < 1.
+ * Frequencies are 0 .. N-1, not centred (Sec. I notation; Eqs. 32, 34).
+ * Data.  Interleaved complex: complex64 (float re, im) for NUFFT_FP32 plans,
+ *   complex128 (double re, im) for NUFFT_FP64 plans.  `batch` right-hand
+ *   sides are contiguous with stride N elements.  Out-of-place only: the
+ *   input and output buffers must not overlap.
+ * Pointers.  Device pointers, or host pointers (pinned or pageable): host
+ *   buffers are staged through device memory with copies on `stream`, and the
+ *   call returns after the result has been copied back.  For device buffers
+ *   the call is asynchronous on `stream`.  Device buffers stay owned by the
+ *   caller.
+ * Stream.  A cudaStream_t (NULL = legacy default stream).
+ * Errors.  Every call returns a status and never aborts or traps; the
+ *   message of the last failure on the calling thread is available from
+ *   nufft_last_error_message().  Argument errors are reported before any
+ *   work is queued.
+ */
+#ifndef NUFFT45_H
+#define NUFFT45_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nufft_stream_t;   /* the same type as cudaStream_t */
+typedef struct nufft_plan_s* nufft_plan_t;    /* opaque */
+
+typedef enum {
+    NUFFT_OK = 0,
+    NUFFT_ERR_ARG = 1,        /* bad argument (size, pointer, tolerance, precision) */
+    NUFFT_ERR_DUP_NODES = 2,  /* two nodes coincide modulo 2 pi: the system of Eq. 47/48 is singular */
+    NUFFT_ERR_ALLOC = 3,      /* device memory allocation failed */
+    NUFFT_ERR_CUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+    NUFFT_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    NUFFT_ERR_ACCURACY = 6    /* the tolerance cannot be met in the requested precision */
+} nufft_status;
+
+typedef enum {
+    NUFFT_FP32 = 1,   /* node-dependent plan in float64, transforms in float32 (complex64 data) */
+    NUFFT_FP64 = 2    /* everything in float64 (complex128 data) */
+} nufft_prec;
+
+/*
+ * nufft_plan -- precompute everything that depends on the nodes.
+ *   Sec. III (Fig. 1, upper half) and Sec. IV: the log-kernel samples v(q/P)
+ *   by a type-1 NUFFT of unit strengths of length R = eta P (Eqs. 13, 19, 28,
+ *   41, 42, folded by Eq. 7), the kernel samples K_q = L(e^{j 2 pi (q/P + ja)})
+ *   (Eq. 29), the Lagrange coefficients L_m (Eq. 43), the derivative samples
+ *   L'(z_p) by a type-2 NUFFT (Eq. 16), and the node weights
+ *   w_p = h(-P t_p + j P a) / (L'(z_p) z_p) (Eqs. 17, 23, 27, 40).
+ *   The shift a and the oversampling eta follow Sec. V (Eq. 49) from `tol`.
+ * N      number of nodes (= number of coefficients), 1 <= N <= 2^28.
+ * x      N nodes in radians (float64), device or host.  Not retained.
+ * tol    target relative L2 error: NUFFT_FP64 accepts [1e-12, 1e-1],
+ *        NUFFT_FP32 accepts [1e-6, 1e-1]; tighter values return
+ *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
+ * prec   NUFFT_FP32 or NUFFT_FP64.
+ * plan   receives the plan; owned by the caller, release with nufft_destroy.
+ * The call synchronises `stream` once to check for coincident nodes
+ * (NUFFT_ERR_DUP_NODES, no plan is returned).
+ */
+nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream,
+                        nufft_plan_t* plan);
+
+/*
+ * nufft_inv5 -- type-5 NUFFT (Eq. 48): given samples s(t_p) of
+ *   s(t) = sum_{m<N} S_m e^{j 2 pi m t}, return S.  Method of Sec. III,
+ *   Fig. 1 (lower half): a_p = s(t_p) w_p (Eq. 27), type-1 NUFFT,
+ *   scaling by e^{-2 pi k a} and length-N inverse DFT (Eq. 37), product with
+ *   K_q (Eq. 30), length-N DFT and scaling by e^{2 pi m a} / N (Eq. 31).
+ * f      batch x N samples at the plan's nodes (node order as given to nufft_plan).
+ * c      batch x N coefficients S_0 .. S_{N-1}.
+ */
+nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream);
+
+/*
+ * nufft_inv4 -- type-4 NUFFT (Eq. 47): given A(k) = sum_p a_p e^{-j 2 pi k t_p},
+ *   k = 0..N-1, return a.  Method of Sec. IV, Fig. 2: Eq. 37 on A, product
+ *   with K_q (Eq. 30), Eq. 31, type-2 NUFFT at the nodes, times w_p (Eq. 40).
+ * A      batch x N spectral samples.
+ * a      batch x N node amplitudes (node order as given to nufft_plan).
+ */
+nufft_status nufft_inv4(nufft_plan_t plan, const void* A, void* a, int64_t batch, nufft_stream_t stream);
+
+/*
+ * nufft_fwd1 -- type-1 NUFFT (Eq. 32): A_k = sum_p a_p e^{-j 2 pi k t_p},
+ *   k = 0..N-1, by gridding on an oversampled grid, FFT and deconvolution
+ *   (Sec. II).  a: batch x N amplitudes, A: batch x N.
+ */
+nufft_status nufft_fwd1(nufft_plan_t plan, const void* a, void* A, int64_t batch, nufft_stream_t stream);
+
+/*
+ * nufft_fwd2 -- type-2 NUFFT (Eq. 34): s_p = sum_{m<N} S_m e^{j 2 pi m t_p},
+ *   by deconvolution, inverse FFT and interpolation (Sec. II).
+ *   c: batch x N coefficients, f: batch x N samples.
+ */
+nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream);
+
+/* nufft_destroy -- release a plan (NULL is accepted).  Waits for work queued
+ * on the plan's creation stream that uses its buffers. */
+nufft_status nufft_destroy(nufft_plan_t plan);
+
+/* Parameters a plan chose (Sec. V).  rho = e^{-2 pi a}; gamma = rho^{-N}. */
+typedef struct {
+    int64_t N;
+    int prec;
+    double tol;
+    double gamma, a, rho;
+    int eta;                 /* R = eta N, Eq. 41 */
+    int64_t R;
+    int64_t grid_solve;      /* oversampled grid of the transforms */
+    int64_t grid_plan;       /* oversampled grid of the length-R type-1 NUFFT */
+    int w_solve, w_plan;     /* spreading widths (grid points) */
+    double beta_solve, beta_plan;
+    int64_t batch_chunk;     /* right-hand sides processed per pass */
+} nufft_plan_info_t;
+
+nufft_status nufft_plan_info(nufft_plan_t plan, nufft_plan_info_t* info);
+
+/*
+ * nufft_plan_export -- copy a node-dependent quantity of the plan, as N
+ * complex128 values, into dst (device or host):
+ *   which = 0: K_q = L(e^{j 2 pi (q/N + j a)}), q = 0..N-1      (Eqs. 10, 29)
+ *   which = 1: L'(z_p), p in node order                        (Sec. III-D)
+ *   which = 2: w_p = h(-N t_p + j N a) / (L'(z_p) z_p)          (Eqs. 27, 40)
+ * Synchronises `stream`.
+ */
+nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_stream_t stream);
+
+/* Drop the cache of node-independent tables (deconvolution and scaling
+ * factors, FFT twiddles) kept per (N, precision, tolerance).  Plans that are
+ * alive keep their own reference. */
+nufft_status nufft_cache_clear(void);
+
+const char* nufft_status_string(nufft_status st);
+const char* nufft_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT45_H */

@@ -1,0 +1,168 @@
+"""Thin Python binding of libnufft45 (non-iterative type-4/5 NUFFTs, GB300).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+library.  The C entry points are available under their own names
+(``nufft_plan``, ``nufft_inv5``, ``nufft_inv4``, ``nufft_fwd1``,
+``nufft_fwd2``, ``nufft_destroy``, ...) on the object returned by ``lib()``;
+``Plan`` wraps them for torch tensors (device memory, streams) and
+``autograd`` adds the differentiable inverses.
+
+There is no CPU fallback: importing the transforms without the built
+library raises.
+"""
+import ctypes
+import os
+
+__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "build", "library_path"]
+
+FP32 = 1
+FP64 = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "lib", "libnufft45.so")
+_lib = None
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def build(force=False):
+    from . import _build
+    return _build.build(force=force)
+
+
+class NufftError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status, message))
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64), ("prec", ctypes.c_int), ("tol", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("a", ctypes.c_double), ("rho", ctypes.c_double),
+        ("eta", ctypes.c_int), ("R", ctypes.c_int64), ("grid_solve", ctypes.c_int64),
+        ("grid_plan", ctypes.c_int64), ("w_solve", ctypes.c_int), ("w_plan", ctypes.c_int),
+        ("beta_solve", ctypes.c_double), ("beta_plan", ctypes.c_double),
+        ("batch_chunk", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def lib():
+    """Load libnufft45.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libnufft45.so is not built (%s); run paper_1604_06236_gb300.build()" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.nufft_plan.argtypes = [i64, vp, dbl, i32, vp, ctypes.POINTER(vp)]
+        for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2"):
+            getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
+        L.nufft_destroy.argtypes = [vp]
+        L.nufft_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.nufft_plan_export.argtypes = [vp, i32, vp, vp]
+        L.nufft_cache_clear.argtypes = []
+        L.nufft_status_string.argtypes = [i32]
+        L.nufft_status_string.restype = ctypes.c_char_p
+        L.nufft_last_error_message.argtypes = []
+        L.nufft_last_error_message.restype = ctypes.c_char_p
+        for name in ("nufft_plan", "nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_destroy",
+                     "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != 0:
+        L = lib()
+        raise NufftError(L.nufft_status_string(status).decode(), L.nufft_last_error_message().decode())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A plan for N nodes (radians), float64 tensor on the GPU or host.
+
+    prec FP32: complex64 data, float64 node weights; prec FP64: complex128.
+    """
+
+    def __init__(self, x, tol=None, prec=FP32, stream=None):
+        import torch
+        if not isinstance(x, torch.Tensor):
+            x = torch.as_tensor(x)
+        x = x.to(torch.float64).contiguous()
+        if tol is None:
+            tol = 1e-5 if prec == FP32 else 1e-10
+        self.N = x.numel()
+        self.prec = prec
+        self.tol = tol
+        self.dtype = torch.complex64 if prec == FP32 else torch.complex128
+        self.device = x.device if x.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        self._h = ctypes.c_void_p()
+        self._x_keep = x
+        check(lib().nufft_plan(self.N, _ptr(x), float(tol), int(prec), _stream_handle(stream), ctypes.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().nufft_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = PlanInfo()
+        check(lib().nufft_plan_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def export(self, which, stream=None):
+        import torch
+        out = torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        check(lib().nufft_plan_export(self._h, int(which), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def _run(self, fname, inp, out=None, stream=None):
+        import torch
+        if inp.dtype != self.dtype:
+            raise TypeError("expected %s data, got %s" % (self.dtype, inp.dtype))
+        if inp.shape[-1] != self.N:
+            raise ValueError("last dimension must be N = %d" % self.N)
+        inp = inp.contiguous()
+        if out is None:
+            out = torch.empty_like(inp)
+        batch = inp.numel() // self.N
+        check(getattr(lib(), fname)(self._h, _ptr(inp), _ptr(out), batch, _stream_handle(stream)))
+        return out
+
+    def inv5(self, f, out=None, stream=None):
+        """Type-5: coefficients S (k = 0..N-1) from samples at the nodes (Eq. 48)."""
+        return self._run("nufft_inv5", f, out, stream)
+
+    def inv4(self, A, out=None, stream=None):
+        """Type-4: node amplitudes a from spectral samples A(k), k = 0..N-1 (Eq. 47)."""
+        return self._run("nufft_inv4", A, out, stream)
+
+    def fwd1(self, a, out=None, stream=None):
+        """Type-1: A(k) = sum_p a_p e^{-j 2 pi k t_p} (Eq. 32)."""
+        return self._run("nufft_fwd1", a, out, stream)
+
+    def fwd2(self, c, out=None, stream=None):
+        """Type-2: s(t_p) = sum_m c_m e^{j 2 pi m t_p} (Eq. 34)."""
+        return self._run("nufft_fwd2", c, out, stream)

@@ -1,0 +1,477 @@
+// Stockham autosort FFT for any length, staged through shared memory.
+//
+// A length n with prime factors in {2,3,5,7} is split into passes of
+// composite radix R_i (prod R_i = n, R_i <= 512 for complex64 and <= 256 for
+// complex128).  Each pass reads and writes the array once, fully coalesced:
+// a CTA loads C butterflies (C consecutive j, each with R inputs of stride
+// n/R), applies the inter-pass twiddles, performs the C length-R DFTs in
+// shared memory with radix-2/3/4/5/7/8 Stockham sub-stages (ping-pong
+// buffers), and stores the results in Stockham order, so the final pass leaves
+// the transform in natural order.  Lengths with a larger prime factor use
+// Bluestein's chirp-z convolution on a smooth length m >= 2n - 1.
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace nufft45 {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T> struct FftLimits;
+template <> struct FftLimits<float> { static constexpr int kElems = 8192; static constexpr int kLmax = 512; };
+template <> struct FftLimits<double> { static constexpr int kElems = 4096; static constexpr int kLmax = 256; };
+
+struct PassArgs {
+    int64_t n, nR, Ns, total;  // total = batch * n / R butterflies
+    int R, PR, C, nsub;
+    int sub[12];
+    int in_cfast, out_cfast;
+    int shift;
+    int64_t mask;
+};
+
+template <typename T>
+__device__ __forceinline__ c2<T> twiddle(const c2<T>* __restrict__ lo, const c2<T>* __restrict__ hi, int shift,
+                                         int64_t mask, int64_t e, int dir) {
+    c2<T> w = cmul(__ldg(&lo[e & mask]), __ldg(&hi[e >> shift]));
+    if (dir > 0) w.y = -w.y;
+    return w;
+}
+
+// ---- small DFTs in registers (dir = -1 forward, +1 inverse) ----------------
+template <typename V> __device__ __forceinline__ void dft2(V* v) {
+    V a = v[0], b = v[1];
+    v[0] = cadd(a, b); v[1] = csub(a, b);
+}
+template <typename V> __device__ __forceinline__ void dft4(V* v, int dir) {
+    V s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    V s13 = cadd(v[1], v[3]), d13 = cmulj(csub(v[1], v[3]), dir);
+    v[0] = cadd(s02, s13); v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13); v[3] = csub(d02, d13);
+}
+template <typename V> __device__ __forceinline__ void dft8(V* v, int dir) {
+    using T = decltype(v[0].x);
+    const T h = (T)0.70710678118654752440;
+    V e[4] = {v[0], v[2], v[4], v[6]};
+    V o[4] = {v[1], v[3], v[5], v[7]};
+    dft4(e, dir); dft4(o, dir);
+    // W8^1 = h (1 + dir j), W8^2 = dir j, W8^3 = h (-1 + dir j)
+    V o1 = cscale(cadd(o[1], cmulj(o[1], dir)), h);
+    V o2 = cmulj(o[2], dir);
+    V o3 = cscale(csub(cmulj(o[3], dir), o[3]), h);
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+}
+template <typename V> __device__ __forceinline__ void dft3(V* v, int dir) {
+    using T = decltype(v[0].x);
+    const T s3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
+    V t1 = cadd(v[1], v[2]);
+    V t2 = csub(v[0], cscale(t1, (T)0.5));
+    V t3 = cmulj(cscale(csub(v[1], v[2]), s3), dir);
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+}
+template <typename V> __device__ __forceinline__ void dft5(V* v, int dir) {
+    using T = decltype(v[0].x);
+    const T c1 = (T)0.30901699437494742410, c2_ = (T)-0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
+    V a0 = v[0];
+    V p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
+    V p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
+    V r1 = cadd(a0, cadd(cscale(p1, c1), cscale(p2, c2_)));
+    V r2 = cadd(a0, cadd(cscale(p1, c2_), cscale(p2, c1)));
+    V i1 = cmulj(cadd(cscale(m1, s1), cscale(m2, s2)), dir);
+    V i2 = cmulj(csub(cscale(m1, s2), cscale(m2, s1)), dir);
+    v[0] = cadd(a0, cadd(p1, p2));
+    v[1] = cadd(r1, i1); v[4] = csub(r1, i1);
+    v[2] = cadd(r2, i2); v[3] = csub(r2, i2);
+}
+// radix 7: direct DFT with W_7 from the length-n twiddle table (7 | n)
+template <typename T>
+__device__ __forceinline__ void dft7(c2<T>* v, int dir, const c2<T>* lo, const c2<T>* hi, int shift,
+                                     int64_t mask, int64_t n) {
+    c2<T> w[7];
+    for (int q = 0; q < 7; ++q) w[q] = twiddle<T>(lo, hi, shift, mask, (int64_t)q * (n / 7), dir);
+    c2<T> out[7];
+    for (int m = 0; m < 7; ++m) {
+        c2<T> acc = v[0];
+        for (int k = 1; k < 7; ++k) acc = cadd(acc, cmul(v[k], w[(m * k) % 7]));
+        out[m] = acc;
+    }
+    for (int m = 0; m < 7; ++m) v[m] = out[m];
+}
+
+template <typename T, int r>
+__device__ __forceinline__ void substage(const c2<T>* __restrict__ src, c2<T>* __restrict__ dst, int R, int PR,
+                                         int C, int Nsub, int dir, const c2<T>* lo, const c2<T>* hi, int shift,
+                                         int64_t mask, int64_t n) {
+    const int Rr = R / r;
+    const int nbf = C * Rr;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        const int c = bf / Rr, jj = bf - c * Rr;
+        const c2<T>* s = src + c * PR;
+        c2<T> v[r];
+#pragma unroll
+        for (int k = 0; k < r; ++k) v[k] = s[jj + k * Rr];
+        const int jm = jj % Nsub;
+        if (jm != 0) {
+            const int64_t step = (int64_t)jm * (n / ((int64_t)Nsub * r));
+#pragma unroll
+            for (int k = 1; k < r; ++k) v[k] = cmul(v[k], twiddle<T>(lo, hi, shift, mask, step * k, dir));
+        }
+        if constexpr (r == 2) dft2(v);
+        else if constexpr (r == 3) dft3(v, dir);
+        else if constexpr (r == 4) dft4(v, dir);
+        else if constexpr (r == 5) dft5(v, dir);
+        else if constexpr (r == 8) dft8(v, dir);
+        else dft7<T>(v, dir, lo, hi, shift, mask, n);
+        c2<T>* d = dst + c * PR + (jj / Nsub) * Nsub * r + jm;
+#pragma unroll
+        for (int m = 0; m < r; ++m) d[m * Nsub] = v[m];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_fft_pass(const c2<T>* in, c2<T>* out,  // may alias (single pass)
+                                                       PassArgs a, const c2<T>* __restrict__ lo,
+                                                       const c2<T>* __restrict__ hi, int dir) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2<T>* s0 = reinterpret_cast<c2<T>*>(smem_raw);
+    c2<T>* s1 = s0 + (size_t)a.C * a.PR;
+    const int64_t g0 = (int64_t)blockIdx.x * a.C;
+    const int tot = a.C * a.R;
+    const int64_t tw_step = a.n / (a.Ns * a.R);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int c, k;
+        if (a.in_cfast) { c = e % a.C; k = e / a.C; } else { k = e % a.R; c = e / a.R; }
+        const int64_t g = g0 + c;
+        c2<T> x = mk<T>(0, 0);
+        if (g < a.total) {
+            const int64_t b = g / a.nR, j = g - b * a.nR;
+            x = in[b * a.n + j + (int64_t)k * a.nR];
+            const int64_t jm = j % a.Ns;
+            if (jm != 0 && k != 0) x = cmul(x, twiddle<T>(lo, hi, a.shift, a.mask, jm * k * tw_step, dir));
+        }
+        s0[c * a.PR + k] = x;
+    }
+    __syncthreads();
+    c2<T>* src = s0;
+    c2<T>* dst = s1;
+    int Nsub = 1;
+    for (int st = 0; st < a.nsub; ++st) {
+        const int r = a.sub[st];
+        switch (r) {
+            case 2: substage<T, 2>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+            case 3: substage<T, 3>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+            case 4: substage<T, 4>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+            case 5: substage<T, 5>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+            case 7: substage<T, 7>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+            default: substage<T, 8>(src, dst, a.R, a.PR, a.C, Nsub, dir, lo, hi, a.shift, a.mask, a.n); break;
+        }
+        __syncthreads();
+        c2<T>* t = src; src = dst; dst = t;
+        Nsub *= r;
+    }
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int c, m;
+        if (a.out_cfast) { c = e % a.C; m = e / a.C; } else { m = e % a.R; c = e / a.R; }
+        const int64_t g = g0 + c;
+        if (g >= a.total) continue;
+        const int64_t b = g / a.nR, j = g - b * a.nR;
+        const int64_t jm = j % a.Ns;
+        out[b * a.n + (j / a.Ns) * a.Ns * a.R + jm + (int64_t)m * a.Ns] = src[c * a.PR + m];
+    }
+}
+
+__global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d, double2* hi_d,
+                                float2* lo_f, float2* hi_f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) {
+        double s, c;
+        sincospi(-2.0 * (double)i / (double)n, &s, &c);
+        if (lo_d) lo_d[i] = make_double2(c, s);
+        if (lo_f) lo_f[i] = make_float2((float)c, (float)s);
+    }
+    if (i < nhi) {
+        // exponent i*B mod n, exact in integers before the division
+        const int64_t e = (i * B) % n;
+        double s, c;
+        sincospi(-2.0 * (double)e / (double)n, &s, &c);
+        if (hi_d) hi_d[i] = make_double2(c, s);
+        if (hi_f) hi_f[i] = make_float2((float)c, (float)s);
+    }
+}
+
+// ---- Bluestein --------------------------------------------------------------
+// chirp c_k = e^{+j pi k^2/n}; forward filter h_m = c_m (m in (-n, n)),
+// inverse filter conj(h).  Phases are reduced exactly: k^2 mod 2n.
+__global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chirp_f, double2* hf, double2* hi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int64_t k = -1;
+    if (i < n) k = i; else if (i > m - n) k = m - i;
+    double2 c = make_double2(0.0, 0.0);
+    if (k >= 0) {
+        const int64_t e = (int64_t)(((unsigned long long)k * (unsigned long long)k) % (unsigned long long)(2 * n));
+        double s, co;
+        sincospi((double)e / (double)n, &s, &co);
+        c = make_double2(co, s);
+        if (i < n) {
+            if (chirp_d) chirp_d[i] = c;
+            if (chirp_f) chirp_f[i] = make_float2((float)co, (float)s);
+        }
+    }
+    hf[i] = c;
+    hi[i] = make_double2(c.x, -c.y);
+}
+
+__global__ void k_scale_c128_to(const double2* in, int64_t m, double s, double2* out_d, float2* out_f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double2 v = in[i];
+    v.x *= s; v.y *= s;
+    if (out_d) out_d[i] = v;
+    if (out_f) out_f[i] = make_float2((float)v.x, (float)v.y);
+}
+
+template <typename T>
+__global__ void k_blue_pre(const c2<T>* __restrict__ x, int64_t n, int64_t m, const c2<T>* __restrict__ chirp,
+                           int dir, int64_t batch, c2<T>* __restrict__ a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * batch) return;
+    const int64_t b = i / m, j = i - b * m;
+    c2<T> v = mk<T>(0, 0);
+    if (j < n) {
+        c2<T> c = chirp[j];
+        v = dir < 0 ? cmulc(x[b * n + j], c) : cmul(x[b * n + j], c);
+    }
+    a[i] = v;
+}
+
+template <typename T>
+__global__ void k_blue_mul(c2<T>* __restrict__ a, const c2<T>* __restrict__ h, int64_t m, int64_t batch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * batch) return;
+    a[i] = cmul(a[i], h[i % m]);
+}
+
+template <typename T>
+__global__ void k_blue_post(const c2<T>* __restrict__ a, int64_t n, int64_t m, const c2<T>* __restrict__ chirp,
+                            int dir, int64_t batch, c2<T>* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * batch) return;
+    const int64_t b = i / n, k = i - b * n;
+    c2<T> c = chirp[k];
+    c2<T> v = a[b * m + k];
+    x[i] = dir < 0 ? cmulc(v, c) : cmul(v, c);
+}
+
+std::vector<int> factor_small(int64_t n) {
+    std::vector<int> f;
+    for (int p : {2, 3, 5, 7}) while (n % p == 0) { f.push_back(p); n /= p; }
+    return f;
+}
+
+// split the prime factors into `k` passes with balanced products (each <= lmax)
+bool split_passes(std::vector<int> f, int k, int lmax, std::vector<int64_t>& out) {
+    std::sort(f.begin(), f.end(), std::greater<int>());
+    out.assign(k, 1);
+    for (int p : f) {
+        int best = -1;
+        for (int i = 0; i < k; ++i)
+            if (out[i] * p <= lmax && (best < 0 || out[i] < out[best])) best = i;
+        if (best < 0) return false;
+        out[best] *= p;
+    }
+    return true;
+}
+
+std::vector<int> sub_radices(int64_t R) {
+    std::vector<int> s;
+    while (R % 8 == 0) { s.push_back(8); R /= 8; }
+    while (R % 4 == 0) { s.push_back(4); R /= 4; }
+    while (R % 2 == 0) { s.push_back(2); R /= 2; }
+    for (int p : {3, 5, 7}) while (R % p == 0) { s.push_back(p); R /= p; }
+    return s;
+}
+
+template <typename T>
+nufft_status make_passes(FFTPlan& p) {
+    const int64_t n = p.n;
+    std::vector<int> f = factor_small(n);
+    std::vector<int64_t> radices;
+    if (n <= FftLimits<T>::kElems) {
+        radices.push_back(n);
+    } else {
+        int k = 2;
+        while (!split_passes(f, k, FftLimits<T>::kLmax, radices)) ++k;
+    }
+    int64_t Ns = 1;
+    for (int64_t R : radices) {
+        FFTPass ps;
+        ps.R = (int)R;
+        ps.Ns = Ns;
+        std::vector<int> sr = sub_radices(R);
+        ps.nsub = (int)sr.size();
+        for (int i = 0; i < ps.nsub; ++i) ps.sub[i] = sr[i];
+        if (radices.size() == 1) ps.C = std::max<int64_t>(1, FftLimits<T>::kElems / R);
+        else ps.C = 16;
+        p.passes.push_back(ps);
+        Ns *= R;
+    }
+    return NUFFT_OK;
+}
+
+template <typename T>
+nufft_status exec_passes(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
+                         c2<T>** result) {
+    const c2<T>* lo = static_cast<const c2<T>*>(p.tw_lo);
+    const c2<T>* hi = static_cast<const c2<T>*>(p.tw_hi);
+    c2<T>* src = buf;
+    c2<T>* dst = (p.passes.size() == 1) ? buf : work;
+    for (size_t i = 0; i < p.passes.size(); ++i) {
+        const FFTPass& ps = p.passes[i];
+        PassArgs a;
+        a.n = p.n; a.R = ps.R; a.nR = p.n / ps.R; a.Ns = ps.Ns;
+        a.total = batch * a.nR;
+        a.C = (int)std::min<int64_t>(ps.C, a.total);
+        a.PR = ps.R + 1;
+        a.nsub = ps.nsub;
+        for (int q = 0; q < 12; ++q) a.sub[q] = ps.sub[q];
+        a.in_cfast = (a.nR >= a.C) ? 1 : 0;
+        a.out_cfast = (ps.Ns >= a.C) ? 1 : 0;
+        a.shift = p.shift;
+        a.mask = ((int64_t)1 << p.shift) - 1;
+        const size_t smem = 2 * (size_t)a.C * a.PR * sizeof(c2<T>);
+        const int64_t blocks = (a.total + a.C - 1) / a.C;
+        NUFFT_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_fft_pass<T><<<(unsigned)blocks, kThreads, smem, s>>>(src, dst, a, lo, hi, dir);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        src = dst;
+        dst = (dst == buf) ? work : buf;
+    }
+    *result = src;
+    return NUFFT_OK;
+}
+
+}  // namespace
+
+bool is_smooth(int64_t n) {
+    if (n < 1) return false;
+    for (int p : {2, 3, 5, 7}) while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int64_t next_smooth(int64_t n) {
+    if (n < 1) n = 1;
+    while (!is_smooth(n)) ++n;
+    return n;
+}
+
+FFTPlan::~FFTPlan() {
+    cudaFree(tw_lo);
+    cudaFree(tw_hi);
+    cudaFree(chirp);
+    cudaFree(chirp_hat_fwd);
+    cudaFree(chirp_hat_inv);
+}
+
+int64_t fft_work_elems(const FFTPlan& p) { return p.bluestein ? 2 * p.m : p.n; }
+
+nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
+    p.n = n;
+    p.prec = prec;
+    if (n < 1) return fail(NUFFT_ERR_ARG, "FFT length %lld < 1", (long long)n);
+    if (!is_smooth(n)) {
+        p.bluestein = true;
+        p.m = next_smooth(2 * n - 1);
+        p.sub.reset(new FFTPlan());
+        nufft_status st = fft_make(*p.sub, p.m, prec, s);
+        if (st != NUFFT_OK) return st;
+        const int64_t m = p.m;
+        double2 *hf = nullptr, *hi = nullptr, *work = nullptr;
+        NUFFT_CUDA_TRY(cudaMalloc(&hf, sizeof(double2) * m));
+        NUFFT_CUDA_TRY(cudaMalloc(&hi, sizeof(double2) * m));
+        NUFFT_CUDA_TRY(cudaMalloc(&work, sizeof(double2) * fft_work_elems(*p.sub)));
+        const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+        NUFFT_CUDA_TRY(cudaMalloc(&p.chirp, es * n));
+        NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_fwd, es * m));
+        NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_inv, es * m));
+        const int tb = 256;
+        k_blue_chirp<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
+            n, m, prec == 2 ? (double2*)p.chirp : nullptr, prec == 2 ? nullptr : (float2*)p.chirp, hf, hi);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        // the filter spectra are always formed in float64
+        FFTPlan p64;
+        st = fft_make(p64, m, 2, s);
+        if (st != NUFFT_OK) return st;
+        double2* res = nullptr;
+        for (int which = 0; which < 2; ++which) {
+            double2* h = which == 0 ? hf : hi;
+            st = fft_exec<double>(p64, h, work, 1, -1, s, &res);
+            if (st != NUFFT_OK) return st;
+            void* dst = which == 0 ? p.chirp_hat_fwd : p.chirp_hat_inv;
+            k_scale_c128_to<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
+                res, m, 1.0 / (double)m, prec == 2 ? (double2*)dst : nullptr, prec == 2 ? nullptr : (float2*)dst);
+            NUFFT_CUDA_TRY(cudaGetLastError());
+        }
+        NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(hf);
+        cudaFree(hi);
+        cudaFree(work);
+        return NUFFT_OK;
+    }
+    // two-level twiddle table
+    int shift = 0;
+    while (((int64_t)1 << (2 * shift)) < n) ++shift;
+    p.shift = shift;
+    const int64_t B = (int64_t)1 << shift;
+    const int64_t nhi = (n + B - 1) / B;
+    const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+    NUFFT_CUDA_TRY(cudaMalloc(&p.tw_lo, es * B));
+    NUFFT_CUDA_TRY(cudaMalloc(&p.tw_hi, es * nhi));
+    const int64_t cnt = std::max(B, nhi);
+    k_make_twiddles<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+        n, B, nhi, prec == 2 ? (double2*)p.tw_lo : nullptr, prec == 2 ? (double2*)p.tw_hi : nullptr,
+        prec == 2 ? nullptr : (float2*)p.tw_lo, prec == 2 ? nullptr : (float2*)p.tw_hi);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return prec == 2 ? make_passes<double>(p) : make_passes<float>(p);
+}
+
+template <typename T>
+nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
+                      c2<T>** result) {
+    if (batch <= 0) { *result = buf; return NUFFT_OK; }
+    if (!p.bluestein) return exec_passes<T>(p, buf, work, batch, dir, s, result);
+    const int64_t n = p.n, m = p.m;
+    c2<T>* a = work;
+    c2<T>* aw = work + m * batch;
+    const c2<T>* chirp = static_cast<const c2<T>*>(p.chirp);
+    const int tb = 256;
+    k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    c2<T>* r = nullptr;
+    nufft_status st = exec_passes<T>(*p.sub, a, aw, batch, -1, s, &r);
+    if (st != NUFFT_OK) return st;
+    const c2<T>* h = static_cast<const c2<T>*>(dir < 0 ? p.chirp_hat_fwd : p.chirp_hat_inv);
+    k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    c2<T>* r2 = nullptr;
+    st = exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
+    if (st != NUFFT_OK) return st;
+    k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    *result = buf;
+    return NUFFT_OK;
+}
+
+template nufft_status fft_exec<float>(const FFTPlan&, float2*, float2*, int64_t, int, cudaStream_t, float2**);
+template nufft_status fft_exec<double>(const FFTPlan&, double2*, double2*, int64_t, int, cudaStream_t, double2**);
+
+}  // namespace nufft45

@@ -1,0 +1,131 @@
+// Internal interfaces of the nufft45 library (host side, C++).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "nufft45.h"
+#include "common.cuh"
+
+namespace nufft45 {
+
+nufft_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line);
+nufft_status fail(nufft_status st, const char* fmt, ...);
+
+// ---------------------------------------------------------------- FFT ------
+// One Stockham autosort pass of composite radix R: for every j < n/R the R
+// inputs x[j + k n/R] are twiddled by W_{Ns R}^{(j mod Ns) k}, transformed by a
+// length-R DFT done in shared memory (sub-radices `sub`), and written to
+// y[(j/Ns) Ns R + (j mod Ns) + m Ns].  After all passes the output is in
+// natural order.
+struct FFTPass {
+    int R = 1;
+    int64_t Ns = 1;
+    int nsub = 0;
+    int sub[12] = {0};
+    int C = 1;          // butterflies (columns) per CTA
+};
+
+struct FFTPlan {
+    int64_t n = 0;
+    int prec = 0;                       // 1 = float, 2 = double
+    std::vector<FFTPass> passes;
+    // two-level table of W_n^e = e^{-j 2 pi e / n}: lo[e & (B-1)] * hi[e >> shift]
+    int shift = 0;
+    void* tw_lo = nullptr;
+    void* tw_hi = nullptr;
+    // Bluestein (n has a prime factor > 7): length-m convolution
+    bool bluestein = false;
+    int64_t m = 0;
+    std::unique_ptr<FFTPlan> sub;
+    void* chirp = nullptr;              // e^{+j pi k^2 / n}, k < n
+    void* chirp_hat_fwd = nullptr;      // FFT_m of the forward filter, / m
+    void* chirp_hat_inv = nullptr;      // FFT_m of the inverse filter, / m
+    ~FFTPlan();
+};
+
+bool is_smooth(int64_t n);                 // only prime factors 2, 3, 5, 7
+int64_t next_smooth(int64_t n);            // smallest smooth m >= n
+nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s);
+// scratch elements (complex) fft_exec needs besides its buffer, per batch item
+int64_t fft_work_elems(const FFTPlan& p);
+// In-place-by-result: transforms `buf` (batch contiguous items of n) with
+// dir = -1 (sum x e^{-j2pi jk/n}) or +1 (sum x e^{+j2pi jk/n}), unnormalised.
+// Returns the pointer that holds the result (buf or work).
+template <typename T>
+nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir,
+                      cudaStream_t s, c2<T>** result);
+
+// ------------------------------------------------------- node geometry ----
+// Nodes sorted by cell of a grid of size n (counting sort, ties by index),
+// plus the wrapped ("extended") copy used by output-stationary spreading: the
+// nodes of the last w/2 cells are prepended with cell - n and those of the
+// first w/2 cells appended with cell + n.  Grid point g gathers the extended
+// nodes [cstart[g], cstart[g + w]).
+struct Geometry {
+    int64_t N = 0, n = 0;
+    int w = 0;                 // halo width the extended arrays were built for
+    int* srt_perm = nullptr;   // sorted slot -> node index                [N]
+    int* srt_cell = nullptr;   //                                          [N]
+    double* srt_frac = nullptr;  // n t - cell in [0,1)                    [N]
+    float* srt_fracf = nullptr;  //                                        [N]
+    int* ext_perm = nullptr;   //                                          [2N]
+    int* ext_cell = nullptr;   //                                          [2N]
+    double* ext_frac = nullptr;  //                                        [2N]
+    float* ext_fracf = nullptr;  //                                        [2N]
+    int* cstart = nullptr;     // [n + w + 1]
+    int* dup_flag = nullptr;   // set when two nodes coincide mod 1
+};
+
+// ------------------------------------------------------------- launchers --
+struct KernelShape { int w; double beta; };
+
+void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s);
+nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n, int w,
+                            bool want_float, int* scratch_int, cudaStream_t s);
+int64_t geometry_scratch_ints(int64_t N, int64_t n);
+void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s);
+
+template <typename T>
+void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs,
+                   const c2<T>* wt_ext, c2<T>* grid, int64_t batch, cudaStream_t s);
+template <typename T>
+void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt,
+                   c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s);
+
+// out[b][k] = in[b][(k - K0) mod n] * fac[k], k < P
+template <typename T>
+void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0,
+                   const T* fac, int64_t batch, cudaStream_t s);
+// out[b][g] = in[b][k] * fac[k] where k = g' + K0 for the centred index g' of g, 0 elsewhere
+template <typename T>
+void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out,
+                  int64_t n, int64_t batch, cudaStream_t s);
+// out[b][k] = in[b][k] * (mulc ? mulc[k] : 1) * (fac ? fac[k] : 1)
+template <typename T>
+void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P,
+                      const c2<T>* mulc, const T* fac, int64_t batch, cudaStream_t s);
+
+// plan-stage kernels (float64)
+struct GLRule { int nq; double z[48]; double wq[48]; };
+void gauss_legendre_half(int nq, GLRule& r);   // nodes in (0,1), weights for int_0^1 of an even function
+// tables over k < M: mode 0: 1/phihat((k-K0)/n); 1: rho^k/phihat; 2: rho^-k/(P phihat);
+// 3: Lambda_k/phihat, Lambda_k = -rho^k/k; 4: rho^k; 5: rho^-k/P
+void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
+                  int64_t P, double* out_d, float* out_f, cudaStream_t s);
+// out[i] = e^{sign j 2 pi K0 t_{perm[i]}}, i < (count_dev ? *count_dev : cap)
+void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
+                double2* out, cudaStream_t s);
+void launch_fold(const double2* B, int64_t nR, int64_t K0R, const double* fac, int64_t P, int eta, double2* Y,
+                 cudaStream_t s);
+void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
+                           cudaStream_t s);
+void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s);
+void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s);
+template <typename TS>
+void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
+                         const double2* w_user, c2<TS>* mod_out, c2<TS>* wmod_out, cudaStream_t s);
+
+}  // namespace nufft45

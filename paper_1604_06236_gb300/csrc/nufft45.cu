@@ -1,0 +1,616 @@
+// Host runtime and C ABI of the nufft45 library: parameter choice (Sec. V),
+// the cache of node-independent tables, the node-dependent plan (Sec. III,
+// Fig. 1 upper half), and the type-1/2/4/5 transforms (Figs. 1 and 2).
+#include "internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace nufft45 {
+
+// --------------------------------------------------------------- errors ----
+static thread_local char g_msg[512] = "";
+
+nufft_status fail(nufft_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+nufft_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line) {
+    const nufft_status st = (e == cudaErrorMemoryAllocation) ? NUFFT_ERR_ALLOC : NUFFT_ERR_CUDA;
+    fail(st, "%s failed: %s (%s:%d)", expr, cudaGetErrorString(e), file, line);
+    cudaGetLastError();   // clear a sticky launch error so the context stays usable
+    return st;
+}
+
+// Test hook: make the next `count` device allocations of this library fail
+// as if the device were out of memory.
+static int g_fail_allocs = 0;
+
+// ------------------------------------------------- stream-ordered arenas ---
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    cudaStream_t stream = nullptr;
+    nufft_status reserve(size_t bytes, cudaStream_t s) {
+        stream = s;
+        cap = bytes;
+        if (g_fail_allocs > 0) { --g_fail_allocs; return fail(NUFFT_ERR_ALLOC, "injected allocation failure"); }
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s);
+        if (e != cudaSuccess) { base = nullptr; return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__); }
+        return NUFFT_OK;
+    }
+    template <typename X> X* take(size_t count) {
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + count * sizeof(X);
+        return reinterpret_cast<X*>(base + off);
+    }
+    void release() {
+        if (base) cudaFreeAsync(base, stream);
+        base = nullptr;
+    }
+};
+
+// a size accumulator with the same alignment rule as Arena::take
+struct Sizer {
+    size_t used = 0;
+    template <typename X> void add(size_t count) { used = ((used + 255) & ~(size_t)255) + count * sizeof(X); }
+};
+
+static void init_pool_once() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;   // keep freed blocks for reuse instead of returning them
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+// -------------------------------------------------------- parameters -------
+struct Params {
+    int64_t N = 0;
+    int prec = 0;
+    double tol = 0;
+    double gamma = 0, a = 0, rho = 0, log_rho = 0, rhoP = 0;
+    int eta = 0;
+    int64_t R = 0;
+    int64_t ns = 0, nR = 0;
+    int64_t K0s = 0, K0R = 0;
+    KernelShape ks_solve{0, 0}, ks_plan{0, 0};
+};
+
+// ES kernel shape for an even width w on an oversampling-2 grid
+static KernelShape es_shape(int w) { return KernelShape{w, 2.30 * w}; }
+
+// Sec. V: the truncation of Eq. 42 at R = eta P leaves a relative error close
+// to mu ~ gamma^-eta (Eq. 49 with gamma = e^{2 pi P a}); round-off in the
+// scaling by e^{2 pi p a} of Eqs. 31 and 43 grows with gamma.  float64:
+// gamma = 1000 and eta from tol; float32 transforms: gamma = 30, eta = 5, so
+// that the float64 plan is accurate to ~1e-8 and the float32 stages dominate.
+static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
+    p.N = N;
+    p.prec = prec;
+    p.tol = tol;
+    int w_solve, w_plan;
+    if (prec == NUFFT_FP64) {
+        if (tol < 1e-12) return fail(NUFFT_ERR_ACCURACY, "tol %g below what the float64 path attains (1e-12)", tol);
+        p.gamma = 1000.0;
+        p.eta = std::max(2, (int)std::ceil(std::log10(4.0 / tol) / 3.0));
+        w_plan = w_solve = tol < 1e-8 ? 16 : 12;
+    } else {
+        if (tol < 1e-6) return fail(NUFFT_ERR_ACCURACY, "tol %g below what the float32 path attains (1e-6)", tol);
+        p.gamma = 30.0;
+        p.eta = 5;
+        w_plan = 14;
+        w_solve = 8;
+    }
+    p.log_rho = -std::log(p.gamma) / (double)N;
+    p.a = std::log(p.gamma) / (2.0 * M_PI * (double)N);
+    p.rho = std::exp(p.log_rho);
+    p.rhoP = 1.0 / p.gamma;
+    p.R = (int64_t)p.eta * N;
+    p.ks_solve = es_shape(w_solve);
+    p.ks_plan = es_shape(w_plan);
+    const int wmax = std::max(w_solve, w_plan);
+    p.ns = next_smooth(std::max<int64_t>(2 * N, 2 * wmax));
+    p.nR = next_smooth(std::max<int64_t>(2 * p.R, 2 * wmax));
+    p.K0s = N / 2;
+    p.K0R = p.R / 2;
+    return NUFFT_OK;
+}
+
+// ------------------------------------------ node-independent tables --------
+struct Tables {
+    Params prm;
+    FFTPlan fft_ns, fft_P;          // solve precision
+    FFTPlan fft_ns64, fft_P64, fft_nR64;
+    // float64 plan tables
+    double* fold = nullptr;         // Lambda_k / phihat_R, k < R
+    double* plan_place = nullptr;   // 1/phihat (plan width, grid ns), k < P
+    double* sneg64 = nullptr;       // rho^-k / P
+    // solve tables, solve precision
+    void* fac1 = nullptr;           // 1/phihat
+    void* fac5 = nullptr;           // rho^k/phihat
+    void* fac4 = nullptr;           // rho^-k/(P phihat)
+    void* rpos = nullptr;           // rho^k
+    void* sneg = nullptr;           // rho^-k/P
+    void* mem = nullptr;
+    ~Tables() { cudaFree(mem); }
+};
+
+using TablesPtr = std::shared_ptr<Tables>;
+static std::mutex g_cache_mu;
+static std::map<std::tuple<int64_t, int, double>, TablesPtr> g_cache;
+
+static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& out) {
+    TablesPtr t = std::make_shared<Tables>();
+    t->prm = prm;
+    const int64_t P = prm.N;
+    const size_t es = prm.prec == NUFFT_FP64 ? sizeof(double) : sizeof(float);
+    Sizer z;
+    z.add<double>(prm.R); z.add<double>(P); z.add<double>(P);
+    for (int i = 0; i < 5; ++i) z.add<char>(es * P);
+    if (g_fail_allocs > 0) { --g_fail_allocs; return fail(NUFFT_ERR_ALLOC, "injected allocation failure"); }
+    NUFFT_CUDA_TRY(cudaMalloc(&t->mem, z.used));
+    Arena ar;
+    ar.base = (char*)t->mem;
+    ar.cap = z.used;
+    t->fold = ar.take<double>(prm.R);
+    t->plan_place = ar.take<double>(P);
+    t->sneg64 = ar.take<double>(P);
+    t->fac1 = ar.take<char>(es * P);
+    t->fac5 = ar.take<char>(es * P);
+    t->fac4 = ar.take<char>(es * P);
+    t->rpos = ar.take<char>(es * P);
+    t->sneg = ar.take<char>(es * P);
+    nufft_status st;
+    const int sp = prm.prec == NUFFT_FP64 ? 2 : 1;
+    if ((st = fft_make(t->fft_ns, prm.ns, sp, s)) != NUFFT_OK) return st;
+    if ((st = fft_make(t->fft_P, P, sp, s)) != NUFFT_OK) return st;
+    if ((st = fft_make(t->fft_ns64, prm.ns, 2, s)) != NUFFT_OK) return st;
+    if ((st = fft_make(t->fft_P64, P, 2, s)) != NUFFT_OK) return st;
+    if ((st = fft_make(t->fft_nR64, prm.nR, 2, s)) != NUFFT_OK) return st;
+    GLRule glR, glS;
+    gauss_legendre_half(2 + (3 * prm.ks_plan.w) / 2 + 4, glR);
+    gauss_legendre_half(2 + (3 * prm.ks_solve.w) / 2 + 4, glS);
+    launch_table(prm.ks_plan, glR, prm.nR, prm.K0R, prm.R, prm.log_rho, 3, P, t->fold, nullptr, s);
+    launch_table(prm.ks_plan, glR, prm.ns, prm.K0s, P, prm.log_rho, 0, P, t->plan_place, nullptr, s);
+    launch_table(prm.ks_plan, glR, prm.ns, prm.K0s, P, prm.log_rho, 5, P, t->sneg64, nullptr, s);
+    const bool d = prm.prec == NUFFT_FP64;
+    void* tabs[5] = {t->fac1, t->fac5, t->fac4, t->rpos, t->sneg};
+    const int modes[5] = {0, 1, 2, 4, 5};
+    for (int i = 0; i < 5; ++i)
+        launch_table(prm.ks_solve, glS, prm.ns, prm.K0s, P, prm.log_rho, modes[i], P,
+                     d ? (double*)tabs[i] : nullptr, d ? nullptr : (float*)tabs[i], s);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    out = t;
+    return NUFFT_OK;
+}
+
+static nufft_status get_tables(const Params& prm, cudaStream_t s, TablesPtr& out) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto key = std::make_tuple(prm.N, prm.prec, prm.tol);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) { out = it->second; return NUFFT_OK; }
+    nufft_status st = make_tables(prm, s, out);
+    if (st == NUFFT_OK) g_cache[key] = out;
+    return st;
+}
+
+}  // namespace nufft45
+
+using namespace nufft45;
+
+// ------------------------------------------------------------------ plan ---
+struct nufft_plan_s {
+    Params prm;
+    TablesPtr tab;
+    cudaStream_t stream = nullptr;
+    Arena mem;                       // node-dependent buffers
+    Geometry gs;
+    uint64_t* T = nullptr;
+    double2* K64 = nullptr;
+    double2* D64 = nullptr;
+    double2* w64 = nullptr;
+    void* Ks = nullptr;              // K in the solve precision
+    void* wt1_ext = nullptr;         // e^{-j 2 pi K0 t}, extended slot order
+    void* wt5_ext = nullptr;         // w e^{-j 2 pi K0 t}
+    void* wt2_srt = nullptr;         // e^{+j 2 pi K0 t}, sorted slot order
+    void* wt4_srt = nullptr;         // w e^{+j 2 pi K0 t}
+    int64_t chunk = 1;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t solve_elem(const Params& p) { return p.prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2); }
+
+int64_t per_item_elems(const nufft_plan_s* pl) {
+    const Tables& t = *pl->tab;
+    return pl->prm.ns + fft_work_elems(t.fft_ns) + pl->prm.N + fft_work_elems(t.fft_P);
+}
+
+nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    cudaStream_t s = pl->stream;
+    const int64_t N = prm.N, P = N;
+    const bool f32 = prm.prec == NUFFT_FP32;
+    const size_t es = solve_elem(prm);
+    // persistent buffers
+    Sizer z;
+    z.add<uint64_t>(N);
+    z.add<int>(N); z.add<int>(N); z.add<double>(N); z.add<float>(N);
+    z.add<int>(2 * N); z.add<int>(2 * N); z.add<double>(2 * N); z.add<float>(2 * N);
+    z.add<int>(prm.ns + prm.ks_solve.w + 1); z.add<int>(1);
+    z.add<double2>(P); z.add<double2>(N); z.add<double2>(N);
+    z.add<char>(es * P);
+    z.add<char>(es * 2 * N); z.add<char>(es * 2 * N); z.add<char>(es * N); z.add<char>(es * N);
+    nufft_status st = pl->mem.reserve(z.used, s);
+    if (st != NUFFT_OK) return st;
+    Arena& m = pl->mem;
+    pl->T = m.take<uint64_t>(N);
+    Geometry& gs = pl->gs;
+    gs.srt_perm = m.take<int>(N); gs.srt_cell = m.take<int>(N); gs.srt_frac = m.take<double>(N);
+    gs.srt_fracf = m.take<float>(N);
+    gs.ext_perm = m.take<int>(2 * N); gs.ext_cell = m.take<int>(2 * N); gs.ext_frac = m.take<double>(2 * N);
+    gs.ext_fracf = m.take<float>(2 * N);
+    gs.cstart = m.take<int>(prm.ns + prm.ks_solve.w + 1);
+    gs.dup_flag = m.take<int>(1);
+    pl->K64 = m.take<double2>(P);
+    pl->D64 = m.take<double2>(N);
+    pl->w64 = m.take<double2>(N);
+    pl->Ks = m.take<char>(es * P);
+    pl->wt1_ext = m.take<char>(es * 2 * N);
+    pl->wt5_ext = m.take<char>(es * 2 * N);
+    pl->wt2_srt = m.take<char>(es * N);
+    pl->wt4_srt = m.take<char>(es * N);
+
+    // temporaries of the plan
+    Geometry gR;
+    Sizer zt;
+    const int64_t geo_ints = std::max(geometry_scratch_ints(N, prm.nR), geometry_scratch_ints(N, prm.ns));
+    zt.add<int>(geo_ints);
+    zt.add<int>(N); zt.add<int>(N); zt.add<double>(N);
+    zt.add<int>(2 * N); zt.add<int>(2 * N); zt.add<double>(2 * N);
+    zt.add<int>(prm.nR + prm.ks_plan.w + 1); zt.add<int>(1);
+    zt.add<double2>(2 * N);                                   // plan strengths
+    zt.add<double2>(prm.nR); zt.add<double2>(fft_work_elems(tab.fft_nR64));
+    zt.add<double2>(P); zt.add<double2>(fft_work_elems(tab.fft_P64));
+    zt.add<double2>(prm.ns); zt.add<double2>(fft_work_elems(tab.fft_ns64));
+    zt.add<double2>(N);                                       // modulation, sorted order
+    zt.add<unsigned long long>(1);
+    Arena tmp;
+    if ((st = tmp.reserve(zt.used, s)) != NUFFT_OK) return st;
+    int* geo = tmp.take<int>(geo_ints);
+    gR.srt_perm = tmp.take<int>(N); gR.srt_cell = tmp.take<int>(N); gR.srt_frac = tmp.take<double>(N);
+    gR.ext_perm = tmp.take<int>(2 * N); gR.ext_cell = tmp.take<int>(2 * N); gR.ext_frac = tmp.take<double>(2 * N);
+    gR.cstart = tmp.take<int>(prm.nR + prm.ks_plan.w + 1);
+    gR.dup_flag = tmp.take<int>(1);
+    double2* strR = tmp.take<double2>(2 * N);
+    double2* gridR = tmp.take<double2>(prm.nR);
+    double2* workR = tmp.take<double2>(fft_work_elems(tab.fft_nR64));
+    double2* vecP = tmp.take<double2>(P);
+    double2* workP = tmp.take<double2>(fft_work_elems(tab.fft_P64));
+    double2* gridS = tmp.take<double2>(prm.ns);
+    double2* workS = tmp.take<double2>(fft_work_elems(tab.fft_ns64));
+    double2* modp = tmp.take<double2>(N);
+    unsigned long long* sumT = tmp.take<unsigned long long>(1);
+
+    // nodes: exact turns; sum t_p mod 1 for the constant phase of Eq. 29
+    launch_canon(x_dev, N, pl->T, s);
+    launch_sum_turns(pl->T, N, sumT, s);
+    // geometry of the length-R type-1 grid and of the transforms' grid
+    if ((st = build_geometry(gR, pl->T, N, prm.nR, prm.ks_plan.w, false, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
+    // v(q/P) (Eqs. 13, 19, 28): type-1 of unit strengths for k = 0..R-1,
+    // centred at K0R by the strengths e^{-j 2 pi K0R t_p}, folded by Eq. 7
+    launch_mod(pl->T, gR.ext_perm, 2 * N, gR.cstart + (prm.nR + prm.ks_plan.w), (uint64_t)prm.K0R, -1, strR, s);
+    launch_spread<double>(gR, prm.ks_plan, nullptr, 0, strR, gridR, 1, s);
+    double2* BR = nullptr;
+    if ((st = fft_exec<double>(tab.fft_nR64, gridR, workR, 1, -1, s, &BR)) != NUFFT_OK) { tmp.release(); return st; }
+    launch_fold(BR, prm.nR, prm.K0R, tab.fold, P, prm.eta, vecP, s);
+    double2* v = nullptr;
+    if ((st = fft_exec<double>(tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
+    // K_q (Eq. 29)
+    launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, s);
+    if (!f32) NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->Ks, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
+    // L_m (Eq. 43) and the coefficients (m+1) L_{m+1} of L' (Eq. 16)
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(vecP, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
+    double2* F = nullptr;
+    if ((st = fft_exec<double>(tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
+    double2* dco = (F == vecP) ? workP : vecP;
+    launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
+    // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
+    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.ks_solve.w, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
+    launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, gridS, prm.ns, 1, s);
+    double2* gs_sp = nullptr;
+    if ((st = fft_exec<double>(tab.fft_ns64, gridS, workS, 1, +1, s, &gs_sp)) != NUFFT_OK) { tmp.release(); return st; }
+    launch_mod(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, modp, s);
+    launch_interp<double>(gs, prm.ks_plan, gs_sp, modp, pl->D64, N, 1, s);
+    // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
+    launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
+    const int* ext_count = gs.cstart + (prm.ns + prm.ks_solve.w);
+    if (f32) {
+        launch_slot_weights<float>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
+                                   (float2*)pl->wt1_ext, (float2*)pl->wt5_ext, s);
+        launch_slot_weights<float>(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->w64,
+                                   (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, s);
+    } else {
+        launch_slot_weights<double>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
+                                    (double2*)pl->wt1_ext, (double2*)pl->wt5_ext, s);
+        launch_slot_weights<double>(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->w64,
+                                    (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, s);
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    tmp.release();
+    return NUFFT_OK;
+}
+
+// ------------------------------------------------------------ transforms ---
+enum Op { OP_INV5, OP_INV4, OP_FWD1, OP_FWD2 };
+
+template <typename T>
+nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* out, int64_t bc, c2<T>* gA, c2<T>* gW,
+                       c2<T>* vA, c2<T>* vW, cudaStream_t s) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    const int64_t N = prm.N, P = N, ns = prm.ns;
+    const T* fac1 = (const T*)tab.fac1;
+    const T* fac5 = (const T*)tab.fac5;
+    const T* fac4 = (const T*)tab.fac4;
+    const T* rpos = (const T*)tab.rpos;
+    const T* sneg = (const T*)tab.sneg;
+    const c2<T>* K = (const c2<T>*)pl->Ks;
+    nufft_status st;
+    c2<T>* r = nullptr;
+    // the middle stage of Eqs. 37, 30, 31 on the vector in vA (already scaled
+    // by rho^k); returns the pointer holding DFT(K * P IDFT(.)) before rho^-m/P
+    auto middle = [&](c2<T>** res) -> nufft_status {
+        c2<T>* r1 = nullptr;
+        nufft_status e = fft_exec<T>(tab.fft_P, vA, vW, bc, +1, s, &r1);
+        if (e != NUFFT_OK) return e;
+        launch_pointwise<T>(r1, P, r1, P, P, K, nullptr, bc, s);
+        return fft_exec<T>(tab.fft_P, r1, r1 == vA ? vW : vA, bc, -1, s, res);
+    };
+    switch (op) {
+        case OP_INV5: {
+            launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            launch_select<T>(r, ns, vA, P, P, prm.K0s, fac5, bc, s);
+            if ((st = middle(&r)) != NUFFT_OK) return st;
+            launch_pointwise<T>(r, P, out, N, P, nullptr, sneg, bc, s);
+            break;
+        }
+        case OP_INV4: {
+            launch_pointwise<T>(in, N, vA, P, P, nullptr, rpos, bc, s);
+            if ((st = middle(&r)) != NUFFT_OK) return st;
+            launch_place<T>(r, P, P, prm.K0s, fac4, gA, ns, bc, s);
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
+            break;
+        }
+        case OP_FWD1: {
+            launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt1_ext, gA, bc, s);
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            launch_select<T>(r, ns, out, N, P, prm.K0s, fac1, bc, s);
+            break;
+        }
+        case OP_FWD2: {
+            launch_place<T>(in, N, P, prm.K0s, fac1, gA, ns, bc, s);
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt2_srt, out, N, bc, s);
+            break;
+        }
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template <typename T>
+nufft_status run_op(nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* out, int64_t batch, cudaStream_t s) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    const int64_t bc = std::min<int64_t>(batch, pl->chunk);
+    Sizer z;
+    z.add<c2<T>>(prm.ns * bc);
+    z.add<c2<T>>(fft_work_elems(tab.fft_ns) * bc);
+    z.add<c2<T>>(prm.N * bc);
+    z.add<c2<T>>(fft_work_elems(tab.fft_P) * bc);
+    Arena sc;
+    nufft_status st = sc.reserve(z.used, s);
+    if (st != NUFFT_OK) return st;
+    c2<T>* gA = sc.take<c2<T>>(prm.ns * bc);
+    c2<T>* gW = sc.take<c2<T>>(fft_work_elems(tab.fft_ns) * bc);
+    c2<T>* vA = sc.take<c2<T>>(prm.N * bc);
+    c2<T>* vW = sc.take<c2<T>>(fft_work_elems(tab.fft_P) * bc);
+    for (int64_t b0 = 0; b0 < batch && st == NUFFT_OK; b0 += bc) {
+        const int64_t nb = std::min(bc, batch - b0);
+        st = run_chunk<T>(pl, op, in + b0 * prm.N, out + b0 * prm.N, nb, gA, gW, vA, vW, s);
+    }
+    sc.release();
+    return st;
+}
+
+nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int64_t batch, nufft_stream_t stream) {
+    if (!plan) return fail(NUFFT_ERR_ARG, "null plan");
+    if (batch < 0) return fail(NUFFT_ERR_ARG, "negative batch");
+    if (batch == 0) return NUFFT_OK;
+    if (!in || !out) return fail(NUFFT_ERR_ARG, "null data pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = solve_elem(plan->prm) * (size_t)plan->prm.N * (size_t)batch;
+    const char* ib = (const char*)in;
+    const char* ob = (const char*)out;
+    if (ib < ob + bytes && ob < ib + bytes) return fail(NUFFT_ERR_ARG, "input and output overlap");
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    const void* din_p = in;
+    void* dout_p = out;
+    Arena stage;
+    if (!din || !dout) {
+        nufft_status st = stage.reserve(2 * bytes, s);
+        if (st != NUFFT_OK) return st;
+        char* a = stage.take<char>(bytes);
+        char* b = stage.take<char>(bytes);
+        if (!din) {
+            NUFFT_CUDA_TRY(cudaMemcpyAsync(a, in, bytes, cudaMemcpyHostToDevice, s));
+            din_p = a;
+        }
+        if (!dout) dout_p = b;
+    }
+    nufft_status st;
+    if (plan->prm.prec == NUFFT_FP64)
+        st = run_op<double>(plan, op, (const double2*)din_p, (double2*)dout_p, batch, s);
+    else
+        st = run_op<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s);
+    if (st == NUFFT_OK && !dout) {
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(out, dout_p, bytes, cudaMemcpyDeviceToHost, s));
+        NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    } else if (st == NUFFT_OK && !din) {
+        NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // the staged input must outlive its use
+    }
+    stage.release();
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream, nufft_plan_t* plan) {
+    if (!plan) return fail(NUFFT_ERR_ARG, "null plan output pointer");
+    *plan = nullptr;
+    if (N < 1 || N > ((int64_t)1 << 28)) return fail(NUFFT_ERR_ARG, "N = %lld out of range [1, 2^28]", (long long)N);
+    if (!x) return fail(NUFFT_ERR_ARG, "null node pointer");
+    if (prec != NUFFT_FP32 && prec != NUFFT_FP64) return fail(NUFFT_ERR_ARG, "precision %d is not NUFFT_FP32/NUFFT_FP64", prec);
+    if (!(tol > 0.0) || !std::isfinite(tol) || tol > 0.1) return fail(NUFFT_ERR_ARG, "tol %g out of range (0, 0.1]", tol);
+    Params prm;
+    nufft_status st = choose_params(N, tol, prec, prm);
+    if (st != NUFFT_OK) return st;
+    int dev = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    init_pool_once();
+    cudaStream_t s = (cudaStream_t)stream;
+    nufft_plan_s* pl = new nufft_plan_s();
+    pl->prm = prm;
+    pl->stream = s;
+    if ((st = get_tables(prm, s, pl->tab)) != NUFFT_OK) { delete pl; return st; }
+    // right-hand sides per pass: keep the transforms' scratch near 256 MiB
+    const int64_t item = per_item_elems(pl) * (int64_t)solve_elem(prm);
+    pl->chunk = std::max<int64_t>(1, ((int64_t)256 << 20) / std::max<int64_t>(1, item));
+    // nodes on the device (host arrays are staged)
+    const double* xd = x;
+    Arena xs;
+    if (!is_device_ptr(x)) {
+        if ((st = xs.reserve(sizeof(double) * N, s)) != NUFFT_OK) { delete pl; return st; }
+        double* d = xs.take<double>(N);
+        cudaError_t e = cudaMemcpyAsync(d, x, sizeof(double) * N, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { xs.release(); delete pl; return cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__); }
+        xd = d;
+    }
+    st = run_plan(pl, xd);
+    xs.release();
+    int dup = 0;
+    if (st == NUFFT_OK) {
+        cudaError_t e = cudaMemcpyAsync(&dup, pl->gs.dup_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "plan synchronisation", __FILE__, __LINE__);
+    }
+    if (st == NUFFT_OK && dup) st = fail(NUFFT_ERR_DUP_NODES, "two nodes coincide modulo 2 pi");
+    if (st != NUFFT_OK) {
+        pl->mem.release();
+        cudaStreamSynchronize(s);
+        delete pl;
+        return st;
+    }
+    *plan = pl;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream) {
+    return run_public(plan, OP_INV5, f, c, batch, stream);
+}
+nufft_status nufft_inv4(nufft_plan_t plan, const void* A, void* a, int64_t batch, nufft_stream_t stream) {
+    return run_public(plan, OP_INV4, A, a, batch, stream);
+}
+nufft_status nufft_fwd1(nufft_plan_t plan, const void* a, void* A, int64_t batch, nufft_stream_t stream) {
+    return run_public(plan, OP_FWD1, a, A, batch, stream);
+}
+nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream) {
+    return run_public(plan, OP_FWD2, c, f, batch, stream);
+}
+
+nufft_status nufft_destroy(nufft_plan_t plan) {
+    if (!plan) return NUFFT_OK;
+    plan->mem.release();
+    cudaStreamSynchronize(plan->stream);
+    delete plan;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_plan_info(nufft_plan_t plan, nufft_plan_info_t* info) {
+    if (!plan || !info) return fail(NUFFT_ERR_ARG, "null argument");
+    const Params& p = plan->prm;
+    info->N = p.N; info->prec = p.prec; info->tol = p.tol;
+    info->gamma = p.gamma; info->a = p.a; info->rho = p.rho;
+    info->eta = p.eta; info->R = p.R;
+    info->grid_solve = p.ns; info->grid_plan = p.nR;
+    info->w_solve = p.ks_solve.w; info->w_plan = p.ks_plan.w;
+    info->beta_solve = p.ks_solve.beta; info->beta_plan = p.ks_plan.beta;
+    info->batch_chunk = plan->chunk;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_stream_t stream) {
+    if (!plan || !dst) return fail(NUFFT_ERR_ARG, "null argument");
+    const double2* src = which == 0 ? plan->K64 : which == 1 ? plan->D64 : which == 2 ? plan->w64 : nullptr;
+    if (!src) return fail(NUFFT_ERR_ARG, "unknown export %d", which);
+    cudaStream_t s = (cudaStream_t)stream;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double2) * plan->prm.N, cudaMemcpyDefault, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+nufft_status nufft_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache.clear();
+    return NUFFT_OK;
+}
+
+const char* nufft_status_string(nufft_status st) {
+    switch (st) {
+        case NUFFT_OK: return "NUFFT_OK";
+        case NUFFT_ERR_ARG: return "NUFFT_ERR_ARG";
+        case NUFFT_ERR_DUP_NODES: return "NUFFT_ERR_DUP_NODES";
+        case NUFFT_ERR_ALLOC: return "NUFFT_ERR_ALLOC";
+        case NUFFT_ERR_CUDA: return "NUFFT_ERR_CUDA";
+        case NUFFT_ERR_TIMEOUT: return "NUFFT_ERR_TIMEOUT";
+        case NUFFT_ERR_ACCURACY: return "NUFFT_ERR_ACCURACY";
+    }
+    return "unknown status";
+}
+
+const char* nufft_last_error_message(void) { return g_msg; }
+
+// Test hook (not part of the public header): make the next `count` device
+// allocations fail with NUFFT_ERR_ALLOC, to exercise the error paths without
+// exhausting the device.
+void nufft_debug_fail_allocs(int count) { g_fail_allocs = count; }
+
+}  // extern "C"

@@ -1,0 +1,459 @@
+// Node geometry (exact cells, counting sort), output-stationary spreading
+// (type-1 gridding) and interpolation (type-2), and the pointwise stages.
+//
+// Spreading is a gather: every grid point g owns its sum
+//     b_g = sum_p c_p phi(g - n t_p),
+// and reads the nodes of cells [g - w/2, g + w/2 - 1], a contiguous range of
+// the cell-sorted (and periodically extended) node list.  A CTA stages the
+// nodes of its tile in shared memory, each thread accumulates its grid
+// point(s) in registers for a chunk of right-hand sides, and the tile is
+// written once with coalesced stores: no atomics on the grid, deterministic
+// summation order.
+#include "internal.h"
+
+#include <algorithm>
+
+namespace nufft45 {
+
+namespace {
+
+constexpr int kTB = 256;
+
+inline unsigned nblk(int64_t n, int tb = kTB) { return (unsigned)((n + tb - 1) / tb); }
+
+__global__ void k_canon(const double* __restrict__ x, int64_t N, uint64_t* __restrict__ T) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    // t = x / (2 pi) mod 1 (IEEE division and floor), T = trunc(t 2^64)
+    double u = x[i] / 6.283185307179586476925286766559;
+    u -= floor(u);
+    if (u >= 1.0) u = 0.0;
+    T[i] = __double2ull_rz(u * 18446744073709551616.0);
+}
+
+// cell = floor(n t) = high word of T*n, fraction = low word / 2^64, exactly
+__global__ void k_cells(const uint64_t* __restrict__ T, int64_t N, uint64_t n, int* __restrict__ cell,
+                        double* __restrict__ frac, int* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint64_t t = T[i];
+    const int c = (int)__umul64hi(t, n);
+    cell[i] = c;
+    frac[i] = (double)(t * n) * 5.42101086242752217003726400434970855712890625e-20;
+    atomicAdd(&count[c], 1);
+}
+
+// exclusive scan of int counts, three phases (block scan, scan of block sums,
+// add); out has L + 1 entries, out[L] = total
+constexpr int kScanTB = 1024;
+constexpr int kScanPer = 2 * kScanTB;
+
+__global__ void k_scan_blocks(const int* __restrict__ in, int64_t L, int* __restrict__ out, int* __restrict__ sums) {
+    __shared__ int s[kScanPer];
+    const int64_t base = (int64_t)blockIdx.x * kScanPer;
+    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x) s[e] = (base + e < L) ? in[base + e] : 0;
+    __syncthreads();
+    // Blelloch up-sweep / down-sweep
+    int off = 1;
+    for (int d = kScanPer >> 1; d > 0; d >>= 1) {
+        __syncthreads();
+        if (threadIdx.x < d) {
+            int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
+            s[bi] += s[ai];
+        }
+        off <<= 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { sums[blockIdx.x] = s[kScanPer - 1]; s[kScanPer - 1] = 0; }
+    for (int d = 1; d < kScanPer; d <<= 1) {
+        off >>= 1;
+        __syncthreads();
+        if (threadIdx.x < d) {
+            int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
+            int t = s[ai]; s[ai] = s[bi]; s[bi] += t;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x)
+        if (base + e < L) out[base + e] = s[e];
+}
+
+__global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict__ total) {
+    // one block, sequential over chunks of blockDim with a carry
+    __shared__ int s[kScanTB];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int v = i < nb ? sums[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+            int t = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + s[threadIdx.x] - v;   // exclusive
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int64_t L, const int* __restrict__ sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L) out[i] += sums[i / kScanPer];
+}
+
+__global__ void k_scatter(const int* __restrict__ cell, int64_t N, const int* __restrict__ start,
+                          int* __restrict__ fill, int* __restrict__ perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int c = cell[i];
+    perm[start[c] + atomicAdd(&fill[c], 1)] = (int)i;
+}
+
+// order the nodes of each cell by (T, index): deterministic, and equal nodes
+// become neighbours for the duplicate check
+__global__ void k_order_cells(const int* __restrict__ start, int64_t n, const uint64_t* __restrict__ T,
+                              int* __restrict__ perm) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int a = start[c], b = start[c + 1];
+    for (int i = a + 1; i < b; ++i) {
+        const int p = perm[i];
+        const uint64_t tp = T[p];
+        int j = i - 1;
+        while (j >= a) {
+            const int q = perm[j];
+            const uint64_t tq = T[q];
+            if (tq < tp || (tq == tp && q < p)) break;
+            perm[j + 1] = q;
+            --j;
+        }
+        perm[j + 1] = p;
+    }
+}
+
+__global__ void k_sorted_fill(const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ frac,
+                              const uint64_t* __restrict__ T, int64_t N, int* __restrict__ scell,
+                              double* __restrict__ sfrac, float* __restrict__ sfracf, int* __restrict__ dup) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = perm[i];
+    scell[i] = cell[p];
+    const double f = frac[p];
+    sfrac[i] = f;
+    if (sfracf) sfracf[i] = (float)f;
+    if (i + 1 < N && T[perm[i + 1]] == T[p]) *dup = 1;
+}
+
+// extended list: [nodes of cells n-h..n-1, shifted by -n] [all nodes] [nodes of cells 0..h-1, shifted by +n]
+__global__ void k_ext_fill(const int* __restrict__ start, int64_t n, int h, int64_t N, const int* __restrict__ sperm,
+                           const int* __restrict__ scell, const double* __restrict__ sfrac,
+                           int* __restrict__ eperm, int* __restrict__ ecell, double* __restrict__ efrac,
+                           float* __restrict__ efracf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pre = start[n] - start[n - h];
+    const int post = start[h];
+    if (i >= pre + N + post) return;
+    int64_t slot;
+    int shift;
+    if (i < pre) { slot = start[n - h] + i; shift = -(int)n; }
+    else if (i < pre + N) { slot = i - pre; shift = 0; }
+    else { slot = i - pre - N; shift = (int)n; }
+    eperm[i] = sperm[slot];
+    ecell[i] = scell[slot] + shift;
+    const double f = sfrac[slot];
+    efrac[i] = f;
+    if (efracf) efracf[i] = (float)f;
+}
+
+// cstart[e], e = cell + w/2 in [0, n + w]
+__global__ void k_cstart(const int* __restrict__ start, int64_t n, int w, int64_t N, int* __restrict__ cstart) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = w / 2;
+    if (e > n + w) return;
+    const int pre = start[n] - start[n - h];
+    int v;
+    if (e < h) v = start[n - h + e] - start[n - h];
+    else if (e < n + h) v = pre + start[e - h];
+    else v = pre + (int)N + start[e - h - n];
+    cstart[e] = v;
+}
+
+__global__ void k_sum_turns(const uint64_t* __restrict__ T, int64_t N, unsigned long long* out) {
+    // sum mod 2^64 (exactly sum t_p mod 1); unsigned wrap-around is associative
+    __shared__ unsigned long long s[kTB];
+    unsigned long long acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        acc += T[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) s[threadIdx.x] += s[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, s[0]);
+}
+
+// ---- spreading (gather) -----------------------------------------------------
+template <typename T> struct FracPtr;
+template <> struct FracPtr<float> { static const float* ext(const Geometry& g) { return g.ext_fracf; } static const float* srt(const Geometry& g) { return g.srt_fracf; } };
+template <> struct FracPtr<double> { static const double* ext(const Geometry& g) { return g.ext_frac; } static const double* srt(const Geometry& g) { return g.srt_frac; } };
+
+constexpr int kChunk = 256;
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, T beta, const int* __restrict__ cstart,
+                                                const int* __restrict__ eperm, const int* __restrict__ ecell,
+                                                const T* __restrict__ efrac, const c2<T>* __restrict__ src,
+                                                int64_t src_bs, const c2<T>* __restrict__ wt, c2<T>* __restrict__ grid,
+                                                int64_t batch) {
+    __shared__ int s_cell[kChunk];
+    __shared__ T s_frac[kChunk];
+    __shared__ c2<T> s_str[BC][kChunk];
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t g = g0 + threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * BC;
+    const int64_t glast = min(g0 + (int64_t)blockDim.x, n) - 1;
+    const int t0 = cstart[g0], t1 = cstart[glast + w];
+    int lo = 0, hi = 0;
+    if (g < n) { lo = cstart[g]; hi = cstart[g + w]; }
+    c2<T> acc[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) acc[b] = mk<T>(0, 0);
+    for (int ch = t0; ch < t1; ch += kChunk) {
+        const int cnt = min(kChunk, t1 - ch);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int i = ch + e;
+            s_cell[e] = ecell[i];
+            s_frac[e] = efrac[i];
+            const c2<T> wv = wt[i];
+            if (src) {
+                const int p = eperm[i];
+#pragma unroll
+                for (int b = 0; b < BC; ++b)
+                    s_str[b][e] = (b0 + b < batch) ? cmul(src[(b0 + b) * src_bs + p], wv) : mk<T>(0, 0);
+            } else {
+#pragma unroll
+                for (int b = 0; b < BC; ++b) s_str[b][e] = wv;
+            }
+        }
+        __syncthreads();
+        const int a = max(lo, ch), z = min(hi, ch + cnt);
+        for (int i = a; i < z; ++i) {
+            const int e = i - ch;
+            const T d = (T)(g - s_cell[e]) - s_frac[e];
+            const T ph = es_kernel<T>(d, two_over_w, beta);
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                acc[b].x = fma(ph, s_str[b][e].x, acc[b].x);
+                acc[b].y = fma(ph, s_str[b][e].y, acc[b].y);
+            }
+        }
+    }
+    if (g < n) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b0 + b < batch) grid[(b0 + b) * n + g] = acc[b];
+    }
+}
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T two_over_w, T beta,
+                                                const int* __restrict__ sperm, const int* __restrict__ scell,
+                                                const T* __restrict__ sfrac, const c2<T>* __restrict__ grid,
+                                                const c2<T>* __restrict__ wt, c2<T>* __restrict__ dst, int64_t dst_bs,
+                                                int64_t batch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t b0 = (int64_t)blockIdx.y * BC;
+    const int c = scell[i];
+    const T f = sfrac[i];
+    const int h = w / 2;
+    T ker[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<T>((T)(m + 1 - h) - f, two_over_w, beta) : (T)0;
+    c2<T> acc[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) acc[b] = mk<T>(0, 0);
+    int64_t gi = c + 1 - h;
+    if (gi < 0) gi += n;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (m < w) {
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                if (b0 + b < batch) {
+                    const c2<T> v = grid[(b0 + b) * n + gi];
+                    acc[b].x = fma(ker[m], v.x, acc[b].x);
+                    acc[b].y = fma(ker[m], v.y, acc[b].y);
+                }
+            }
+            if (++gi == n) gi = 0;
+        }
+    }
+    const int p = sperm[i];
+    const c2<T> wv = wt[i];
+#pragma unroll
+    for (int b = 0; b < BC; ++b)
+        if (b0 + b < batch) dst[(b0 + b) * dst_bs + p] = cmul(acc[b], wv);
+}
+
+template <typename T>
+__global__ void k_select(const c2<T>* __restrict__ in, int64_t n, c2<T>* __restrict__ out, int64_t out_bs, int64_t P,
+                         int64_t K0, const T* __restrict__ fac, int64_t batch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * batch) return;
+    const int64_t b = i / P, k = i - b * P;
+    const int64_t src = imod(k - K0, n);
+    out[b * out_bs + k] = cscale(in[b * n + src], fac[k]);
+}
+
+template <typename T>
+__global__ void k_place(const c2<T>* __restrict__ in, int64_t in_bs, int64_t P, int64_t K0, const T* __restrict__ fac,
+                        c2<T>* __restrict__ out, int64_t n, int64_t batch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * batch) return;
+    const int64_t b = i / n, gidx = i - b * n;
+    // centred index of grid slot gidx: k' in [-K0, P - K0)
+    const int64_t kc = gidx < n - K0 ? gidx : gidx - n;
+    const int64_t k = kc + K0;
+    c2<T> v = mk<T>(0, 0);
+    if (k >= 0 && k < P) v = cscale(in[b * in_bs + k], fac[k]);
+    out[i] = v;
+}
+
+template <typename T>
+__global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* __restrict__ out, int64_t out_bs,
+                            int64_t P, const c2<T>* __restrict__ mulc, const T* __restrict__ fac, int64_t batch) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * batch) return;
+    const int64_t b = i / P, k = i - b * P;
+    c2<T> v = in[b * in_bs + k];
+    if (mulc) v = cmul(v, mulc[k]);
+    if (fac) v = cscale(v, fac[k]);
+    out[b * out_bs + k] = v;
+}
+
+}  // namespace
+
+void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s) {
+    k_canon<<<nblk(N), kTB, 0, s>>>(x, N, T);
+}
+
+void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    const int blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + kTB - 1) / kTB));
+    k_sum_turns<<<blocks, kTB, 0, s>>>(T, N, out);
+}
+
+int64_t geometry_scratch_ints(int64_t N, int64_t n) {
+    // cell[N] + count[n+1] + start[n+1] + sums + total
+    const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
+    return 2 * N + 2 * (n + 2) + nb + 2 + 2 * N /* frac as doubles */;
+}
+
+nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n, int w, bool want_float,
+                            int* scratch, cudaStream_t s) {
+    if (n < 2 * w) return fail(NUFFT_ERR_ARG, "grid %lld too small for width %d", (long long)n, w);
+    g.N = N; g.n = n; g.w = w;
+    int* cell = scratch;
+    double* frac = reinterpret_cast<double*>(scratch + 2 * N);   // 8-byte aligned: 2N ints
+    int* count = scratch + 4 * N;
+    int* start = count + (n + 2);
+    int* sums = start + (n + 2);
+    const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
+    NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(g.dup_flag, 0, sizeof(int), s));
+    k_cells<<<nblk(N), kTB, 0, s>>>(T, N, (uint64_t)n, cell, frac, count);
+    k_scan_blocks<<<(unsigned)nb, kScanTB, 0, s>>>(count, n + 1, start, sums);
+    k_scan_sums<<<1, kScanTB, 0, s>>>(sums, nb, sums + nb);
+    k_scan_add<<<nblk(n + 1), kTB, 0, s>>>(start, n + 1, sums);
+    NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
+    k_scatter<<<nblk(N), kTB, 0, s>>>(cell, N, start, count, g.srt_perm);
+    k_order_cells<<<nblk(n), kTB, 0, s>>>(start, n, T, g.srt_perm);
+    k_sorted_fill<<<nblk(N), kTB, 0, s>>>(g.srt_perm, cell, frac, T, N, g.srt_cell, g.srt_frac,
+                                          want_float ? g.srt_fracf : nullptr, g.dup_flag);
+    k_ext_fill<<<nblk(2 * N), kTB, 0, s>>>(start, n, w / 2, N, g.srt_perm, g.srt_cell, g.srt_frac, g.ext_perm,
+                                           g.ext_cell, g.ext_frac, want_float ? g.ext_fracf : nullptr);
+    k_cstart<<<nblk(n + w + 1), kTB, 0, s>>>(start, n, w, N, g.cstart);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template <typename T>
+void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs, const c2<T>* wt_ext,
+                   c2<T>* grid, int64_t batch, cudaStream_t s) {
+    const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
+    const T* ef = FracPtr<T>::ext(g);
+    if (batch == 1) {
+        dim3 gr(nblk(g.n), 1);
+        k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+                                          wt_ext, grid, batch);
+    } else if (batch <= 4 || sizeof(T) == 8) {
+        dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
+        k_spread<T, 4><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+                                          wt_ext, grid, batch);
+    } else {
+        dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
+        k_spread<T, 8><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+                                          wt_ext, grid, batch);
+    }
+}
+
+template <typename T>
+void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt, c2<T>* dst,
+                   int64_t dst_bs, int64_t batch, cudaStream_t s) {
+    const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
+    const T* sf = FracPtr<T>::srt(g);
+    if (batch == 1) {
+        dim3 gr(nblk(g.N), 1);
+        k_interp<T, 1><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
+                                          dst_bs, batch);
+    } else {
+        dim3 gr(nblk(g.N), (unsigned)((batch + 3) / 4));
+        k_interp<T, 4><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
+                                          dst_bs, batch);
+    }
+}
+
+template <typename T>
+void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0, const T* fac,
+                   int64_t batch, cudaStream_t s) {
+    k_select<T><<<nblk(P * batch), kTB, 0, s>>>(in, n, out, out_bs, P, K0, fac, batch);
+}
+
+template <typename T>
+void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out, int64_t n,
+                  int64_t batch, cudaStream_t s) {
+    k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch);
+}
+
+template <typename T>
+void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P, const c2<T>* mulc,
+                      const T* fac, int64_t batch, cudaStream_t s) {
+    k_pointwise<T><<<nblk(P * batch), kTB, 0, s>>>(in, in_bs, out, out_bs, P, mulc, fac, batch);
+}
+
+#define INST(T)                                                                                                  \
+    template void launch_spread<T>(const Geometry&, KernelShape, const c2<T>*, int64_t, const c2<T>*, c2<T>*,   \
+                                   int64_t, cudaStream_t);                                                       \
+    template void launch_interp<T>(const Geometry&, KernelShape, const c2<T>*, const c2<T>*, c2<T>*, int64_t,   \
+                                   int64_t, cudaStream_t);                                                       \
+    template void launch_select<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, int64_t, const T*, int64_t, \
+                                   cudaStream_t);                                                                \
+    template void launch_place<T>(const c2<T>*, int64_t, int64_t, int64_t, const T*, c2<T>*, int64_t, int64_t,  \
+                                  cudaStream_t);                                                                 \
+    template void launch_pointwise<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, const c2<T>*, const T*,  \
+                                      int64_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace nufft45
