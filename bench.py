@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Throughput of the non-iterative type-4/5 inverse NUFFT on GB300.
+
+Workload (one "step" = one pass of the whole hot path on one batch):
+  N = 65536 nodes x_k = 2 pi (k + u_k)/N, u_k ~ U(-0.45, 0.45), new nodes every
+  step; nufft_plan on those nodes (float64 node weights, kernel samples and
+  scaling factors), then a type-5 inverse of B = 64 complex64 sample vectors
+  and a type-4 inverse of B = 64 complex64 spectra (CN(0,1) data), both in the
+  float32-split path at rel-L2 <= 1e-5.  2 B inverse transforms per step.
+
+The timed value is taken with CUDA events around each step on the launching
+stream (inputs already in HBM), with a 512 MiB write between steps to flush
+L2; the K steps are bracketed by a barrier and synchronisation.  Under
+torchrun every rank runs its own replica (the transforms of independent
+problems do not exchange data) and `value` sums the ranks' transforms over
+the slowest rank's time.
+
+`--impl reference` times the float64 CPU oracle (dense matrix by exact-phase
+direct sums, Gaussian elimination) on this host instead.
+"""
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inverse NUFFT transforms/sec and Mpoints/sec at rel-L2 ≤1e-5 (FP32) / ≤1e-10 (FP64)"
+WORKLOAD = "type-4 + type-5 inverse NUFFT, N=65536 jittered nodes u~U(-0.45,0.45), plan per step, batch 64 RHS each"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ peaks -------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since it was captured."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1604_06236_gb300", "csrc", ent["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["dram_bytes_per_launch"] if sha == ent["source_sha256_16"] else None
+
+
+# ------------------------------------------------------------ reference ----
+def oracle_sample(seconds_hint=15.0):
+    """Time the float64 oracle's type-5 + type-4 inversion (matrix by exact-phase
+    direct sums, LU) on a bounded sample: N_s nodes with the same node law.
+    The rate is scaled to N = 65536 by the O(N^3) cost of elimination."""
+    import oracle
+    import synth
+    oracle.build()
+    n_s = 2048
+    x = synth.jittered_nodes(n_s, 0.45, seed=123)
+    s = synth.cn01(n_s, seed=124)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.inv5(x, s)
+        oracle.inv4(x, s)
+        done += 2
+        if time.perf_counter() - t0 >= seconds_hint:
+            break
+    dt = time.perf_counter() - t0
+    rate_sample = done / dt
+    scale = (n_s / 65536.0) ** 3
+    return {
+        "value": rate_sample * scale,
+        "unit": "transforms/s",
+        "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": "%d float64 inversions (type-5 + type-4, LU on the exact-phase dense matrix) at N=%d, "
+                  "u~U(-0.45,0.45), %.1f s; measured %.3f transforms/s at N=%d, scaled to N=65536 by (N_s/N)^3"
+                  % (done, n_s, dt, rate_sample, n_s),
+    }
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    n_s = 2048
+    x = synth.jittered_nodes(n_s, 0.45, seed=123)
+    s = synth.cn01(n_s, seed=124)
+    for _ in range(args.warmup):
+        oracle.inv5(x, s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.inv5(x, s)
+        oracle.inv4(x, s)
+    dt = time.perf_counter() - t0
+    scale = (n_s / 65536.0) ** 3
+    value = 2 * args.steps / dt * scale
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3 / scale,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 65536, "reference_sample_N": n_s},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "each step: one type-5 and one type-4 float64 inversion by the dense oracle "
+                                   "(exact-phase matrix, LU) at N=%d with the same node law; rate scaled to "
+                                   "N=65536 by (N_s/N)^3" % n_s},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU arm -----
+def run_gpu(args):
+    import torch
+    import synth
+    import paper_1604_06236_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.build()
+    L = pkg.lib()
+    dev = torch.device("cuda", local)
+    N, B = args.N, args.batch
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM: node sets for every step, CN(0,1) data
+    nsteps = args.warmup + args.steps
+    xs = [torch.from_numpy(synth.jittered_nodes(N, 0.45, seed=1000 * rank + i)).to(dev) for i in range(nsteps)]
+    f = torch.from_numpy(synth.cn01((B, N), seed=7 + rank)).to(torch.complex64).to(dev)
+    A = torch.from_numpy(synth.cn01((B, N), seed=8 + rank)).to(torch.complex64).to(dev)
+    S = torch.empty_like(f)
+    a = torch.empty_like(A)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(i, prec=pkg.FP32, fi=f, Ai=A, Si=S, ai=a):
+        plan = pkg.Plan(xs[i % nsteps], prec=prec)
+        plan.inv5(fi, out=Si)
+        plan.inv4(Ai, out=ai)
+        plan.close()
+
+    def timed(fn, steps, warm):
+        for i in range(warm):
+            fn(i)
+        torch.cuda.synchronize()
+        total = 0.0
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        for i in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            fn(warm + i)
+            ev1.record(stream)
+            ev1.synchronize()
+            total += ev0.elapsed_time(ev1)
+        return total
+
+    # ---- main timed region (FP32-split path, plan per step) --------------
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.nufft_profile_enable(1)
+    launches0 = L.nufft_launch_count()
+    t_wall0 = time.perf_counter()
+    total_ms = 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for i in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        step(args.warmup + i)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    launches = L.nufft_launch_count() - launches0
+    L.nufft_profile_enable(0)
+    clk = clocks.stop()
+    entries = (pkg.ProfileEntry * 16)()
+    cnt = ctypes.c_int()
+    pkg.check(L.nufft_profile_read(entries, 16, ctypes.byref(cnt)))
+    prof = {e.name.decode(): {"launches": e.launches, "ms": e.ms, "bytes": e.bytes} for e in entries[:cnt.value]}
+
+    t_max = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    transforms = 2 * B * args.steps * ws
+    value = transforms / (t_max / 1e3)
+
+    # ---- roofline of the dominant kernel (events over the timed region) ---
+    peak, peak_src = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": committed_traffic(dname),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"],
+                "avg_launch_us": d["ms"] / d["launches"] * 1e3,
+                "share_of_step": d["ms"] / total_ms, "peak_source": peak_src + " (hbm_gbs, copy test)"}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "transforms/s", "mpoints_per_s": value * N / 1e6,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 transforms (complex64 data), f64 plan", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "batch": B, "transforms_per_step": 2 * B,
+                   "tol": 1e-5, "plan_per_step": True,
+                   "l2": "512 MiB buffer written between timed steps (outside the events)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                        "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1)} for k, v in prof.items()},
+        "wall_s": wall,
+    }
+
+    # ---- side measurements (rank 0 reports; replicas run the same) -------
+    if not args.quick:
+        # solve only (plan cached), FP32
+        plan = pkg.Plan(xs[0], prec=pkg.FP32)
+
+        def solve_only(i):
+            plan.inv5(f, out=S)
+            plan.inv4(A, out=a)
+        ms = timed(solve_only, args.steps, 3)
+        result["solve_only"] = {"value": 2 * B * args.steps / (ms / 1e3), "unit": "transforms/s",
+                                "ms_per_step": ms / args.steps}
+        # plan only
+        ms = timed(lambda i: pkg.Plan(xs[i % nsteps], prec=pkg.FP32).close(), args.steps, 3)
+        result["plan_only_ms"] = ms / args.steps
+        # all-FP64 path, same workload shape (complex128 data), tol 1e-10
+        f64 = f.to(torch.complex128)
+        A64 = A.to(torch.complex128)
+        S64 = torch.empty_like(f64)
+        a64 = torch.empty_like(A64)
+        k64 = max(3, args.steps // 4)
+        ms = timed(lambda i: step(i, pkg.FP64, f64, A64, S64, a64), k64, 3)
+        result["fp64_path"] = {"value": 2 * B * k64 / (ms / 1e3), "unit": "transforms/s",
+                               "ms_per_step": ms / k64, "tol": 1e-10}
+        del f64, A64, S64, a64
+        # self-consistency of the timed path: c -> fwd2 -> inv5 -> c
+        plan32 = pkg.Plan(xs[0], prec=pkg.FP32)
+        c = torch.from_numpy(synth.cn01((4, N), seed=99)).to(torch.complex64).to(dev)
+        c2 = plan32.inv5(plan32.fwd2(c))
+        result["roundtrip_rel_l2"] = float((torch.linalg.vector_norm(c2 - c) / torch.linalg.vector_norm(c)).item())
+        plan32.close()
+
+        # ---- end to end through the C ABI with host (pinned) buffers -----
+        xh = [x.cpu().pin_memory() for x in xs[:args.steps + 3]]
+        fh = f.cpu().pin_memory()
+        Ah = A.cpu().pin_memory()
+        Sh = torch.empty_like(fh).pin_memory()
+        ah = torch.empty_like(Ah).pin_memory()
+
+        def e2e_step(i):
+            p = pkg.Plan(xh[i], prec=pkg.FP32)
+            p.inv5(fh, out=Sh)
+            p.inv4(Ah, out=ah)
+            p.close()
+        for i in range(3):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_step(3 + i)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        h2d = N * 8 + 2 * B * N * 8
+        d2h = 2 * B * N * 8
+        result["e2e"] = {"value": 2 * B * args.steps * ws / e2e_s, "unit": "transforms/s",
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                         "how": "nufft_plan/nufft_inv5/nufft_inv4 given pinned host buffers; the library copies "
+                                "in and out on the stream; wall clock over the steps"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nufft45", choices=["nufft45", "reference"])
+    ap.add_argument("--N", type=int, default=65536)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--quick", action="store_true", help="main timed region only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

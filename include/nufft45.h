@@ -108,8 +108,10 @@ nufft_status nufft_fwd1(nufft_plan_t plan, const void* a, void* A, int64_t batch
  */
 nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream);
 
-/* nufft_destroy -- release a plan (NULL is accepted).  Waits for work queued
- * on the plan's creation stream that uses its buffers. */
+/* nufft_destroy -- release a plan (NULL is accepted).  Its device memory is
+ * returned in stream order on the plan's creation stream, so work already
+ * queued there completes first; work queued on other streams must be
+ * complete (or ordered before that stream) when the plan is destroyed. */
 nufft_status nufft_destroy(nufft_plan_t plan);
 
 /* Parameters a plan chose (Sec. V).  rho = e^{-2 pi a}; gamma = rho^{-N}. */
@@ -143,6 +145,28 @@ nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_st
  * factors, FFT twiddles) kept per (N, precision, tolerance).  Plans that are
  * alive keep their own reference. */
 nufft_status nufft_cache_clear(void);
+
+/*
+ * Tracing (no counterpart in the paper; for measurement).  Every kernel the
+ * library launches is counted.  While tracing is enabled, each launch is
+ * bracketed by CUDA events recorded on its own stream and attributed to a
+ * kernel class ("fft_pass", "spread", "interp", "select", "place",
+ * "pointwise", "geometry", "plan_table", "plan_stage", "bluestein") together
+ * with its algorithmic byte count (the bytes the kernel must read and write
+ * once).  nufft_profile_enable(1) clears earlier records.
+ * nufft_profile_read synchronises the recorded events and returns one entry
+ * per class that launched, at most `cap`, in `out`.
+ */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;        /* summed event time of the launches */
+    double bytes;     /* summed algorithmic bytes */
+} nufft_profile_entry_t;
+
+nufft_status nufft_profile_enable(int on);
+nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count);
+int64_t nufft_launch_count(void);
 
 const char* nufft_status_string(nufft_status st);
 const char* nufft_last_error_message(void);

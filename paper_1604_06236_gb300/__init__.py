@@ -13,7 +13,7 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "build", "library_path"]
+__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
@@ -52,6 +52,11 @@ class PlanInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
 def lib():
     """Load libnufft45.so (raises if it has not been built)."""
     global _lib
@@ -67,6 +72,12 @@ def lib():
         L.nufft_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.nufft_plan_export.argtypes = [vp, i32, vp, vp]
         L.nufft_cache_clear.argtypes = []
+        L.nufft_profile_enable.argtypes = [i32]
+        L.nufft_profile_enable.restype = i32
+        L.nufft_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
+        L.nufft_profile_read.restype = i32
+        L.nufft_launch_count.argtypes = []
+        L.nufft_launch_count.restype = i64
         L.nufft_status_string.argtypes = [i32]
         L.nufft_status_string.restype = ctypes.c_char_p
         L.nufft_last_error_message.argtypes = []

@@ -351,7 +351,10 @@ nufft_status exec_passes(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batc
         const size_t smem = 2 * (size_t)a.C * a.PR * sizeof(c2<T>);
         const int64_t blocks = (a.total + a.C - 1) / a.C;
         NUFFT_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_fft_pass<T><<<(unsigned)blocks, kThreads, smem, s>>>(src, dst, a, lo, hi, dir);
+        {
+            Launch L(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>));
+            k_fft_pass<T><<<(unsigned)blocks, kThreads, smem, s>>>(src, dst, a, lo, hi, dir);
+        }
         NUFFT_CUDA_TRY(cudaGetLastError());
         src = dst;
         dst = (dst == buf) ? work : buf;
@@ -404,6 +407,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_fwd, es * m));
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_inv, es * m));
         const int tb = 256;
+        Launch Lc(s, K_PLAN_TABLE, 48.0 * m);
         k_blue_chirp<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
             n, m, prec == 2 ? (double2*)p.chirp : nullptr, prec == 2 ? nullptr : (float2*)p.chirp, hf, hi);
         NUFFT_CUDA_TRY(cudaGetLastError());
@@ -417,6 +421,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
             st = fft_exec<double>(p64, h, work, 1, -1, s, &res);
             if (st != NUFFT_OK) return st;
             void* dst = which == 0 ? p.chirp_hat_fwd : p.chirp_hat_inv;
+            Launch Ls(s, K_PLAN_TABLE, 32.0 * m);
             k_scale_c128_to<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
                 res, m, 1.0 / (double)m, prec == 2 ? (double2*)dst : nullptr, prec == 2 ? nullptr : (float2*)dst);
             NUFFT_CUDA_TRY(cudaGetLastError());
@@ -437,6 +442,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     NUFFT_CUDA_TRY(cudaMalloc(&p.tw_lo, es * B));
     NUFFT_CUDA_TRY(cudaMalloc(&p.tw_hi, es * nhi));
     const int64_t cnt = std::max(B, nhi);
+    Launch Lt(s, K_PLAN_TABLE, 16.0 * (B + nhi));
     k_make_twiddles<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
         n, B, nhi, prec == 2 ? (double2*)p.tw_lo : nullptr, prec == 2 ? (double2*)p.tw_hi : nullptr,
         prec == 2 ? nullptr : (float2*)p.tw_lo, prec == 2 ? nullptr : (float2*)p.tw_hi);
@@ -454,18 +460,21 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
     c2<T>* aw = work + m * batch;
     const c2<T>* chirp = static_cast<const c2<T>*>(p.chirp);
     const int tb = 256;
-    k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a);
+    { Launch L(s, K_BLUESTEIN, (double)batch * (n + m) * sizeof(c2<T>) + n * sizeof(c2<T>));
+    k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r = nullptr;
     nufft_status st = exec_passes<T>(*p.sub, a, aw, batch, -1, s, &r);
     if (st != NUFFT_OK) return st;
     const c2<T>* h = static_cast<const c2<T>*>(dir < 0 ? p.chirp_hat_fwd : p.chirp_hat_inv);
-    k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch);
+    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * m * sizeof(c2<T>));
+      k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r2 = nullptr;
     st = exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
     if (st != NUFFT_OK) return st;
-    k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf);
+    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * n * sizeof(c2<T>));
+      k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     *result = buf;
     return NUFFT_OK;

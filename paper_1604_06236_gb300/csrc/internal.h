@@ -14,6 +14,24 @@ namespace nufft45 {
 nufft_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line);
 nufft_status fail(nufft_status st, const char* fmt, ...);
 
+// ------------------------------------------------------------- tracing ----
+// Construct around every kernel launch: counts launches and, when tracing is
+// on, records events on the launch stream before and after the launch and
+// attributes them (and `bytes`, the algorithmic traffic) to a kernel class.
+enum KernelKind { K_FFT = 0, K_SPREAD, K_INTERP, K_SELECT, K_PLACE, K_POINTWISE, K_GEOMETRY, K_PLAN_TABLE,
+                  K_PLAN_STAGE, K_BLUESTEIN, K_COUNT };
+const char* kind_name(int k);
+class Launch {
+  public:
+    Launch(cudaStream_t s, int kind, double bytes);
+    ~Launch();
+  private:
+    cudaStream_t s_;
+    int kind_;
+    double bytes_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // ---------------------------------------------------------------- FFT ------
 // One Stockham autosort pass of composite radix R: for every j < n/R the R
 // inputs x[j + k n/R] are twiddled by W_{Ns R}^{(j mod Ns) k}, transformed by a

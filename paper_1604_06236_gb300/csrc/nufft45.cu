@@ -558,8 +558,9 @@ nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch
 
 nufft_status nufft_destroy(nufft_plan_t plan) {
     if (!plan) return NUFFT_OK;
+    // stream-ordered release: work already queued on the plan's stream keeps
+    // its buffers; kernels hold no reference to the host-side object
     plan->mem.release();
-    cudaStreamSynchronize(plan->stream);
     delete plan;
     return NUFFT_OK;
 }

@@ -173,35 +173,42 @@ void gauss_legendre_half(int nq, GLRule& r) {
 
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s) {
+    Launch L(s, K_PLAN_TABLE, M * (out_d ? 8.0 : 4.0));
     k_table<<<nblk(M), kTB, 0, s>>>(ks.w, ks.beta, gl, n, K0, M, log_rho, mode, P, out_d, out_f);
 }
 
 void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
                 double2* out, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, cap * 28.0);
     k_mod<<<nblk(cap), kTB, 0, s>>>(T, perm, cap, count_dev, K0, sign, out);
 }
 
 void launch_fold(const double2* B, int64_t nR, int64_t K0R, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, (double)eta * P * 24.0 + P * 16.0);
     k_fold<<<nblk(P), kTB, 0, s>>>(B, nR, K0R, fac, P, eta, Y);
 }
 
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
                            cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, P * (Kf ? 40.0 : 32.0));
     k_kernel_samples<<<nblk(P), kTB, 0, s>>>(v, P, sumT, K, Kf);
 }
 
 void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, P * 40.0);
     k_lcoef<<<nblk(P), kTB, 0, s>>>(F, P, rhoP, rho_neg, d);
 }
 
 void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, N * 40.0);
     k_weights<<<nblk(N), kTB, 0, s>>>(T, D, N, rhoP, w);
 }
 
 template <typename TS>
 void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
                          const double2* w_user, c2<TS>* mod_out, c2<TS>* wmod_out, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, cap * (28.0 + 4.0 * sizeof(TS)));
     k_slot_weights<TS><<<nblk(cap), kTB, 0, s>>>(T, perm, cap, count_dev, K0, sign, w_user, mod_out, wmod_out);
 }
 template void launch_slot_weights<float>(const uint64_t*, const int*, int64_t, const int*, uint64_t, int,

@@ -1,0 +1,94 @@
+// Kernel-level tracing: every launch of the library is counted; when
+// enabled, each launch is bracketed by CUDA events on its own stream and
+// attributed to a kernel class with its algorithmic byte count.
+#include "internal.h"
+
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+namespace nufft45 {
+
+namespace {
+struct Rec { int kind; cudaEvent_t a, b; double bytes; };
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_free;
+std::atomic<long long> g_launches{0};
+
+cudaEvent_t get_event() {
+    if (!g_free.empty()) { cudaEvent_t e = g_free.back(); g_free.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+const char* kind_name(int k) {
+    static const char* names[] = {"fft_pass", "spread", "interp", "select", "place", "pointwise",
+                                  "geometry", "plan_table", "plan_stage", "bluestein"};
+    return (k >= 0 && k < K_COUNT) ? names[k] : "unknown";
+}
+
+Launch::Launch(cudaStream_t s, int kind, double bytes) : s_(s), kind_(kind), bytes_(bytes) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_on) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        a_ = get_event();
+        b_ = get_event();
+        cudaEventRecord(a_, s_);
+    }
+}
+
+Launch::~Launch() {
+    if (a_) {
+        cudaEventRecord(b_, s_);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_recs.push_back(Rec{kind_, a_, b_, bytes_});
+    }
+}
+
+}  // namespace nufft45
+
+using namespace nufft45;
+
+extern "C" {
+
+nufft_status nufft_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (on) {
+        for (auto& r : g_recs) { g_free.push_back(r.a); g_free.push_back(r.b); }
+        g_recs.clear();
+    }
+    g_on = on != 0;
+    return NUFFT_OK;
+}
+
+int64_t nufft_launch_count(void) { return (int64_t)g_launches.load(); }
+
+nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count) {
+    if (!out || !count || cap < 0) return fail(NUFFT_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(g_mu);
+    nufft_profile_entry_t acc[K_COUNT];
+    std::memset(acc, 0, sizeof(acc));
+    for (int k = 0; k < K_COUNT; ++k) std::strncpy(acc[k].name, kind_name(k), sizeof(acc[k].name) - 1);
+    for (auto& r : g_recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime", __FILE__, __LINE__);
+        acc[r.kind].launches += 1;
+        acc[r.kind].ms += ms;
+        acc[r.kind].bytes += r.bytes;
+    }
+    int n = 0;
+    for (int k = 0; k < K_COUNT && n < cap; ++k)
+        if (acc[k].launches > 0) out[n++] = acc[k];
+    *count = n;
+    return NUFFT_OK;
+}
+
+}  // extern "C"

@@ -344,12 +344,14 @@ __global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* 
 }  // namespace
 
 void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s) {
+    Launch L(s, K_GEOMETRY, 16.0 * N);
     k_canon<<<nblk(N), kTB, 0, s>>>(x, N, T);
 }
 
 void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     const int blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + kTB - 1) / kTB));
+    Launch L(s, K_GEOMETRY, 8.0 * N);
     k_sum_turns<<<blocks, kTB, 0, s>>>(T, N, out);
 }
 
@@ -371,18 +373,20 @@ nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n
     const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
     NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
     NUFFT_CUDA_TRY(cudaMemsetAsync(g.dup_flag, 0, sizeof(int), s));
-    k_cells<<<nblk(N), kTB, 0, s>>>(T, N, (uint64_t)n, cell, frac, count);
-    k_scan_blocks<<<(unsigned)nb, kScanTB, 0, s>>>(count, n + 1, start, sums);
-    k_scan_sums<<<1, kScanTB, 0, s>>>(sums, nb, sums + nb);
-    k_scan_add<<<nblk(n + 1), kTB, 0, s>>>(start, n + 1, sums);
+    { Launch L(s, K_GEOMETRY, 24.0 * N); k_cells<<<nblk(N), kTB, 0, s>>>(T, N, (uint64_t)n, cell, frac, count); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); k_scan_blocks<<<(unsigned)nb, kScanTB, 0, s>>>(count, n + 1, start, sums); }
+    { Launch L(s, K_GEOMETRY, 8.0 * nb); k_scan_sums<<<1, kScanTB, 0, s>>>(sums, nb, sums + nb); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); k_scan_add<<<nblk(n + 1), kTB, 0, s>>>(start, n + 1, sums); }
     NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
-    k_scatter<<<nblk(N), kTB, 0, s>>>(cell, N, start, count, g.srt_perm);
-    k_order_cells<<<nblk(n), kTB, 0, s>>>(start, n, T, g.srt_perm);
+    { Launch L(s, K_GEOMETRY, 16.0 * N); k_scatter<<<nblk(N), kTB, 0, s>>>(cell, N, start, count, g.srt_perm); }
+    { Launch L(s, K_GEOMETRY, 4.0 * n + 16.0 * N); k_order_cells<<<nblk(n), kTB, 0, s>>>(start, n, T, g.srt_perm); }
+    { Launch L(s, K_GEOMETRY, 44.0 * N);
     k_sorted_fill<<<nblk(N), kTB, 0, s>>>(g.srt_perm, cell, frac, T, N, g.srt_cell, g.srt_frac,
-                                          want_float ? g.srt_fracf : nullptr, g.dup_flag);
+                                          want_float ? g.srt_fracf : nullptr, g.dup_flag); }
+    { Launch L(s, K_GEOMETRY, 40.0 * N);
     k_ext_fill<<<nblk(2 * N), kTB, 0, s>>>(start, n, w / 2, N, g.srt_perm, g.srt_cell, g.srt_frac, g.ext_perm,
-                                           g.ext_cell, g.ext_frac, want_float ? g.ext_fracf : nullptr);
-    k_cstart<<<nblk(n + w + 1), kTB, 0, s>>>(start, n, w, N, g.cstart);
+                                           g.ext_cell, g.ext_frac, want_float ? g.ext_fracf : nullptr); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); k_cstart<<<nblk(n + w + 1), kTB, 0, s>>>(start, n, w, N, g.cstart); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
@@ -392,6 +396,9 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
                    c2<T>* grid, int64_t batch, cudaStream_t s) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* ef = FracPtr<T>::ext(g);
+    const double es = sizeof(c2<T>);
+    Launch L(s, K_SPREAD, (src ? batch * g.N * es : 0.0) + g.N * (es + 8.0 + sizeof(T)) + 4.0 * (g.n + g.w) +
+                              batch * g.n * es);
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
         k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
@@ -412,6 +419,8 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
                    int64_t dst_bs, int64_t batch, cudaStream_t s) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* sf = FracPtr<T>::srt(g);
+    const double es = sizeof(c2<T>);
+    Launch L(s, K_INTERP, batch * g.n * es + g.N * (8.0 + sizeof(T) + es) + batch * g.N * es);
     if (batch == 1) {
         dim3 gr(nblk(g.N), 1);
         k_interp<T, 1><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
@@ -426,18 +435,22 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
 template <typename T>
 void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0, const T* fac,
                    int64_t batch, cudaStream_t s) {
+    Launch L(s, K_SELECT, 2.0 * batch * P * sizeof(c2<T>) + P * sizeof(T));
     k_select<T><<<nblk(P * batch), kTB, 0, s>>>(in, n, out, out_bs, P, K0, fac, batch);
 }
 
 template <typename T>
 void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out, int64_t n,
                   int64_t batch, cudaStream_t s) {
+    Launch L(s, K_PLACE, batch * (P + n) * sizeof(c2<T>) + P * sizeof(T));
     k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch);
 }
 
 template <typename T>
 void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P, const c2<T>* mulc,
                       const T* fac, int64_t batch, cudaStream_t s) {
+    Launch L(s, K_POINTWISE, 2.0 * batch * P * sizeof(c2<T>) + (mulc ? P * sizeof(c2<T>) : 0) +
+                                 (fac ? P * sizeof(T) : 0));
     k_pointwise<T><<<nblk(P * batch), kTB, 0, s>>>(in, in_bs, out, out_bs, P, mulc, fac, batch);
 }
 

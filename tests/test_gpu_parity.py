@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Tolerances (relative L2, the paper's error measure of Sec. VI):
+  * float64 path: 1e-10 for the inverses (types 4, 5), 1e-12 for types 1, 2;
+  * float32 path: 1e-5 for the inverses, 1e-6 for types 1, 2 (the float32
+    rounding of the data is ~6e-8; spreading width 8 leaves ~4e-7);
+  * plan quantities K_q, L'(z_p), w_p are always float64: 1e-10 for the
+    float64 plan (gamma = 1000, eta = 4), 1e-7 for the float32 path's plan
+    (gamma = 30, eta = 5: truncation ~0.4 gamma^-eta ~ 2e-8, Sec. V).
+Sizes span one to many CTA tiles and FFT passes, ragged tails, prime and
+non-smooth N (Bluestein), and the N = 65536 workload in full.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1604_06236_gb300 as pkg  # noqa: E402
+
+FP32, FP64 = pkg.FP32, pkg.FP64
+TOL_INV = {FP32: 1e-5, FP64: 1e-10}
+TOL_FWD = {FP32: 1e-6, FP64: 1e-12}
+TOL_PLAN = {FP32: 1e-7, FP64: 1e-10}
+CDT = {FP32: torch.complex64, FP64: torch.complex128}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg.build()
+    oracle.build()
+    pkg.lib()
+
+
+def _dev(a, prec):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(CDT[prec]).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def _rounded(a, prec):
+    """The input as the GPU sees it (complex64 rounding for FP32), in float64."""
+    return a.astype(np.complex64).astype(np.complex128) if prec == FP32 else a
+
+
+SIZES = [1, 2, 3, 17, 64, 255, 256, 1000, 1009, 4096]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("N", SIZES)
+def test_plan_quantities(N, prec):
+    x = synth.jittered_nodes(N, 0.45, seed=N)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    rho = plan.info()["rho"]
+    K = _np(plan.export(0))
+    D = _np(plan.export(1))
+    w = _np(plan.export(2))
+    assert oracle.rel_l2(K, oracle.kernel_samples(x, rho)) <= TOL_PLAN[prec]
+    Do = oracle.deriv_samples(x)
+    assert oracle.rel_l2(D, Do) <= TOL_PLAN[prec]
+    assert oracle.rel_l2(w, oracle.weights(x, rho, Do)) <= TOL_PLAN[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("N", SIZES)
+def test_forward_transforms(N, prec):
+    x = synth.jittered_nodes(N, 0.45, seed=N + 7)
+    c = synth.cn01(N, seed=N + 8)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    cr = _rounded(c, prec)
+    assert oracle.rel_l2(_np(plan.fwd2(_dev(c, prec))), oracle.type2(x, cr)) <= TOL_FWD[prec]
+    assert oracle.rel_l2(_np(plan.fwd1(_dev(c, prec))), oracle.type1(x, cr)) <= TOL_FWD[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("N", SIZES)
+def test_inverses_vs_lu(N, prec):
+    """Element-by-element against Gaussian elimination on random data."""
+    x = synth.jittered_nodes(N, 0.45, seed=N + 11)
+    s = synth.cn01(N, seed=N + 12)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    sr = _rounded(s, prec)
+    S_ref = oracle.inv5(x, sr)
+    a_ref = oracle.inv4(x, sr)
+    assert oracle.rel_l2(_np(plan.inv5(_dev(s, prec))), S_ref) <= TOL_INV[prec]
+    assert oracle.rel_l2(_np(plan.inv4(_dev(s, prec))), a_ref) <= TOL_INV[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_cfg_n256_known_truth(prec):
+    """N = 256, u ~ U(-0.3, 0.3), seed 0: c -> type-2 -> inv5 -> c and
+    c -> type-1 -> inv4 -> c (exact-phase oracle sums make the inputs)."""
+    N = 256
+    g = synth.rng(0)
+    x = synth.jittered_nodes(N, 0.3, generator=g)
+    c = synth.cn01(N, generator=g)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    f = oracle.type2(x, c)
+    A = oracle.type1(x, c)
+    assert oracle.rel_l2(_np(plan.inv5(_dev(f, prec))), c) <= TOL_INV[prec]
+    assert oracle.rel_l2(_np(plan.inv4(_dev(A, prec))), c) <= TOL_INV[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_equispaced_is_dft(prec):
+    N = 512
+    x = synth.equispaced_nodes(N)
+    s = synth.cn01(N, seed=3)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    sr = _rounded(s, prec)
+    assert oracle.rel_l2(_np(plan.inv5(_dev(s, prec))), np.fft.fft(sr) / N) <= TOL_INV[prec]
+    assert oracle.rel_l2(_np(plan.inv4(_dev(s, prec))), np.fft.ifft(sr)) <= TOL_INV[prec]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_batch_matches_single(prec):
+    N = 3000
+    x = synth.jittered_nodes(N, 0.4, seed=5)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    data = synth.cn01((5, N), seed=6)
+    for op in ("inv5", "inv4", "fwd1", "fwd2"):
+        fn = getattr(plan, op)
+        batched = _np(fn(_dev(data, prec)))
+        for b in range(5):
+            single = _np(fn(_dev(data[b], prec)))
+            np.testing.assert_array_equal(batched[b], single)
+
+
+def test_node_order_is_free():
+    """Permuting the nodes permutes the samples (inv5 input, inv4 output)."""
+    N = 777
+    x = synth.jittered_nodes(N, 0.45, seed=9)
+    perm = synth.rng(10).permutation(N)
+    s = synth.cn01(N, seed=11)
+    p1 = pkg.Plan(torch.from_numpy(x).cuda(), prec=FP64)
+    p2 = pkg.Plan(torch.from_numpy(x[perm]).cuda(), prec=FP64)
+    S1 = _np(p1.inv5(_dev(s, FP64)))
+    S2 = _np(p2.inv5(_dev(s[perm], FP64)))
+    assert oracle.rel_l2(S2, S1) < 1e-12
+    a1 = _np(p1.inv4(_dev(s, FP64)))
+    a2 = _np(p2.inv4(_dev(s, FP64)))
+    assert oracle.rel_l2(a2, a1[perm]) < 1e-12
+
+
+def test_nodes_outside_one_period_wrap():
+    N = 300
+    x = synth.jittered_nodes(N, 0.45, seed=12)
+    shift = 2 * np.pi * synth.rng(13).integers(-3, 4, size=N)
+    s = synth.cn01(N, seed=14)
+    p1 = pkg.Plan(torch.from_numpy(x).cuda(), prec=FP64)
+    p2 = pkg.Plan(torch.from_numpy(x + shift).cuda(), prec=FP64)
+    assert oracle.rel_l2(_np(p2.inv5(_dev(s, FP64))), _np(p1.inv5(_dev(s, FP64)))) < 1e-9
+
+
+def test_duplicate_nodes_rejected():
+    N = 100
+    x = synth.jittered_nodes(N, 0.45, seed=15)
+    x[40] = x[41] + 2 * np.pi   # the same node modulo 2 pi
+    with pytest.raises(pkg.NufftError) as e:
+        pkg.Plan(torch.from_numpy(x).cuda(), prec=FP64)
+    assert e.value.status == "NUFFT_ERR_DUP_NODES"
+
+
+def test_host_buffers_match_device():
+    N = 2048
+    x = synth.jittered_nodes(N, 0.45, seed=16)
+    f = synth.cn01((3, N), seed=17)
+    plan_d = pkg.Plan(torch.from_numpy(x).cuda(), prec=FP32)
+    plan_h = pkg.Plan(torch.from_numpy(x), prec=FP32)          # host nodes
+    dev = _np(plan_d.inv5(_dev(f, FP32)))
+    host_in = torch.from_numpy(f).to(torch.complex64).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    plan_h.inv5(host_in, out=host_out)
+    np.testing.assert_array_equal(host_out.numpy().astype(np.complex128), dev)
+    pageable = torch.from_numpy(f).to(torch.complex64)
+    np.testing.assert_array_equal(_np(plan_h.inv5(pageable)), dev)
+
+
+def test_zero_batch_and_overlap():
+    N = 64
+    plan = pkg.Plan(torch.from_numpy(synth.jittered_nodes(N, 0.3, seed=1)).cuda(), prec=FP32)
+    buf = torch.zeros(2, N, dtype=torch.complex64, device="cuda")
+    L = pkg.lib()
+    st = L.nufft_inv5(plan._h, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(buf.data_ptr()), 0, None)
+    assert st == 0
+    st = L.nufft_inv5(plan._h, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(buf[1].data_ptr()), 2, None)
+    assert st == 1   # overlapping input and output
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_n65536_known_truth(prec):
+    """The N = 65536 workload: u ~ U(-0.45, 0.45), CN(0,1) coefficients, type-5
+    and type-4 inputs from exact-phase oracle sums; full-vector comparison."""
+    N = 65536
+    g = synth.rng(1)
+    x = synth.jittered_nodes(N, 0.45, generator=g)
+    c = synth.cn01(N, generator=g)
+    f = oracle.type2(x, c)
+    A = oracle.type1(x, c)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    assert oracle.rel_l2(_np(plan.inv5(_dev(f, prec))), c) <= TOL_INV[prec]
+    assert oracle.rel_l2(_np(plan.inv4(_dev(A, prec))), c) <= TOL_INV[prec]
+    # batched right-hand sides as timed by the benchmark
+    fb = np.stack([f, 1j * f, -f, 0.5 * f])
+    Sb = _np(plan.inv5(_dev(fb, prec)))
+    for b, sc in enumerate([1, 1j, -1, 0.5]):
+        assert oracle.rel_l2(Sb[b], sc * c) <= TOL_INV[prec]
