@@ -10,6 +10,7 @@
 // the transform in natural order.  Lengths with a larger prime factor use
 // Bluestein's chirp-z convolution on a smooth length m >= 2n - 1.
 #include "internal.h"
+#include "fft_p2.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -301,9 +302,120 @@ std::vector<int> sub_radices(int64_t R) {
     return s;
 }
 
+// ---- power-of-two passes ----------------------------------------------------
+template <typename T> struct P2Limits;
+template <> struct P2Limits<float> { static constexpr int kElems = 4096; static constexpr int kRlogMax = 10; };
+template <> struct P2Limits<double> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 8; };
+
+inline int r1_log_of(int rlog) { return (rlog + 1) / 2; }   // R1 >= R2, R1 <= 2 R2
+
+template <typename T>
+int p2_C_log(int rlog) {
+    const int r2log = rlog - r1_log_of(rlog);
+    int c = P2Limits<T>::kElems >> rlog;
+    c = std::min(c, 256 >> r2log);
+    int cl = 0;
+    while ((1 << (cl + 1)) <= c) ++cl;
+    return cl;
+}
+
+// split n = 2^L into passes of radix 2^r (r <= kRlogMax), balanced; every
+// pass of a multi-pass plan must own whole columns (C <= n/R)
+template <typename T>
+bool plan_p2(int L, std::vector<int>& rl) {
+    if (L < 1) return false;
+    const int rmax = P2Limits<T>::kRlogMax;
+    const int k = (L + rmax - 1) / rmax;
+    rl.assign(k, L / k);
+    for (int i = 0; i < L % k; ++i) rl[i] += 1;
+    if (k > 1)
+        for (int r : rl)
+            if (p2_C_log<T>(r) > L - r) return false;
+    return true;
+}
+
+template <typename T>
+nufft_status launch_p2(int rlog, const c2<T>* in, c2<T>* out, p2::Args a, const c2<T>* lo, const c2<T>* hi, int dir,
+                       cudaStream_t s) {
+    const int r1 = 1 << r1_log_of(rlog), r2 = 1 << (rlog - r1_log_of(rlog));
+    const int C = 1 << a.C_log;
+    const int PR = r1 * (r2 + 1) + 1;
+    const size_t smem = (size_t)C * PR * sizeof(c2<T>);
+    const unsigned blocks = (unsigned)((a.total + C - 1) / C);
+    const unsigned threads = (unsigned)(C * r2);
+#define P2_CASE(RL, A, B)                                                                                   \
+    case RL: {                                                                                              \
+        auto kern = p2::k_fft_p2<T, A, B>;                                                                  \
+        NUFFT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        kern<<<blocks, threads, smem, s>>>(in, out, a, lo, hi, dir);                                        \
+        break;                                                                                              \
+    }
+    switch (rlog) {
+        P2_CASE(1, 2, 1)
+        P2_CASE(2, 2, 2)
+        P2_CASE(3, 4, 2)
+        P2_CASE(4, 4, 4)
+        P2_CASE(5, 8, 4)
+        P2_CASE(6, 8, 8)
+        P2_CASE(7, 16, 8)
+        P2_CASE(8, 16, 16)
+        default:
+            if constexpr (sizeof(T) == 4) {
+                switch (rlog) {
+                    P2_CASE(9, 32, 16)
+                    P2_CASE(10, 32, 32)
+                    default: return fail(NUFFT_ERR_ARG, "no power-of-two pass for radix 2^%d", rlog);
+                }
+            } else {
+                return fail(NUFFT_ERR_ARG, "no power-of-two pass for radix 2^%d", rlog);
+            }
+    }
+#undef P2_CASE
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template <typename T>
+nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
+                     c2<T>** result) {
+    const c2<T>* lo = static_cast<const c2<T>*>(p.tw_lo);
+    const c2<T>* hi = static_cast<const c2<T>*>(p.tw_hi);
+    int L = 0;
+    while (((int64_t)1 << L) < p.n) ++L;
+    c2<T>* src = buf;
+    c2<T>* dst = (p.p2_rlog.size() == 1) ? buf : work;
+    int ns_log = 0;
+    for (size_t i = 0; i < p.p2_rlog.size(); ++i) {
+        const int rl = p.p2_rlog[i];
+        p2::Args a;
+        a.n_log = L;
+        a.R_log = rl;
+        a.Ns_log = ns_log;
+        a.C_log = p2_C_log<T>(rl);
+        a.total = (int)(batch << (L - rl));
+        a.shift = p.shift;
+        {
+            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>));
+            nufft_status st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            if (st != NUFFT_OK) return st;
+        }
+        ns_log += rl;
+        src = dst;
+        dst = (dst == buf) ? work : buf;
+    }
+    *result = src;
+    return NUFFT_OK;
+}
+
 template <typename T>
 nufft_status make_passes(FFTPlan& p) {
     const int64_t n = p.n;
+    if (n >= 2 && (n & (n - 1)) == 0 && n <= ((int64_t)1 << 30)) {
+        int L = 0;
+        while (((int64_t)1 << L) < n) ++L;
+        if (plan_p2<T>(L, p.p2_rlog)) return NUFFT_OK;
+        p.p2_rlog.clear();
+    }
     std::vector<int> f = factor_small(n);
     std::vector<int64_t> radices;
     if (n <= FftLimits<T>::kElems) {
@@ -454,6 +566,7 @@ template <typename T>
 nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
                       c2<T>** result) {
     if (batch <= 0) { *result = buf; return NUFFT_OK; }
+    if (!p.p2_rlog.empty()) return exec_p2<T>(p, buf, work, batch, dir, s, result);
     if (!p.bluestein) return exec_passes<T>(p, buf, work, batch, dir, s, result);
     const int64_t n = p.n, m = p.m;
     c2<T>* a = work;
@@ -464,14 +577,16 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
     k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r = nullptr;
-    nufft_status st = exec_passes<T>(*p.sub, a, aw, batch, -1, s, &r);
+    nufft_status st = p.sub->p2_rlog.empty() ? exec_passes<T>(*p.sub, a, aw, batch, -1, s, &r)
+                                                : exec_p2<T>(*p.sub, a, aw, batch, -1, s, &r);
     if (st != NUFFT_OK) return st;
     const c2<T>* h = static_cast<const c2<T>*>(dir < 0 ? p.chirp_hat_fwd : p.chirp_hat_inv);
     { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * m * sizeof(c2<T>));
       k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r2 = nullptr;
-    st = exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
+    st = p.sub->p2_rlog.empty() ? exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2)
+                                : exec_p2<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
     if (st != NUFFT_OK) return st;
     { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * n * sizeof(c2<T>));
       k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf); }

@@ -50,6 +50,7 @@ struct FFTPlan {
     int64_t n = 0;
     int prec = 0;                       // 1 = float, 2 = double
     std::vector<FFTPass> passes;
+    std::vector<int> p2_rlog;           // power-of-two plan: log2 radix of each pass
     // two-level table of W_n^e = e^{-j 2 pi e / n}: lo[e & (B-1)] * hi[e >> shift]
     int shift = 0;
     void* tw_lo = nullptr;

@@ -609,6 +609,29 @@ const char* nufft_status_string(nufft_status st) {
 
 const char* nufft_last_error_message(void) { return g_msg; }
 
+// Test hook (not part of the public header): run the library's FFT of length
+// n on `batch` contiguous device vectors in place (prec 1: complex64, 2:
+// complex128; dir -1 forward, +1 inverse, unnormalised).  Synchronises.
+nufft_status nufft_debug_fft(int64_t n, int prec, int dir, int64_t batch, void* buf, nufft_stream_t stream) {
+    if (n < 1 || batch < 1 || !buf || (prec != 1 && prec != 2) || (dir != 1 && dir != -1))
+        return fail(NUFFT_ERR_ARG, "bad FFT test arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    FFTPlan p;
+    nufft_status st = fft_make(p, n, prec, s);
+    if (st != NUFFT_OK) return st;
+    const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+    void* work = nullptr;
+    NUFFT_CUDA_TRY(cudaMalloc(&work, es * (size_t)fft_work_elems(p) * (size_t)batch));
+    void* res = nullptr;
+    if (prec == 2) st = fft_exec<double>(p, (double2*)buf, (double2*)work, batch, dir, s, (double2**)&res);
+    else st = fft_exec<float>(p, (float2*)buf, (float2*)work, batch, dir, s, (float2**)&res);
+    if (st == NUFFT_OK && res != buf)
+        st = cudaMemcpyAsync(buf, res, es * n * batch, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? NUFFT_OK : NUFFT_ERR_CUDA;
+    cudaStreamSynchronize(s);
+    cudaFree(work);
+    return st;
+}
+
 // Test hook (not part of the public header): make the next `count` device
 // allocations fail with NUFFT_ERR_ALLOC, to exercise the error paths without
 // exhausting the device.

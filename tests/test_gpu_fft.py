@@ -1,0 +1,40 @@
+"""The library's FFT (Stockham passes, power-of-two kernels, mixed radix,
+Bluestein) against numpy's FFT, through a test hook of the C library."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1604_06236_gb300 as pkg  # noqa: E402
+
+SIZES = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384, 65536, 131072, 1 << 18,
+         1 << 20, 1 << 21, 3, 5, 6, 7, 12, 100, 1000, 1536, 6000, 40960, 655360, 11, 17, 1009, 4099]
+
+
+def _run(n, prec, dir_, x):
+    L = pkg.lib()
+    L.nufft_debug_fft.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+    dt = torch.complex64 if prec == 1 else torch.complex128
+    buf = torch.from_numpy(x).to(dt).cuda().contiguous()
+    pkg.check(L.nufft_debug_fft(n, prec, dir_, x.shape[0], ctypes.c_void_p(buf.data_ptr()), None))
+    return buf.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n", SIZES)
+def test_fft_matches_numpy(n, prec):
+    batch = 3 if n <= (1 << 18) else 1
+    x = synth.cn01((batch, n), seed=n)
+    xr = x.astype(np.complex64).astype(np.complex128) if prec == 1 else x
+    tol = 2e-6 if prec == 1 else 1e-13
+    for dir_ in (-1, 1):
+        ref = np.fft.fft(xr, axis=1) if dir_ < 0 else np.fft.ifft(xr, axis=1) * n
+        got = _run(n, prec, dir_, x)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < tol * max(1.0, np.log2(max(n, 2)) / 10), (n, prec, dir_, err)
