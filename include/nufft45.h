@@ -68,8 +68,9 @@ typedef enum {
  *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
  * prec   NUFFT_FP32 or NUFFT_FP64.
  * plan   receives the plan; owned by the caller, release with nufft_destroy.
- * The call synchronises `stream` once to check for coincident nodes
- * (NUFFT_ERR_DUP_NODES, no plan is returned).
+ * The call synchronises `stream` once to check for coincident nodes: two
+ * nodes whose turns t differ by less than 2^-44 modulo 1 make the systems of
+ * Eqs. 47/48 numerically singular and return NUFFT_ERR_DUP_NODES (no plan).
  */
 nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream,
                         nufft_plan_t* plan);

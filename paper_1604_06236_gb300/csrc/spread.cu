@@ -148,7 +148,12 @@ __global__ void k_sorted_fill(const int* __restrict__ perm, const int* __restric
     const double f = frac[p];
     sfrac[i] = f;
     if (sfracf) sfracf[i] = (float)f;
-    if (i + 1 < N && T[perm[i + 1]] == T[p]) *dup = 1;
+    // coincident nodes: neighbours in sorted (= cyclic turn) order closer than
+    // 2^-44 turns, including the pair that wraps from the last to the first
+    if (N > 1) {
+        const uint64_t d = T[perm[i + 1 < N ? i + 1 : 0]] - T[p];
+        if (d < (1ull << 20)) *dup = 1;
+    }
 }
 
 // extended list: [nodes of cells n-h..n-1, shifted by -n] [all nodes] [nodes of cells 0..h-1, shifted by +n]
