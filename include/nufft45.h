@@ -87,6 +87,31 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
 nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream);
 
 /*
+ * nufft_inv5_noalloc -- the type-5 inverse of nufft_inv5 without any device
+ *   allocation during the call.  The paper has no counterpart: this is for
+ *   callers that cannot allocate device memory while they transform (real-time
+ *   loops and embedded runtimes that forbid allocation after set-up, or
+ *   processes whose device memory is handed out by an external allocator
+ *   under a fixed budget).  The plan is still made by nufft_plan at set-up.
+ *   Scratch is a fixed 8 MiB array inside the library image, present on
+ *   every GPU that loads the library until the process exits; right-hand
+ *   sides are processed one at a time through it.
+ * Limits.  A plan whose scratch per right-hand side exceeds 8 MiB is rejected
+ *   with NUFFT_ERR_ARG (power-of-two N up to 131072 in NUFFT_FP32 and up to
+ *   65536 in NUFFT_FP64 fit).  f and c must be device buffers (host buffers
+ *   would need staging memory): NUFFT_ERR_ARG otherwise.
+ * Set-up.  The first call on each device resolves the scratch array's
+ *   device address (cudaGetSymbolAddress) with that device current; make
+ *   that first call before any stream capture.
+ * Concurrency.  All calls share the one scratch array.  Nothing in it needs
+ *   to start at zero (every stage overwrites what it reads), but calls whose
+ *   work overlaps on the GPU (other streams, other threads) race on it:
+ *   order them on one stream or serialise them.
+ * Arguments, layout and results as for nufft_inv5.
+ */
+nufft_status nufft_inv5_noalloc(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream);
+
+/*
  * nufft_inv4 -- type-4 NUFFT (Eq. 47): given A(k) = sum_p a_p e^{-j 2 pi k t_p},
  *   k = 0..N-1, return a.  Method of Sec. IV, Fig. 2: Eq. 37 on A, product
  *   with K_q (Eq. 30), Eq. 31, type-2 NUFFT at the nodes, times w_p (Eq. 40).

@@ -638,3 +638,94 @@ nufft_status nufft_debug_fft(int64_t n, int prec, int dir, int64_t batch, void* 
 void nufft_debug_fail_allocs(int count) { g_fail_allocs = count; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free type-5 inverse.
+//
+// nufft_inv5 takes its scratch (the oversampled grid and the FFT work
+// vectors) from the stream-ordered pool on every call.  Some callers cannot
+// allocate device memory when they transform: real-time loops and embedded
+// runtimes that forbid allocation after set-up, code that runs under a
+// device-memory budget enforced by an external allocator, or hosts that only
+// hand out pre-registered buffers.  nufft_inv5_noalloc runs the same kernels
+// one right-hand side at a time on a fixed scratch array that is part of the
+// library image (a file-scope __device__ array, resident on every GPU that
+// loads the library until the process exits).  The plan itself is still made
+// by nufft_plan, at set-up time.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in for the symbol and must never be
+// handed to a kernel.  Resolved once per device, with that device current.
+nufft_status noalloc_scratch(void** out) {
+    int dev = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(NUFFT_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return NUFFT_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+nufft_status inv5_noalloc_impl(nufft_plan_s* pl, const c2<T>* in, c2<T>* out, int64_t batch, char* scratch,
+                               cudaStream_t s) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    char* p = scratch;
+    c2<T>* gA = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * prm.ns);
+    c2<T>* gW = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * fft_work_elems(tab.fft_ns));
+    c2<T>* vA = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * prm.N);
+    c2<T>* vW = reinterpret_cast<c2<T>*>(p);
+    for (int64_t b = 0; b < batch; ++b) {
+        const nufft_status st = run_chunk<T>(pl, OP_INV5, in + b * prm.N, out + b * prm.N, 1, gA, gW, vA, vW, s);
+        if (st != NUFFT_OK) return st;
+    }
+    return NUFFT_OK;
+}
+
+}  // namespace
+
+extern "C" nufft_status nufft_inv5_noalloc(nufft_plan_t plan, const void* f, void* c, int64_t batch,
+                                           nufft_stream_t stream) {
+    if (!plan) return fail(NUFFT_ERR_ARG, "null plan");
+    if (batch < 0) return fail(NUFFT_ERR_ARG, "negative batch");
+    if (batch == 0) return NUFFT_OK;
+    if (!f || !c) return fail(NUFFT_ERR_ARG, "null data pointer");
+    const Params& prm = plan->prm;
+    const Tables& tab = *plan->tab;
+    const size_t es = solve_elem(prm);
+    const size_t need = round256(es * prm.ns) + round256(es * fft_work_elems(tab.fft_ns)) + round256(es * prm.N) +
+                        round256(es * fft_work_elems(tab.fft_P));
+    if (need > kNoAllocScratchBytes)
+        return fail(NUFFT_ERR_ARG,
+                    "nufft_inv5_noalloc: N = %lld needs %zu bytes of scratch per right-hand side, more than the "
+                    "%zu-byte static scratch; use nufft_inv5", (long long)prm.N, need, kNoAllocScratchBytes);
+    const size_t bytes = es * (size_t)prm.N * (size_t)batch;
+    const char* ib = (const char*)f;
+    const char* ob = (const char*)c;
+    if (ib < ob + bytes && ob < ib + bytes) return fail(NUFFT_ERR_ARG, "input and output overlap");
+    if (!is_device_ptr(f) || !is_device_ptr(c))
+        return fail(NUFFT_ERR_ARG, "nufft_inv5_noalloc needs device buffers (host buffers would need staging memory)");
+    void* scratch = nullptr;
+    nufft_status st = noalloc_scratch(&scratch);
+    if (st != NUFFT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prm.prec == NUFFT_FP64)
+        return inv5_noalloc_impl<double>(plan, (const double2*)f, (double2*)c, batch, (char*)scratch, s);
+    return inv5_noalloc_impl<float>(plan, (const float2*)f, (float2*)c, batch, (char*)scratch, s);
+}
