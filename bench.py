@@ -46,23 +46,25 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while timing."""
+    """nvidia-smi samples of SM clock and throttle reasons, time-stamped, so
+    that the samples inside the timed region can be picked out."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.samples = []     # (time, sm, smax, set of reasons)
         self.thread = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
@@ -71,11 +73,19 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [p.strip() for p in line.strip().split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, smax = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            reasons = {nm for nm, v in zip(self.NAMES, parts[5:9]) if v.lower() == "active"}
+            self.samples.append((time.perf_counter(), sm, smax, reasons))
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -83,24 +93,26 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+
+    def summary(self, t0, t1):
+        """Median SM clock and reasons inside [t0, t1]; when the window holds
+        fewer than 3 samples, the nearest samples around it are used and the
+        window is reported."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            mid = 0.5 * (t0 + t1)
+            inside = sorted(self.samples, key=lambda s: abs(s[0] - mid))[:5]
+            window = "timed region shorter than the 100 ms sampling period: %d samples nearest to it" % len(inside)
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set()
+        for s in inside:
+            reasons |= s[3]
+        return {"sm_mhz": float(np.median([s[1] for s in inside])), "sm_max_mhz": max(s[2] for s in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
 # ------------------------------------------------------------ peaks -------
@@ -252,14 +264,15 @@ def run_gpu(args):
         return total
 
     # ---- main timed region (FP32-split path, plan per step) --------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
     L.nufft_profile_enable(1)
     launches0 = L.nufft_launch_count()
     t_wall0 = time.perf_counter()
@@ -279,8 +292,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     launches = L.nufft_launch_count() - launches0
+    t_wall1 = time.perf_counter()
     L.nufft_profile_enable(0)
-    clk = clocks.stop()
     entries = (pkg.ProfileEntry * 16)()
     cnt = ctypes.c_int()
     pkg.check(L.nufft_profile_read(entries, 16, ctypes.byref(cnt)))
@@ -314,7 +327,7 @@ def run_gpu(args):
                    "tol": 1e-5, "plan_per_step": True,
                    "l2": "512 MiB buffer written between timed steps (outside the events)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+        "roofline": roofline, "gpu_launches": launches,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                         "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1)} for k, v in prof.items()},
         "wall_s": wall,
@@ -381,6 +394,9 @@ def run_gpu(args):
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                          "how": "nufft_plan/nufft_inv5/nufft_inv4 given pinned host buffers; the library copies "
                                 "in and out on the stream; wall clock over the steps"}
+    time.sleep(0.3)
+    clocks.stop()
+    result["clocks"] = clocks.summary(t_wall0, t_wall1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = oracle_sample(args.cpu_seconds)
     if rank == 0:

@@ -177,8 +177,9 @@ nufft_status nufft_cache_clear(void);
  * library launches is counted.  While tracing is enabled, each launch is
  * bracketed by CUDA events recorded on its own stream and attributed to a
  * kernel class ("fft_pass", "spread", "interp", "select", "place",
- * "pointwise", "geometry", "plan_table", "plan_stage", "bluestein") together
- * with its algorithmic byte count (the bytes the kernel must read and write
+ * "pointwise", "geometry", "plan_table", "plan_stage", "bluestein"; float64
+ * launches of a class are reported as "<class>_f64") together with its
+ * algorithmic byte count (the bytes the kernel must read and write
  * once).  nufft_profile_enable(1) clears earlier records.
  * nufft_profile_read synchronises the recorded events and returns one entry
  * per class that launched, at most `cap`, in `out`.

@@ -395,7 +395,7 @@ nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, i
         a.total = (int)(batch << (L - rl));
         a.shift = p.shift;
         {
-            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>));
+            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             nufft_status st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
             if (st != NUFFT_OK) return st;
         }
@@ -464,7 +464,7 @@ nufft_status exec_passes(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batc
         const int64_t blocks = (a.total + a.C - 1) / a.C;
         NUFFT_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         {
-            Launch L(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>));
+            Launch L(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             k_fft_pass<T><<<(unsigned)blocks, kThreads, smem, s>>>(src, dst, a, lo, hi, dir);
         }
         NUFFT_CUDA_TRY(cudaGetLastError());
@@ -573,7 +573,7 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
     c2<T>* aw = work + m * batch;
     const c2<T>* chirp = static_cast<const c2<T>*>(p.chirp);
     const int tb = 256;
-    { Launch L(s, K_BLUESTEIN, (double)batch * (n + m) * sizeof(c2<T>) + n * sizeof(c2<T>));
+    { Launch L(s, K_BLUESTEIN, (double)batch * (n + m) * sizeof(c2<T>) + n * sizeof(c2<T>), sizeof(T) == 8);
     k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r = nullptr;
@@ -581,14 +581,14 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
                                                 : exec_p2<T>(*p.sub, a, aw, batch, -1, s, &r);
     if (st != NUFFT_OK) return st;
     const c2<T>* h = static_cast<const c2<T>*>(dir < 0 ? p.chirp_hat_fwd : p.chirp_hat_inv);
-    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * m * sizeof(c2<T>));
+    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * m * sizeof(c2<T>), sizeof(T) == 8);
       k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r2 = nullptr;
     st = p.sub->p2_rlog.empty() ? exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2)
                                 : exec_p2<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
     if (st != NUFFT_OK) return st;
-    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * n * sizeof(c2<T>));
+    { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * n * sizeof(c2<T>), sizeof(T) == 8);
       k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     *result = buf;

@@ -17,13 +17,14 @@ nufft_status fail(nufft_status st, const char* fmt, ...);
 // ------------------------------------------------------------- tracing ----
 // Construct around every kernel launch: counts launches and, when tracing is
 // on, records events on the launch stream before and after the launch and
-// attributes them (and `bytes`, the algorithmic traffic) to a kernel class.
+// attributes them (and `bytes`, the algorithmic traffic) to a kernel class
+// (float64 launches get the class's "_f64" twin).
 enum KernelKind { K_FFT = 0, K_SPREAD, K_INTERP, K_SELECT, K_PLACE, K_POINTWISE, K_GEOMETRY, K_PLAN_TABLE,
                   K_PLAN_STAGE, K_BLUESTEIN, K_COUNT };
 const char* kind_name(int k);
 class Launch {
   public:
-    Launch(cudaStream_t s, int kind, double bytes);
+    Launch(cudaStream_t s, int kind, double bytes, bool f64 = false);
     ~Launch();
   private:
     cudaStream_t s_;

@@ -28,11 +28,14 @@ cudaEvent_t get_event() {
 
 const char* kind_name(int k) {
     static const char* names[] = {"fft_pass", "spread", "interp", "select", "place", "pointwise",
-                                  "geometry", "plan_table", "plan_stage", "bluestein"};
-    return (k >= 0 && k < K_COUNT) ? names[k] : "unknown";
+                                  "geometry", "plan_table", "plan_stage", "bluestein",
+                                  "fft_pass_f64", "spread_f64", "interp_f64", "select_f64", "place_f64",
+                                  "pointwise_f64", "geometry_f64", "plan_table_f64", "plan_stage_f64",
+                                  "bluestein_f64"};
+    return (k >= 0 && k < 2 * K_COUNT) ? names[k] : "unknown";
 }
 
-Launch::Launch(cudaStream_t s, int kind, double bytes) : s_(s), kind_(kind), bytes_(bytes) {
+Launch::Launch(cudaStream_t s, int kind, double bytes, bool f64) : s_(s), kind_(kind + (f64 ? K_COUNT : 0)), bytes_(bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_on) {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -71,9 +74,9 @@ int64_t nufft_launch_count(void) { return (int64_t)g_launches.load(); }
 nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count) {
     if (!out || !count || cap < 0) return fail(NUFFT_ERR_ARG, "null argument");
     std::lock_guard<std::mutex> lk(g_mu);
-    nufft_profile_entry_t acc[K_COUNT];
+    nufft_profile_entry_t acc[2 * K_COUNT];
     std::memset(acc, 0, sizeof(acc));
-    for (int k = 0; k < K_COUNT; ++k) std::strncpy(acc[k].name, kind_name(k), sizeof(acc[k].name) - 1);
+    for (int k = 0; k < 2 * K_COUNT; ++k) std::strncpy(acc[k].name, kind_name(k), sizeof(acc[k].name) - 1);
     for (auto& r : g_recs) {
         cudaError_t e = cudaEventSynchronize(r.b);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__);
@@ -85,7 +88,7 @@ nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count)
         acc[r.kind].bytes += r.bytes;
     }
     int n = 0;
-    for (int k = 0; k < K_COUNT && n < cap; ++k)
+    for (int k = 0; k < 2 * K_COUNT && n < cap; ++k)
         if (acc[k].launches > 0) out[n++] = acc[k];
     *count = n;
     return NUFFT_OK;

@@ -403,7 +403,7 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
     const T* ef = FracPtr<T>::ext(g);
     const double es = sizeof(c2<T>);
     Launch L(s, K_SPREAD, (src ? batch * g.N * es : 0.0) + g.N * (es + 8.0 + sizeof(T)) + 4.0 * (g.n + g.w) +
-                              batch * g.n * es);
+                              batch * g.n * es, sizeof(T) == 8);
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
         k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
@@ -425,7 +425,7 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* sf = FracPtr<T>::srt(g);
     const double es = sizeof(c2<T>);
-    Launch L(s, K_INTERP, batch * g.n * es + g.N * (8.0 + sizeof(T) + es) + batch * g.N * es);
+    Launch L(s, K_INTERP, batch * g.n * es + g.N * (8.0 + sizeof(T) + es) + batch * g.N * es, sizeof(T) == 8);
     if (batch == 1) {
         dim3 gr(nblk(g.N), 1);
         k_interp<T, 1><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
@@ -440,14 +440,14 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
 template <typename T>
 void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0, const T* fac,
                    int64_t batch, cudaStream_t s) {
-    Launch L(s, K_SELECT, 2.0 * batch * P * sizeof(c2<T>) + P * sizeof(T));
+    Launch L(s, K_SELECT, 2.0 * batch * P * sizeof(c2<T>) + P * sizeof(T), sizeof(T) == 8);
     k_select<T><<<nblk(P * batch), kTB, 0, s>>>(in, n, out, out_bs, P, K0, fac, batch);
 }
 
 template <typename T>
 void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out, int64_t n,
                   int64_t batch, cudaStream_t s) {
-    Launch L(s, K_PLACE, batch * (P + n) * sizeof(c2<T>) + P * sizeof(T));
+    Launch L(s, K_PLACE, batch * (P + n) * sizeof(c2<T>) + P * sizeof(T), sizeof(T) == 8);
     k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch);
 }
 
@@ -455,7 +455,7 @@ template <typename T>
 void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P, const c2<T>* mulc,
                       const T* fac, int64_t batch, cudaStream_t s) {
     Launch L(s, K_POINTWISE, 2.0 * batch * P * sizeof(c2<T>) + (mulc ? P * sizeof(c2<T>) : 0) +
-                                 (fac ? P * sizeof(T) : 0));
+                                 (fac ? P * sizeof(T) : 0), sizeof(T) == 8);
     k_pointwise<T><<<nblk(P * batch), kTB, 0, s>>>(in, in_bs, out, out_bs, P, mulc, fac, batch);
 }
 
