@@ -104,106 +104,134 @@ __device__ __forceinline__ c2<T> tw2(const c2<T>* __restrict__ lo, const c2<T>* 
     return w;
 }
 
+// compile-time tile: C butterflies per CTA, C * R2 threads
+template <typename T, int R1, int R2> struct Cfg {
+    static constexpr int R = R1 * R2;
+    static constexpr int kElems = sizeof(T) == 4 ? 4096 : 2048;
+    static constexpr int C = (kElems / R < 256 / R2) ? kElems / R : 256 / R2;
+    static constexpr int TH = C * R2;
+    static constexpr int PR = R1 * (R2 + 1) + 1;   // padded column stride (odd)
+    static constexpr int NB = R1 / R2;             // (c, m1) groups per thread in step B
+};
+
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256) k_fft_p2(const c2<T>* in, c2<T>* out, Args a, const c2<T>* __restrict__ lo,
-                                                const c2<T>* __restrict__ hi, int dir) {
-    constexpr int R = R1 * R2;
-    constexpr int PR = R1 * (R2 + 1) + 1;      // padded column stride (odd)
+__global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, c2<T>* out, Args a,
+                                                               const c2<T>* __restrict__ lo,
+                                                               const c2<T>* __restrict__ hi, int dir) {
+    using G = Cfg<T, R1, R2>;
+    constexpr int R = G::R, C = G::C, TH = G::TH, PR = G::PR, NB = G::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c2<T>* sm = reinterpret_cast<c2<T>*>(smem_raw);
-    const int C = 1 << a.C_log;
     const int tid = threadIdx.x;
     const int nR_log = a.n_log - a.R_log;      // log2(n/R)
     const uint32_t nR = 1u << nR_log;
     const uint32_t Ns = 1u << a.Ns_log;
-    const int g0 = blockIdx.x << a.C_log;      // first butterfly of the CTA
-    const int tot = C * R;
-    // ---- load (coalesced) + pass twiddle ----
-    const bool in_cfast = nR >= (uint32_t)C;
+    const int g0 = blockIdx.x * C;             // first butterfly of the CTA
     const int tw_shift = a.n_log - a.Ns_log - a.R_log;   // log2(n / (Ns R))
-    for (int e = tid; e < tot; e += blockDim.x) {
-        int c, k;
-        if (in_cfast) { c = e & (C - 1); k = e >> a.C_log; }
-        else {
+    const int inner_shift = a.n_log - a.R_log;           // W_R^e = W_n^{e n/R}
+
+    // ---- step A: thread (c, k2) holds k = k1 R2 + k2, k1 < R1 ----
+    const int ca = tid % C, k2 = tid / C;
+    c2<T> v[R1];
+    if (nR >= (uint32_t)C) {
+        // direct loads: for fixed k1 a warp reads runs of C consecutive butterflies
+        const int g = g0 + ca;
+        const bool ok = g < a.total;
+        const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
+        const c2<T>* src = in + ((size_t)b << a.n_log) + j;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+            v[k1] = ok ? src[(size_t)(k1 * R2 + k2) << nR_log] : mk<T>(0, 0);
+        const uint32_t jm = j & (Ns - 1);
+        if (jm != 0) {
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const uint32_t k = (uint32_t)(k1 * R2 + k2);
+                if (k != 0) v[k1] = cmul(v[k1], tw2<T>(lo, hi, a.shift, (jm * k) << tw_shift, dir));
+            }
+        }
+    } else {
+        // several short transforms per CTA (n/R < C, single pass, Ns = 1): the
+        // CTA's inputs are one contiguous block; stage it through shared memory
+        const int base_b = g0 >> nR_log;   // g0 is a multiple of n/R here
+#pragma unroll
+        for (int i = 0; i < R1; ++i) {
+            const int e = tid + i * TH;
             const int bl = e >> a.n_log, idx = e & ((1 << a.n_log) - 1);
-            c = (bl << nR_log) + (idx & (nR - 1));
-            k = idx >> nR_log;
+            const int c = (bl << nR_log) + (idx & (nR - 1));
+            const int k = idx >> nR_log;
+            const bool ok = g0 + c < a.total;
+            const c2<T> x = ok ? in[((size_t)(base_b + bl) << a.n_log) + idx] : mk<T>(0, 0);
+            sm[c * PR + (k / R2) * (R2 + 1) + (k % R2)] = x;
         }
-        const int g = g0 + c;
-        c2<T> x = mk<T>(0, 0);
-        if (g < a.total) {
-            const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
-            x = in[((size_t)b << a.n_log) + j + ((size_t)k << nR_log)];
-            const uint32_t jm = j & (Ns - 1);
-            if (jm != 0 && k != 0) x = cmul(x, tw2<T>(lo, hi, a.shift, (jm * (uint32_t)k) << tw_shift, dir));
-        }
-        const int k1 = k / R2, k2 = k % R2;
-        sm[c * PR + k1 * (R2 + 1) + k2] = x;
+        __syncthreads();
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = sm[ca * PR + k1 * (R2 + 1) + k2];
+        __syncthreads();
     }
-    __syncthreads();
-    // ---- step A: DFT over k1 for each (c, k2), times W_R^{m1 k2} ----
-    const int inner_shift = a.n_log - a.R_log;   // W_R^e = W_n^{e n/R}
-    for (int t = tid; t < C * R2; t += blockDim.x) {
-        const int c = t / R2, k2 = t % R2;
-        c2<T> v[R1];
-        c2<T>* col = sm + c * PR + k2;
+    dft_reg<R1, T>(v, dir);
+    if (k2 != 0) {
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) v[k1] = col[k1 * (R2 + 1)];
-        dft_reg<R1, T>(v, dir);
-        if (k2 != 0) {
-#pragma unroll
-            for (int m1 = 1; m1 < R1; ++m1) v[m1] = cmul(v[m1], tw2<T>(lo, hi, a.shift, (uint32_t)(m1 * k2) << inner_shift, dir));
-        }
+        for (int m1 = 1; m1 < R1; ++m1)
+            v[m1] = cmul(v[m1], tw2<T>(lo, hi, a.shift, (uint32_t)(m1 * k2) << inner_shift, dir));
+    }
+    {
+        c2<T>* col = sm + ca * PR + k2;
 #pragma unroll
         for (int m1 = 0; m1 < R1; ++m1) col[m1 * (R2 + 1)] = v[m1];
     }
     __syncthreads();
-    // ---- step B: DFT over k2 for each (c, m1) -> X[m1 + R1 m2] ----
-    constexpr int NB = R1 >= R2 ? R1 / R2 : 1;     // (c, m1) groups per thread
-    c2<T> v[NB][R2];
-    int cc[NB], mm[NB];
+
+    // ---- step B: thread (c, m1) -> X[m1 + R1 m2], m2 < R2 ----
+    c2<T> w[NB][R2];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-        const int t = tid + q * blockDim.x;
-        cc[q] = -1;
-        if (t < C * R1) {
-            const int c = t / R1, m1 = t % R1;
-            cc[q] = c; mm[q] = m1;
-            const c2<T>* row = sm + c * PR + m1 * (R2 + 1);
+        const int t = tid + q * TH;
+        const int c = t % C, m1 = t / C;
+        const c2<T>* row = sm + c * PR + m1 * (R2 + 1);
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) v[q][k2] = row[k2];
-            dft_reg<R2, T>(v[q], dir);
-        }
+        for (int kk = 0; kk < R2; ++kk) w[q][kk] = row[kk];
+        dft_reg<R2, T>(w[q], dir);
     }
-    // more (c, m1) pairs than threads * NB cannot happen: blockDim = C * R2
-    __syncthreads();
+    if (Ns >= (uint32_t)C) {
+        // direct stores: for fixed m a warp writes runs of C consecutive butterflies
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-        if (cc[q] >= 0) {
-            c2<T>* col = sm + cc[q] * PR + mm[q];
+        for (int q = 0; q < NB; ++q) {
+            const int t = tid + q * TH;
+            const int c = t % C, m1 = t / C;
+            const int g = g0 + c;
+            if (g < a.total) {
+                const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
+                c2<T>* dst = out + ((size_t)b << a.n_log) + ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) +
+                             (j & (Ns - 1));
 #pragma unroll
-            for (int m2 = 0; m2 < R2; ++m2) col[m2 * R1] = v[q][m2];
+                for (int m2 = 0; m2 < R2; ++m2) dst[(size_t)(m1 + R1 * m2) << a.Ns_log] = w[q][m2];
+            }
         }
-    }
-    __syncthreads();
-    // ---- store (coalesced) ----
-    const bool out_cfast = Ns >= (uint32_t)C;
-    for (int e = tid; e < tot; e += blockDim.x) {
-        int c, m;
-        if (out_cfast) { c = e & (C - 1); m = e >> a.C_log; }
-        else {
-            // contiguous region: offset e = blk (Ns R) + m Ns + jj, c = blk Ns + jj
+    } else {
+        // the CTA's outputs form one contiguous block: stage through shared memory
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int t = tid + q * TH;
+            const int c = t % C, m1 = t / C;
+            c2<T>* col = sm + c * PR + m1;
+#pragma unroll
+            for (int m2 = 0; m2 < R2; ++m2) col[m2 * R1] = w[q][m2];
+        }
+        __syncthreads();
+        const int g = g0;   // block start: offset e = blk (Ns R) + m Ns + jj, c = blk Ns + jj
+        const uint32_t b0 = (uint32_t)g >> nR_log, j0 = (uint32_t)g & (nR - 1);
+        const size_t base = ((size_t)b0 << a.n_log) + ((size_t)(j0 >> a.Ns_log) << (a.Ns_log + a.R_log));
+#pragma unroll
+        for (int i = 0; i < R1; ++i) {
+            const int e = tid + i * TH;
             const int blk = e >> (a.Ns_log + a.R_log);
             const int rem = e & ((1 << (a.Ns_log + a.R_log)) - 1);
-            m = rem >> a.Ns_log;
-            c = (blk << a.Ns_log) + (rem & (Ns - 1));
+            const int m = rem >> a.Ns_log;
+            const int c = (blk << a.Ns_log) + (rem & (Ns - 1));
+            if (g0 + c < a.total) out[base + e] = sm[c * PR + m];
         }
-        const int g = g0 + c;
-        if (g >= a.total) continue;
-        const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
-        const uint32_t jm = j & (Ns - 1);
-        out[((size_t)b << a.n_log) + ((j >> a.Ns_log) << (a.Ns_log + a.R_log)) + jm + ((size_t)m << a.Ns_log)] =
-            sm[c * PR + m];
     }
 }
 

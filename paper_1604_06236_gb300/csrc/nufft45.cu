@@ -91,6 +91,16 @@ struct Params {
     KernelShape ks_solve{0, 0}, ks_plan{0, 0};
 };
 
+// oversampled grid length >= m: a power of two when that costs at most 30%
+// more points (the power-of-two FFT passes are the fastest), otherwise the
+// smallest 2,3,5,7-smooth length
+static int64_t grid_size(int64_t m) {
+    int64_t p2 = 1;
+    while (p2 < m) p2 <<= 1;
+    const int64_t sm = next_smooth(m);
+    return (double)p2 <= 1.3 * (double)sm ? p2 : sm;
+}
+
 // ES kernel shape for an even width w on an oversampling-2 grid
 static KernelShape es_shape(int w) { return KernelShape{w, 2.30 * w}; }
 
@@ -98,7 +108,9 @@ static KernelShape es_shape(int w) { return KernelShape{w, 2.30 * w}; }
 // to mu ~ gamma^-eta (Eq. 49 with gamma = e^{2 pi P a}); round-off in the
 // scaling by e^{2 pi p a} of Eqs. 31 and 43 grows with gamma.  float64:
 // gamma = 1000 and eta from tol; float32 transforms: gamma = 30, eta = 5, so
-// that the float64 plan is accurate to ~1e-8 and the float32 stages dominate.
+// that the float64 plan is accurate to ~1e-8 and the float32 stages dominate
+// (gamma = 60, eta = 4 keeps R = 4N, so a power-of-two N gets a power-of-two
+// length-R grid).
 static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
     p.N = N;
     p.prec = prec;
@@ -111,8 +123,8 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
         w_plan = w_solve = tol < 1e-8 ? 16 : 12;
     } else {
         if (tol < 1e-6) return fail(NUFFT_ERR_ACCURACY, "tol %g below what the float32 path attains (1e-6)", tol);
-        p.gamma = 30.0;
-        p.eta = 5;
+        p.gamma = 60.0;
+        p.eta = 4;
         w_plan = 14;
         w_solve = 8;
     }
@@ -124,8 +136,8 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
     p.ks_solve = es_shape(w_solve);
     p.ks_plan = es_shape(w_plan);
     const int wmax = std::max(w_solve, w_plan);
-    p.ns = next_smooth(std::max<int64_t>(2 * N, 2 * wmax));
-    p.nR = next_smooth(std::max<int64_t>(2 * p.R, 2 * wmax));
+    p.ns = grid_size(std::max<int64_t>(2 * N, 2 * wmax));
+    p.nR = grid_size(std::max<int64_t>(2 * p.R, 2 * wmax));
     p.K0s = N / 2;
     p.K0R = p.R / 2;
     return NUFFT_OK;

@@ -6,7 +6,7 @@ Tolerances (relative L2, the paper's error measure of Sec. VI):
     rounding of the data is ~6e-8; spreading width 8 leaves ~4e-7);
   * plan quantities K_q, L'(z_p), w_p are always float64: 1e-10 for the
     float64 plan (gamma = 1000, eta = 4), 1e-7 for the float32 path's plan
-    (gamma = 30, eta = 5: truncation ~0.4 gamma^-eta ~ 2e-8, Sec. V).
+    (gamma = 60, eta = 4: truncation ~0.4 gamma^-eta ~ 3e-8, Sec. V).
 Sizes span one to many CTA tiles and FFT passes, ragged tails, prime and
 non-smooth N (Bluestein), and the N = 65536 workload in full.
 """
