@@ -49,7 +49,13 @@ typedef enum {
 
 typedef enum {
     NUFFT_FP32 = 1,   /* node-dependent plan in float64, transforms in float32 (complex64 data) */
-    NUFFT_FP64 = 2    /* everything in float64 (complex128 data) */
+    NUFFT_FP64 = 2,   /* everything in float64 (complex128 data) */
+    /* OR-ed into the precision: nufft_inv5/nufft_inv4 apply the refined method
+     * of Sec. V (R-NFFT): the inverse is applied again to the residual
+     * b - F x1, formed by a float64 type-2 (resp. type-1) transform, and the
+     * correction is added, taking the relative error from eps to about eps^2
+     * (Eqs. 44-46).  For ill-conditioned node sets (near-coincident nodes). */
+    NUFFT_REFINE = 0x100
 } nufft_prec;
 
 /*
@@ -66,7 +72,7 @@ typedef enum {
  * tol    target relative L2 error: NUFFT_FP64 accepts [1e-12, 1e-1],
  *        NUFFT_FP32 accepts [1e-6, 1e-1]; tighter values return
  *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
- * prec   NUFFT_FP32 or NUFFT_FP64.
+ * prec   NUFFT_FP32 or NUFFT_FP64, optionally | NUFFT_REFINE.
  * plan   receives the plan; owned by the caller, release with nufft_destroy.
  * The call synchronises `stream` once to check for coincident nodes: two
  * nodes whose turns t differ by less than 2^-44 modulo 1 make the systems of
@@ -133,6 +139,35 @@ nufft_status nufft_fwd1(nufft_plan_t plan, const void* a, void* A, int64_t batch
  *   c: batch x N coefficients, f: batch x N samples.
  */
 nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream);
+
+/*
+ * nufft_fwd2_deriv -- derivative of the type-2 sum with respect to t:
+ *   s'(t_p) = sum_{m<N} (j 2 pi m) S_m e^{j 2 pi m t_p}  (d/dt of Eq. 34).
+ *   Used by the node gradients of the type-4/5 inverses: with S = G^{-1} f
+ *   and G_{q,m} = e^{j 2 pi m t_q} (Eq. 48), dS = -G^{-1} (s' o dt).
+ *   c: batch x N coefficients, f: batch x N values at the nodes.
+ */
+nufft_status nufft_fwd2_deriv(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream);
+
+/*
+ * Node gradients of the inverses (for reverse-mode differentiation; the
+ * paper has no counterpart, the formulas follow from Eqs. 47 and 48).
+ * With G_{q,m} = e^{j 2 pi m t_q} and a real loss L whose gradient with
+ * respect to the output is g (convention dL = Re<g, d out>):
+ *   type-5, S = G^{-1} f:   u = G^{-H} g (= nufft_inv4 of g) is the gradient
+ *     with respect to f, and dL/dx_q = -(1/2pi) sum_b Re(conj(u_q) s'_b(t_q)),
+ *     s' the derivative type-2 of S (nufft_fwd2_deriv);
+ *   type-4, a = G^{-H} A:   w = G^{-1} g (= nufft_inv5 of g) is the gradient
+ *     with respect to A, and dL/dx_q = -(1/2pi) sum_b Re(conj(w'_b(t_q)) a_q).
+ * u, S (resp. w, a): batch x N device buffers in the plan's precision; the
+ * sum runs over the batch (right-hand sides sharing the nodes).
+ * grad_x: N float64 device values, overwritten.  Scratch for the derivative
+ * is taken from the device pool.
+ */
+nufft_status nufft_inv5_grad_nodes(nufft_plan_t plan, const void* u, const void* S, int64_t batch, double* grad_x,
+                                   nufft_stream_t stream);
+nufft_status nufft_inv4_grad_nodes(nufft_plan_t plan, const void* w, const void* a, int64_t batch, double* grad_x,
+                                   nufft_stream_t stream);
 
 /* nufft_destroy -- release a plan (NULL is accepted).  Its device memory is
  * returned in stream order on the plan's creation stream, so work already

@@ -8,6 +8,7 @@ from the product package.
 What it computes (the plain definitions, no fast algorithm):
 
 * ``type1(x, a)``     A_k = sum_p a_p e^{-j2pi k t_p}, k = 0..P-1        (Sec. II, Eq. 32)
+* ``type1_at(x,a,ks)`` the same sum at a list of integer frequencies
 * ``type2(x, S)``     s_p = sum_m S_m e^{+j2pi m t_p}, m = 0..P-1        (Sec. II, Eq. 34)
 * ``inv5(x, s)``      solves Eq. 48 for S by Gaussian elimination (LU with
                       partial pivoting, the paper's GE benchmark of Sec. VI)
@@ -15,6 +16,8 @@ What it computes (the plain definitions, no fast algorithm):
 * ``kernel_samples``  K_q = L(rho e^{j2pi q/P}) = prod_p (z_q - z_p)     (Eqs. 10, 11)
 * ``deriv_samples``   D_p = L'(z_p) = prod_{q!=p} (z_p - z_q)            (Sec. III-D)
 * ``weights``         w_p = h(-P t_p + jPa)/(L'(z_p) z_p)                (Eqs. 17, 27, 40)
+* ``inv5_vjp``, ``inv4_vjp``  gradients of a real loss through the inverses
+                      (dense LU and direct sums; pinned by finite differences)
 
 Nodes are given in radians (x) and canonicalised exactly as
 ``t = x/(2 pi) mod 1``, ``T = trunc(t 2^64)``; all phases are formed from the
@@ -64,8 +67,9 @@ def _load():
         lib.oracle_kernel_samples.argtypes = [i64, P, d, P]
         lib.oracle_deriv_samples.argtypes = [i64, P, P]
         lib.oracle_weights.argtypes = [i64, P, d, P, P]
+        lib.oracle_type1_at.argtypes = [i64, P, P, i64, P, P]
         for f in (lib.oracle_canon, lib.oracle_type1, lib.oracle_type2, lib.oracle_matrix,
-                  lib.oracle_kernel_samples, lib.oracle_deriv_samples, lib.oracle_weights):
+                  lib.oracle_kernel_samples, lib.oracle_deriv_samples, lib.oracle_weights, lib.oracle_type1_at):
             f.restype = None
         _lib = lib
     return _lib
@@ -95,6 +99,16 @@ def type1(x, a, k0=0, M=None):
     M = T.size if M is None else M
     A = np.empty(M, dtype=np.complex128)
     _load().oracle_type1(T.size, _ptr(T), _ptr(a), k0, M, _ptr(A))
+    return A
+
+
+def type1_at(x, a, ks):
+    """Eq. 32 at the integer frequencies ks: A_k = sum_p a_p e^{-j 2 pi k t_p}."""
+    T, _ = canon(x)
+    a = _c128(a)
+    ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int64))
+    A = np.empty(ks.size, dtype=np.complex128)
+    _load().oracle_type1_at(T.size, _ptr(T), _ptr(a), ks.size, _ptr(ks), _ptr(A))
     return A
 
 
@@ -163,3 +177,38 @@ def rel_l2(a, b):
     b = np.asarray(b, dtype=np.complex128)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def inv5_vjp(x, f, g_S):
+    """Gradient of a real loss through the type-5 inverse S = G^{-1} f (Eq. 48).
+
+    g_S is the loss gradient with respect to S in the convention
+    dL = Re<g_S, dS> (PyTorch's).  Returns (g_f, g_x):
+      g_f = G^{-H} g_S (the type-4 system of Eq. 47 is G^H),
+      dS = -G^{-1} (s' o dt) with s'(t) = sum_m j 2 pi m S_m e^{j 2 pi m t}
+      (row q of G depends on t_q only), so dL/dt_q = -Re(conj(g_f[q]) s'(t_q)),
+      g_x = dL/dt / (2 pi)  (t = x / 2 pi).
+    Dense LU and exact-phase direct sums."""
+    G = matrix(x)
+    S = np.linalg.solve(G, _c128(f))
+    u = np.linalg.solve(G.conj().T, _c128(g_S))
+    P = S.size
+    sd = type2(x, 2j * np.pi * np.arange(P) * S)
+    g_t = -(np.conj(u) * sd).real
+    return u, g_t / (2 * np.pi)
+
+
+def inv4_vjp(x, A, g_a):
+    """Gradient of a real loss through the type-4 inverse a = G^{-H} A (Eq. 47).
+
+    dL = Re<g_a, da>.  Returns (g_A, g_x): g_A = G^{-1} g_a; with
+    w = g_A and w'(t) = sum_m j 2 pi m w_m e^{j 2 pi m t},
+    dL/dt_q = -Re(a_q conj(w'(t_q))) (G^H depends on t_q through column q),
+    g_x = dL/dt / (2 pi).  Dense LU and exact-phase direct sums."""
+    G = matrix(x)
+    a = np.linalg.solve(G.conj().T, _c128(A))
+    w = np.linalg.solve(G, _c128(g_a))
+    P = a.size
+    wd = type2(x, 2j * np.pi * np.arange(P) * w)
+    g_t = -(a * np.conj(wd)).real
+    return w, g_t / (2 * np.pi)

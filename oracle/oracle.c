@@ -189,3 +189,22 @@ void oracle_weights(int64_t P, const uint64_t* T, double rho, const double* D, d
         w[2 * p + 1] = -bi / nn;
     }
 }
+
+/* Type-1, Eq. 32, at an arbitrary list of integer frequencies ks[0..nk-1]. */
+void oracle_type1_at(int64_t P, const uint64_t* T, const double* a, int64_t nk, const int64_t* ks, double* A)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nk; ++i) {
+        uint64_t kk = (uint64_t)ks[i];
+        double sr = 0.0, si = 0.0;
+        for (int64_t p = 0; p < P; ++p) {
+            double cr, ci;
+            cis_turns(kk * T[p], -1.0, &cr, &ci);
+            double ar = a[2 * p], ai = a[2 * p + 1];
+            sr += ar * cr - ai * ci;
+            si += ar * ci + ai * cr;
+        }
+        A[2 * i] = sr;
+        A[2 * i + 1] = si;
+    }
+}

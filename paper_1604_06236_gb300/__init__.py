@@ -13,10 +13,11 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "build", "library_path", "ProfileEntry", "check"]
+__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "REFINE", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
+REFINE = 0x100   # OR into the precision: one refinement step per inverse (Sec. V)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libnufft45.so")
@@ -66,9 +67,12 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.nufft_plan.argtypes = [i64, vp, dbl, i32, vp, ctypes.POINTER(vp)]
-        for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2"):
+        for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
+        for name in ("nufft_inv5_grad_nodes", "nufft_inv4_grad_nodes"):
+            getattr(L, name).argtypes = [vp, vp, vp, i64, vp, vp]
+            getattr(L, name).restype = i32
         L.nufft_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.nufft_plan_export.argtypes = [vp, i32, vp, vp]
         L.nufft_cache_clear.argtypes = []
@@ -82,7 +86,8 @@ def lib():
         L.nufft_status_string.restype = ctypes.c_char_p
         L.nufft_last_error_message.argtypes = []
         L.nufft_last_error_message.restype = ctypes.c_char_p
-        for name in ("nufft_plan", "nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_destroy",
+        for name in ("nufft_plan", "nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv",
+                     "nufft_destroy",
                      "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear"):
             getattr(L, name).restype = i32
         _lib = L
@@ -117,11 +122,11 @@ class Plan:
             x = torch.as_tensor(x)
         x = x.to(torch.float64).contiguous()
         if tol is None:
-            tol = 1e-5 if prec == FP32 else 1e-10
+            tol = 1e-5 if (prec & 0xFF) == FP32 else 1e-10
         self.N = x.numel()
         self.prec = prec
         self.tol = tol
-        self.dtype = torch.complex64 if prec == FP32 else torch.complex128
+        self.dtype = torch.complex64 if (prec & 0xFF) == FP32 else torch.complex128
         self.device = x.device if x.is_cuda else torch.device("cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         self._x_keep = x
@@ -177,3 +182,29 @@ class Plan:
     def fwd2(self, c, out=None, stream=None):
         """Type-2: s(t_p) = sum_m c_m e^{j 2 pi m t_p} (Eq. 34)."""
         return self._run("nufft_fwd2", c, out, stream)
+
+    def fwd2_deriv(self, c, out=None, stream=None):
+        """d/dt of the type-2 sum: sum_m (j 2 pi m) c_m e^{j 2 pi m t_p}."""
+        return self._run("nufft_fwd2_deriv", c, out, stream)
+
+    def _grad_nodes(self, fname, p1, p2, stream=None):
+        import torch
+        for t in (p1, p2):
+            if t.dtype != self.dtype or t.shape[-1] != self.N:
+                raise TypeError("expected %s tensors with last dimension %d" % (self.dtype, self.N))
+        p1 = p1.contiguous()
+        p2 = p2.contiguous()
+        batch = p1.numel() // self.N
+        if p2.numel() != p1.numel():
+            raise ValueError("both operands need the same batch")
+        out = torch.empty(self.N, dtype=torch.float64, device=p1.device)
+        check(getattr(lib(), fname)(self._h, _ptr(p1), _ptr(p2), batch, _ptr(out), _stream_handle(stream)))
+        return out
+
+    def inv5_grad_nodes(self, u, S, stream=None):
+        """dL/dx for S = inv5(f): u = gradient w.r.t. f (inv4 of dL/dS), S the solution."""
+        return self._grad_nodes("nufft_inv5_grad_nodes", u, S, stream)
+
+    def inv4_grad_nodes(self, w, a, stream=None):
+        """dL/dx for a = inv4(A): w = gradient w.r.t. A (inv5 of dL/da), a the solution."""
+        return self._grad_nodes("nufft_inv4_grad_nodes", w, a, stream)

@@ -119,14 +119,25 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
 template <typename T>
 void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0,
                    const T* fac, int64_t batch, cudaStream_t s);
-// out[b][g] = in[b][k] * fac[k] where k = g' + K0 for the centred index g' of g, 0 elsewhere
+// out[b][g] = in[b][k] * fac[k] (* j 2 pi k when deriv) where k = g' + K0 for the
+// centred index g' of g, 0 elsewhere
 template <typename T>
 void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out,
-                  int64_t n, int64_t batch, cudaStream_t s);
+                  int64_t n, int64_t batch, cudaStream_t s, bool deriv = false);
 // out[b][k] = in[b][k] * (mulc ? mulc[k] : 1) * (fac ? fac[k] : 1)
 template <typename T>
 void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P,
                       const c2<T>* mulc, const T* fac, int64_t batch, cudaStream_t s);
+
+// refinement: out = (double) in; r = in - y (float64 difference, stored in T); out += c
+template <typename T> void launch_widen(const c2<T>* in, double2* out, int64_t n, cudaStream_t s);
+template <typename T> void launch_residual(const c2<T>* in, const double2* y, c2<T>* r, int64_t n, cudaStream_t s);
+template <typename T> void launch_accumulate(c2<T>* out, const c2<T>* c, int64_t n, cudaStream_t s);
+
+// out[q] = scale * sum_b Re(conj(X[b][q]) Y[b][q]) (float64 accumulation)
+template <typename T>
+void launch_grad_nodes(const c2<T>* X, const c2<T>* Y, int64_t N, int64_t batch, double scale, double* out,
+                       cudaStream_t s);
 
 // plan-stage kernels (float64)
 struct GLRule { int nq; double z[48]; double wq[48]; };

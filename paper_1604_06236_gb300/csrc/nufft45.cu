@@ -89,6 +89,8 @@ struct Params {
     int64_t ns = 0, nR = 0;
     int64_t K0s = 0, K0R = 0;
     KernelShape ks_solve{0, 0}, ks_plan{0, 0};
+    bool refine = false;   // one refinement step per inverse (Sec. V)
+    int halo = 0;          // halo width of the transforms' extended node list
 };
 
 // oversampled grid length >= m: a power of two when that costs at most 30%
@@ -140,6 +142,7 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
     p.nR = grid_size(std::max<int64_t>(2 * p.R, 2 * wmax));
     p.K0s = N / 2;
     p.K0R = p.R / 2;
+    p.halo = w_solve;
     return NUFFT_OK;
 }
 
@@ -242,6 +245,8 @@ struct nufft_plan_s {
     void* wt5_ext = nullptr;         // w e^{-j 2 pi K0 t}
     void* wt2_srt = nullptr;         // e^{+j 2 pi K0 t}, sorted slot order
     void* wt4_srt = nullptr;         // w e^{+j 2 pi K0 t}
+    double2* modm64_ext = nullptr;   // float64 e^{-j 2 pi K0 t} (refinement residuals)
+    double2* modp64_srt = nullptr;   // float64 e^{+j 2 pi K0 t}
     int64_t chunk = 1;
 };
 
@@ -272,10 +277,11 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     z.add<uint64_t>(N);
     z.add<int>(N); z.add<int>(N); z.add<double>(N); z.add<float>(N);
     z.add<int>(2 * N); z.add<int>(2 * N); z.add<double>(2 * N); z.add<float>(2 * N);
-    z.add<int>(prm.ns + prm.ks_solve.w + 1); z.add<int>(1);
+    z.add<int>(prm.ns + prm.halo + 1); z.add<int>(1);
     z.add<double2>(P); z.add<double2>(N); z.add<double2>(N);
     z.add<char>(es * P);
     z.add<char>(es * 2 * N); z.add<char>(es * 2 * N); z.add<char>(es * N); z.add<char>(es * N);
+    if (prm.refine) { z.add<double2>(2 * N); z.add<double2>(N); }
     nufft_status st = pl->mem.reserve(z.used, s);
     if (st != NUFFT_OK) return st;
     Arena& m = pl->mem;
@@ -285,7 +291,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     gs.srt_fracf = m.take<float>(N);
     gs.ext_perm = m.take<int>(2 * N); gs.ext_cell = m.take<int>(2 * N); gs.ext_frac = m.take<double>(2 * N);
     gs.ext_fracf = m.take<float>(2 * N);
-    gs.cstart = m.take<int>(prm.ns + prm.ks_solve.w + 1);
+    gs.cstart = m.take<int>(prm.ns + prm.halo + 1);
     gs.dup_flag = m.take<int>(1);
     pl->K64 = m.take<double2>(P);
     pl->D64 = m.take<double2>(N);
@@ -295,6 +301,10 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     pl->wt5_ext = m.take<char>(es * 2 * N);
     pl->wt2_srt = m.take<char>(es * N);
     pl->wt4_srt = m.take<char>(es * N);
+    if (prm.refine) {
+        pl->modm64_ext = m.take<double2>(2 * N);
+        pl->modp64_srt = m.take<double2>(N);
+    }
 
     // temporaries of the plan
     Geometry gR;
@@ -351,7 +361,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     double2* dco = (F == vecP) ? workP : vecP;
     launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
     // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
-    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.ks_solve.w, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.halo, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
     launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, gridS, prm.ns, 1, s);
     double2* gs_sp = nullptr;
     if ((st = fft_exec<double>(tab.fft_ns64, gridS, workS, 1, +1, s, &gs_sp)) != NUFFT_OK) { tmp.release(); return st; }
@@ -359,7 +369,12 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     launch_interp<double>(gs, prm.ks_plan, gs_sp, modp, pl->D64, N, 1, s);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
     launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
-    const int* ext_count = gs.cstart + (prm.ns + prm.ks_solve.w);
+    const int* ext_count = gs.cstart + (prm.ns + prm.halo);
+    if (prm.refine) {
+        // float64 modulations for the residual transforms of the refinement
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->modp64_srt, modp, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        launch_mod(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->modm64_ext, s);
+    }
     if (f32) {
         launch_slot_weights<float>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
                                    (float2*)pl->wt1_ext, (float2*)pl->wt5_ext, s);
@@ -377,7 +392,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
 }
 
 // ------------------------------------------------------------ transforms ---
-enum Op { OP_INV5, OP_INV4, OP_FWD1, OP_FWD2 };
+enum Op { OP_INV5, OP_INV4, OP_FWD1, OP_FWD2, OP_FWD2D };
 
 template <typename T>
 nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* out, int64_t bc, c2<T>* gA, c2<T>* gW,
@@ -425,8 +440,9 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
             launch_select<T>(r, ns, out, N, P, prm.K0s, fac1, bc, s);
             break;
         }
-        case OP_FWD2: {
-            launch_place<T>(in, N, P, prm.K0s, fac1, gA, ns, bc, s);
+        case OP_FWD2:
+        case OP_FWD2D: {
+            launch_place<T>(in, N, P, prm.K0s, fac1, gA, ns, bc, s, op == OP_FWD2D);
             if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
             launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt2_srt, out, N, bc, s);
             break;
@@ -461,6 +477,61 @@ nufft_status run_op(nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* out, int64_
     return st;
 }
 
+// float64 forward transforms with the plan's float64 data (kernel width of
+// the plan, grid of the transforms): y = G x (type-2) or y = G^H x (type-1)
+nufft_status forward64(const nufft_plan_s* pl, bool type2, const double2* x, double2* y, int64_t bc, double2* g,
+                       double2* gw, cudaStream_t s) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    const int64_t N = prm.N;
+    double2* r = nullptr;
+    nufft_status st;
+    if (type2) {
+        launch_place<double>(x, N, N, prm.K0s, tab.plan_place, g, prm.ns, bc, s);
+        if ((st = fft_exec<double>(tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
+        launch_interp<double>(pl->gs, prm.ks_plan, r, pl->modp64_srt, y, N, bc, s);
+    } else {
+        launch_spread<double>(pl->gs, prm.ks_plan, x, N, pl->modm64_ext, g, bc, s);
+        if ((st = fft_exec<double>(tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
+        launch_select<double>(r, prm.ns, y, N, N, prm.K0s, tab.plan_place, bc, s);
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+// Sec. V refinement: x1 = inv(b); r = b - F x1 with a float64 forward F;
+// x2 = x1 + inv(r).  The relative error goes from eps to about eps^2 (Eq. 46).
+template <typename T>
+nufft_status run_refined(nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* out, int64_t batch, cudaStream_t s) {
+    nufft_status st = run_op<T>(pl, op, in, out, batch, s);
+    if (st != NUFFT_OK) return st;
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    const int64_t N = prm.N;
+    const size_t item = sizeof(double2) * (2 * N + prm.ns + fft_work_elems(tab.fft_ns64)) + 2 * sizeof(c2<T>) * N;
+    const int64_t bc = std::max<int64_t>(1, std::min<int64_t>(batch, ((int64_t)512 << 20) / (int64_t)item));
+    Arena ar;
+    if ((st = ar.reserve(item * bc + 8 * 256, s)) != NUFFT_OK) return st;
+    double2* x64 = ar.take<double2>(N * bc);
+    double2* y64 = ar.take<double2>(N * bc);
+    double2* g64 = ar.take<double2>(prm.ns * bc);
+    double2* w64 = ar.take<double2>(fft_work_elems(tab.fft_ns64) * bc);
+    c2<T>* r = ar.take<c2<T>>(N * bc);
+    c2<T>* corr = ar.take<c2<T>>(N * bc);
+    for (int64_t b0 = 0; b0 < batch && st == NUFFT_OK; b0 += bc) {
+        const int64_t nb = std::min(bc, batch - b0);
+        const c2<T>* bin = in + b0 * N;
+        c2<T>* bout = out + b0 * N;
+        launch_widen<T>(bout, x64, N * nb, s);
+        if ((st = forward64(pl, op == OP_INV5, x64, y64, nb, g64, w64, s)) != NUFFT_OK) break;
+        launch_residual<T>(bin, y64, r, N * nb, s);
+        if ((st = run_op<T>(pl, op, r, corr, nb, s)) != NUFFT_OK) break;
+        launch_accumulate<T>(bout, corr, N * nb, s);
+    }
+    ar.release();
+    return st;
+}
+
 nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int64_t batch, nufft_stream_t stream) {
     if (!plan) return fail(NUFFT_ERR_ARG, "null plan");
     if (batch < 0) return fail(NUFFT_ERR_ARG, "negative batch");
@@ -487,10 +558,13 @@ nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int
         if (!dout) dout_p = b;
     }
     nufft_status st;
+    const bool refined = plan->prm.refine && (op == OP_INV5 || op == OP_INV4);
     if (plan->prm.prec == NUFFT_FP64)
-        st = run_op<double>(plan, op, (const double2*)din_p, (double2*)dout_p, batch, s);
+        st = refined ? run_refined<double>(plan, op, (const double2*)din_p, (double2*)dout_p, batch, s)
+                     : run_op<double>(plan, op, (const double2*)din_p, (double2*)dout_p, batch, s);
     else
-        st = run_op<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s);
+        st = refined ? run_refined<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s)
+                     : run_op<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s);
     if (st == NUFFT_OK && !dout) {
         NUFFT_CUDA_TRY(cudaMemcpyAsync(out, dout_p, bytes, cudaMemcpyDeviceToHost, s));
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -503,6 +577,47 @@ nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int
 
 }  // namespace
 
+namespace {
+
+// grad_x[q] = -(1/2pi) sum_b Re(conj(X_b[q]) Y_b[q]) where the derivative
+// type-2 is applied to `deriv_of` first: inv5 (X = u, Y = s' of S) or inv4
+// (X = w' of w, Y = a).
+template <typename T>
+nufft_status grad_nodes_impl(nufft_plan_s* pl, int kind, const c2<T>* p1, const c2<T>* p2, int64_t batch,
+                             double* gx, cudaStream_t s) {
+    const int64_t N = pl->prm.N;
+    Arena ar;
+    nufft_status st = ar.reserve(sizeof(c2<T>) * (size_t)N * (size_t)batch + 256, s);
+    if (st != NUFFT_OK) return st;
+    c2<T>* d = ar.take<c2<T>>((size_t)N * (size_t)batch);
+    const c2<T>* src = kind == 5 ? p2 : p1;     // inv5: S; inv4: w
+    st = run_op<T>(pl, OP_FWD2D, src, d, batch, s);
+    if (st == NUFFT_OK) {
+        const double scale = -1.0 / 6.283185307179586476925286766559;
+        if (kind == 5) launch_grad_nodes<T>(p1, d, N, batch, scale, gx, s);
+        else launch_grad_nodes<T>(d, p2, N, batch, scale, gx, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(e, "launch_grad_nodes", __FILE__, __LINE__);
+    }
+    ar.release();
+    return st;
+}
+
+nufft_status grad_nodes_public(nufft_plan_t plan, int kind, const void* p1, const void* p2, int64_t batch,
+                               double* gx, nufft_stream_t stream) {
+    if (!plan) return fail(NUFFT_ERR_ARG, "null plan");
+    if (batch < 1) return fail(NUFFT_ERR_ARG, "batch must be >= 1");
+    if (!p1 || !p2 || !gx) return fail(NUFFT_ERR_ARG, "null data pointer");
+    if (!is_device_ptr(p1) || !is_device_ptr(p2) || !is_device_ptr(gx))
+        return fail(NUFFT_ERR_ARG, "node gradients need device buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->prm.prec == NUFFT_FP64)
+        return grad_nodes_impl<double>(plan, kind, (const double2*)p1, (const double2*)p2, batch, gx, s);
+    return grad_nodes_impl<float>(plan, kind, (const float2*)p1, (const float2*)p2, batch, gx, s);
+}
+
+}  // namespace
+
 extern "C" {
 
 nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream, nufft_plan_t* plan) {
@@ -510,11 +625,16 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     *plan = nullptr;
     if (N < 1 || N > ((int64_t)1 << 28)) return fail(NUFFT_ERR_ARG, "N = %lld out of range [1, 2^28]", (long long)N);
     if (!x) return fail(NUFFT_ERR_ARG, "null node pointer");
-    if (prec != NUFFT_FP32 && prec != NUFFT_FP64) return fail(NUFFT_ERR_ARG, "precision %d is not NUFFT_FP32/NUFFT_FP64", prec);
+    const bool refine = (prec & NUFFT_REFINE) != 0;
+    prec &= ~NUFFT_REFINE;
+    if (prec != NUFFT_FP32 && prec != NUFFT_FP64)
+        return fail(NUFFT_ERR_ARG, "precision %d is not NUFFT_FP32/NUFFT_FP64 (optionally | NUFFT_REFINE)", prec);
     if (!(tol > 0.0) || !std::isfinite(tol) || tol > 0.1) return fail(NUFFT_ERR_ARG, "tol %g out of range (0, 0.1]", tol);
     Params prm;
     nufft_status st = choose_params(N, tol, prec, prm);
     if (st != NUFFT_OK) return st;
+    prm.refine = refine;
+    if (refine) prm.halo = std::max(prm.ks_solve.w, prm.ks_plan.w);
     int dev = 0;
     NUFFT_CUDA_TRY(cudaGetDevice(&dev));
     init_pool_once();
@@ -566,6 +686,20 @@ nufft_status nufft_fwd1(nufft_plan_t plan, const void* a, void* A, int64_t batch
 }
 nufft_status nufft_fwd2(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream) {
     return run_public(plan, OP_FWD2, c, f, batch, stream);
+}
+
+nufft_status nufft_fwd2_deriv(nufft_plan_t plan, const void* c, void* f, int64_t batch, nufft_stream_t stream) {
+    return run_public(plan, OP_FWD2D, c, f, batch, stream);
+}
+
+nufft_status nufft_inv5_grad_nodes(nufft_plan_t plan, const void* u, const void* S, int64_t batch, double* grad_x,
+                                   nufft_stream_t stream) {
+    return grad_nodes_public(plan, 5, u, S, batch, grad_x, stream);
+}
+
+nufft_status nufft_inv4_grad_nodes(nufft_plan_t plan, const void* w, const void* a, int64_t batch, double* grad_x,
+                                   nufft_stream_t stream) {
+    return grad_nodes_public(plan, 4, w, a, batch, grad_x, stream);
 }
 
 nufft_status nufft_destroy(nufft_plan_t plan) {

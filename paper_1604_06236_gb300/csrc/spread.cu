@@ -322,7 +322,7 @@ __global__ void k_select(const c2<T>* __restrict__ in, int64_t n, c2<T>* __restr
 
 template <typename T>
 __global__ void k_place(const c2<T>* __restrict__ in, int64_t in_bs, int64_t P, int64_t K0, const T* __restrict__ fac,
-                        c2<T>* __restrict__ out, int64_t n, int64_t batch) {
+                        c2<T>* __restrict__ out, int64_t n, int64_t batch, int deriv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * batch) return;
     const int64_t b = i / n, gidx = i - b * n;
@@ -330,7 +330,11 @@ __global__ void k_place(const c2<T>* __restrict__ in, int64_t in_bs, int64_t P, 
     const int64_t kc = gidx < n - K0 ? gidx : gidx - n;
     const int64_t k = kc + K0;
     c2<T> v = mk<T>(0, 0);
-    if (k >= 0 && k < P) v = cscale(in[b * in_bs + k], fac[k]);
+    if (k >= 0 && k < P) {
+        v = cscale(in[b * in_bs + k], fac[k]);
+        // derivative coefficients: times j 2 pi k (d/dt of e^{j 2 pi k t})
+        if (deriv) v = cscale(cmulj(v, 1), (T)(6.283185307179586476925286766559 * (double)k));
+    }
     out[i] = v;
 }
 
@@ -346,7 +350,76 @@ __global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* 
     out[b * out_bs + k] = v;
 }
 
+// refinement helpers: widen to float64; r = in - y (in float64, stored in T); out += c
+template <typename T>
+__global__ void k_widen(const c2<T>* __restrict__ in, double2* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { const c2<T> v = in[i]; out[i] = make_double2((double)v.x, (double)v.y); }
+}
+template <typename T>
+__global__ void k_residual(const c2<T>* __restrict__ in, const double2* __restrict__ y, c2<T>* __restrict__ r,
+                           int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const c2<T> v = in[i];
+        const double2 w = y[i];
+        r[i] = mk<T>((T)((double)v.x - w.x), (T)((double)v.y - w.y));
+    }
+}
+template <typename T>
+__global__ void k_accumulate(c2<T>* __restrict__ out, const c2<T>* __restrict__ c, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cadd(out[i], c[i]);
+}
+
+// node gradient: out[q] = scale * sum_b Re(conj(X[b][q]) Y[b][q]), accumulated in float64
+template <typename T>
+__global__ void k_grad_nodes(const c2<T>* __restrict__ X, const c2<T>* __restrict__ Y, int64_t N, int64_t batch,
+                             double scale, double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    double acc = 0.0;
+    for (int64_t b = 0; b < batch; ++b) {
+        const c2<T> x = X[b * N + q], y = Y[b * N + q];
+        acc += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
+    }
+    out[q] = scale * acc;
+}
+
 }  // namespace
+
+template <typename T>
+void launch_widen(const c2<T>* in, double2* out, int64_t n, cudaStream_t s) {
+    Launch L(s, K_POINTWISE, n * (sizeof(c2<T>) + 16.0), sizeof(T) == 8);
+    k_widen<T><<<nblk(n), kTB, 0, s>>>(in, out, n);
+}
+template <typename T>
+void launch_residual(const c2<T>* in, const double2* y, c2<T>* r, int64_t n, cudaStream_t s) {
+    Launch L(s, K_POINTWISE, n * (2.0 * sizeof(c2<T>) + 16.0), sizeof(T) == 8);
+    k_residual<T><<<nblk(n), kTB, 0, s>>>(in, y, r, n);
+}
+template <typename T>
+void launch_accumulate(c2<T>* out, const c2<T>* c, int64_t n, cudaStream_t s) {
+    Launch L(s, K_POINTWISE, n * 3.0 * sizeof(c2<T>), sizeof(T) == 8);
+    k_accumulate<T><<<nblk(n), kTB, 0, s>>>(out, c, n);
+}
+#define INST_R(T)                                                                         \
+    template void launch_widen<T>(const c2<T>*, double2*, int64_t, cudaStream_t);         \
+    template void launch_residual<T>(const c2<T>*, const double2*, c2<T>*, int64_t, cudaStream_t); \
+    template void launch_accumulate<T>(c2<T>*, const c2<T>*, int64_t, cudaStream_t);
+INST_R(float)
+INST_R(double)
+#undef INST_R
+
+template <typename T>
+void launch_grad_nodes(const c2<T>* X, const c2<T>* Y, int64_t N, int64_t batch, double scale, double* out,
+                       cudaStream_t s) {
+    Launch L(s, K_POINTWISE, 2.0 * batch * N * sizeof(c2<T>) + 8.0 * N, sizeof(T) == 8);
+    k_grad_nodes<T><<<nblk(N), kTB, 0, s>>>(X, Y, N, batch, scale, out);
+}
+template void launch_grad_nodes<float>(const float2*, const float2*, int64_t, int64_t, double, double*, cudaStream_t);
+template void launch_grad_nodes<double>(const double2*, const double2*, int64_t, int64_t, double, double*,
+                                        cudaStream_t);
 
 void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s) {
     Launch L(s, K_GEOMETRY, 16.0 * N);
@@ -401,20 +474,23 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
                    c2<T>* grid, int64_t batch, cudaStream_t s) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* ef = FracPtr<T>::ext(g);
+    // the extended list may carry a wider halo (g.w >= ks.w): cell starts are
+    // indexed by cell + g.w/2, so shift them to cell + ks.w/2
+    const int* cs = g.cstart + (g.w - ks.w) / 2;
     const double es = sizeof(c2<T>);
     Launch L(s, K_SPREAD, (src ? batch * g.N * es : 0.0) + g.N * (es + 8.0 + sizeof(T)) + 4.0 * (g.n + g.w) +
                               batch * g.n * es, sizeof(T) == 8);
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
-        k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch);
     } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
-        k_spread<T, 4><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        k_spread<T, 4><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch);
     } else {
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
-        k_spread<T, 8><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, g.cstart, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        k_spread<T, 8><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch);
     }
 }
@@ -446,9 +522,9 @@ void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64
 
 template <typename T>
 void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out, int64_t n,
-                  int64_t batch, cudaStream_t s) {
+                  int64_t batch, cudaStream_t s, bool deriv) {
     Launch L(s, K_PLACE, batch * (P + n) * sizeof(c2<T>) + P * sizeof(T), sizeof(T) == 8);
-    k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch);
+    k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch, deriv ? 1 : 0);
 }
 
 template <typename T>
@@ -467,7 +543,7 @@ void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs
     template void launch_select<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, int64_t, const T*, int64_t, \
                                    cudaStream_t);                                                                \
     template void launch_place<T>(const c2<T>*, int64_t, int64_t, int64_t, const T*, c2<T>*, int64_t, int64_t,  \
-                                  cudaStream_t);                                                                 \
+                                  cudaStream_t, bool);                                                           \
     template void launch_pointwise<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, const c2<T>*, const T*,  \
                                       int64_t, cudaStream_t);
 INST(float)

@@ -63,6 +63,15 @@ def test_equispaced_reduces_to_dft(P):
     np.testing.assert_allclose(oracle.inv4(x, a), np.fft.ifft(a), rtol=0, atol=1e-13)
 
 
+def test_type1_at_matches_type1():
+    P = 40
+    x = synth.jittered_nodes(P, 0.45, seed=71)
+    a = synth.cn01(P, seed=72)
+    ks = np.array([0, 3, 39, 7, 1000, -5])
+    full = oracle.type1(x, a, k0=-5, M=1006)
+    np.testing.assert_allclose(oracle.type1_at(x, a, ks), full[ks + 5], atol=1e-12)
+
+
 @pytest.mark.parametrize("P", [1, 3, 5, 12])
 def test_brute_force_python(P):
     """Pure-Python double loops with cmath.exp (no exact phases) vs the oracle."""
@@ -186,3 +195,33 @@ def test_lagrange_factorisation_identities(P, gamma):
     np.testing.assert_allclose(K * (cauchy @ s), s_shift, rtol=1e-10, atol=1e-10 * np.abs(s_shift).max())
     h1 = (np.exp(2j * np.pi * np.subtract.outer(q / P, t)[:, :, None] * m[None, None, :]) * rho ** m).sum(-1)
     np.testing.assert_allclose(w[None, :] * h1, cauchy, rtol=1e-10, atol=1e-12 * np.abs(cauchy).max())
+
+
+@pytest.mark.parametrize("which", ["inv5", "inv4"])
+def test_vjp_against_finite_differences(which):
+    """The oracle's gradients of L = ||inv(x, d) - c_t||^2 against central
+    differences of the oracle itself (h = 1e-6 in x, and in Re/Im of d)."""
+    P = 24
+    x = synth.jittered_nodes(P, 0.45, seed=31)
+    d = synth.cn01(P, seed=32)
+    ct = synth.cn01(P, seed=33)
+    solve = oracle.inv5 if which == "inv5" else oracle.inv4
+    vjp = oracle.inv5_vjp if which == "inv5" else oracle.inv4_vjp
+
+    def loss(xx, dd):
+        r = solve(xx, dd) - ct
+        return float(np.vdot(r, r).real)
+
+    g_out = 2 * (solve(x, d) - ct)
+    g_d, g_x = vjp(x, d, g_out)
+    h = 1e-6
+    for q in (0, 5, 11, 23):
+        e = np.zeros(P)
+        e[q] = h
+        fd = (loss(x + e, d) - loss(x - e, d)) / (2 * h)
+        assert abs(fd - g_x[q]) <= 1e-6 * max(1.0, abs(fd)), (q, fd, g_x[q])
+        ed = np.zeros(P, complex)
+        ed[q] = h
+        fdr = (loss(x, d + ed) - loss(x, d - ed)) / (2 * h)
+        fdi = (loss(x, d + 1j * ed) - loss(x, d - 1j * ed)) / (2 * h)
+        assert abs(fdr + 1j * fdi - g_d[q]) <= 1e-6 * max(1.0, abs(g_d[q]))
