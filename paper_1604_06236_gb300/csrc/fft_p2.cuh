@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
                                                                const c2<T>* __restrict__ lo,
                                                                const c2<T>* __restrict__ hi, int dir) {
     using G = Cfg<T, R1, R2>;
-    constexpr int R = G::R, C = G::C, TH = G::TH, PR = G::PR, NB = G::NB;
+    constexpr int C = G::C, TH = G::TH, PR = G::PR, NB = G::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c2<T>* sm = reinterpret_cast<c2<T>*>(smem_raw);
     const int tid = threadIdx.x;

@@ -143,14 +143,18 @@ void launch_grad_nodes(const c2<T>* X, const c2<T>* Y, int64_t N, int64_t batch,
 struct GLRule { int nq; double z[48]; double wq[48]; };
 void gauss_legendre_half(int nq, GLRule& r);   // nodes in (0,1), weights for int_0^1 of an even function
 // tables over k < M: mode 0: 1/phihat((k-K0)/n); 1: rho^k/phihat; 2: rho^-k/(P phihat);
-// 3: Lambda_k/phihat, Lambda_k = -rho^k/k; 4: rho^k; 5: rho^-k/P
+// 3: Lambda_k/phihat, Lambda_k = -rho^k/k; 4: rho^k; 5: rho^-k/P;
+// 6: Lambda_k/phihat((k mod P) - K0)
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s);
 // out[i] = e^{sign j 2 pi K0 t_{perm[i]}}, i < (count_dev ? *count_dev : cap)
 void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
                 double2* out, cudaStream_t s);
-void launch_fold(const double2* B, int64_t nR, int64_t K0R, const double* fac, int64_t P, int eta, double2* Y,
+// Y_m = sum_{r<eta} fac[P r + m] B[r n + (m - K0) mod n]
+void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s);
+// out[r][p] = e^{-j 2 pi P r t_p}, r < eta
+void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, double2* out, cudaStream_t s);
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
                            cudaStream_t s);
 void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s);

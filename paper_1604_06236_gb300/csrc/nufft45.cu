@@ -86,7 +86,7 @@ struct Params {
     double gamma = 0, a = 0, rho = 0, log_rho = 0, rhoP = 0;
     int eta = 0;
     int64_t R = 0;
-    int64_t ns = 0, nR = 0;
+    int64_t ns = 0;
     int64_t K0s = 0, K0R = 0;
     KernelShape ks_solve{0, 0}, ks_plan{0, 0};
     bool refine = false;   // one refinement step per inverse (Sec. V)
@@ -139,10 +139,9 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
     p.ks_plan = es_shape(w_plan);
     const int wmax = std::max(w_solve, w_plan);
     p.ns = grid_size(std::max<int64_t>(2 * N, 2 * wmax));
-    p.nR = grid_size(std::max<int64_t>(2 * p.R, 2 * wmax));
     p.K0s = N / 2;
     p.K0R = p.R / 2;
-    p.halo = w_solve;
+    p.halo = wmax;   // the plan's float64 transforms (width w_plan) share the transforms' node list
     return NUFFT_OK;
 }
 
@@ -150,9 +149,9 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
 struct Tables {
     Params prm;
     FFTPlan fft_ns, fft_P;          // solve precision
-    FFTPlan fft_ns64, fft_P64, fft_nR64;
+    FFTPlan fft_ns64, fft_P64;
     // float64 plan tables
-    double* fold = nullptr;         // Lambda_k / phihat_R, k < R
+    double* fold = nullptr;         // Lambda_k / phihat((k mod P) - K0), k < R
     double* plan_place = nullptr;   // 1/phihat (plan width, grid ns), k < P
     double* sneg64 = nullptr;       // rho^-k / P
     // solve tables, solve precision
@@ -196,11 +195,10 @@ static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& ou
     if ((st = fft_make(t->fft_P, P, sp, s)) != NUFFT_OK) return st;
     if ((st = fft_make(t->fft_ns64, prm.ns, 2, s)) != NUFFT_OK) return st;
     if ((st = fft_make(t->fft_P64, P, 2, s)) != NUFFT_OK) return st;
-    if ((st = fft_make(t->fft_nR64, prm.nR, 2, s)) != NUFFT_OK) return st;
     GLRule glR, glS;
     gauss_legendre_half(2 + (3 * prm.ks_plan.w) / 2 + 4, glR);
     gauss_legendre_half(2 + (3 * prm.ks_solve.w) / 2 + 4, glS);
-    launch_table(prm.ks_plan, glR, prm.nR, prm.K0R, prm.R, prm.log_rho, 3, P, t->fold, nullptr, s);
+    launch_table(prm.ks_plan, glR, prm.ns, prm.K0s, prm.R, prm.log_rho, 6, P, t->fold, nullptr, s);
     launch_table(prm.ks_plan, glR, prm.ns, prm.K0s, P, prm.log_rho, 0, P, t->plan_place, nullptr, s);
     launch_table(prm.ks_plan, glR, prm.ns, prm.K0s, P, prm.log_rho, 5, P, t->sneg64, nullptr, s);
     const bool d = prm.prec == NUFFT_FP64;
@@ -245,8 +243,8 @@ struct nufft_plan_s {
     void* wt5_ext = nullptr;         // w e^{-j 2 pi K0 t}
     void* wt2_srt = nullptr;         // e^{+j 2 pi K0 t}, sorted slot order
     void* wt4_srt = nullptr;         // w e^{+j 2 pi K0 t}
-    double2* modm64_ext = nullptr;   // float64 e^{-j 2 pi K0 t} (refinement residuals)
-    double2* modp64_srt = nullptr;   // float64 e^{+j 2 pi K0 t}
+    double2* modm64_ext = nullptr;   // float64 e^{-j 2 pi K0 t}, extended slot order
+    double2* modp64_srt = nullptr;   // float64 e^{+j 2 pi K0 t}, sorted slot order
     int64_t chunk = 1;
 };
 
@@ -281,7 +279,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     z.add<double2>(P); z.add<double2>(N); z.add<double2>(N);
     z.add<char>(es * P);
     z.add<char>(es * 2 * N); z.add<char>(es * 2 * N); z.add<char>(es * N); z.add<char>(es * N);
-    if (prm.refine) { z.add<double2>(2 * N); z.add<double2>(N); }
+    z.add<double2>(2 * N); z.add<double2>(N);
     nufft_status st = pl->mem.reserve(z.used, s);
     if (st != NUFFT_OK) return st;
     Arena& m = pl->mem;
@@ -301,54 +299,47 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     pl->wt5_ext = m.take<char>(es * 2 * N);
     pl->wt2_srt = m.take<char>(es * N);
     pl->wt4_srt = m.take<char>(es * N);
-    if (prm.refine) {
-        pl->modm64_ext = m.take<double2>(2 * N);
-        pl->modp64_srt = m.take<double2>(N);
-    }
+    pl->modm64_ext = m.take<double2>(2 * N);
+    pl->modp64_srt = m.take<double2>(N);
 
     // temporaries of the plan
-    Geometry gR;
+    const int eta = prm.eta;
     Sizer zt;
-    const int64_t geo_ints = std::max(geometry_scratch_ints(N, prm.nR), geometry_scratch_ints(N, prm.ns));
+    const int64_t geo_ints = geometry_scratch_ints(N, prm.ns);
     zt.add<int>(geo_ints);
-    zt.add<int>(N); zt.add<int>(N); zt.add<double>(N);
-    zt.add<int>(2 * N); zt.add<int>(2 * N); zt.add<double>(2 * N);
-    zt.add<int>(prm.nR + prm.ks_plan.w + 1); zt.add<int>(1);
-    zt.add<double2>(2 * N);                                   // plan strengths
-    zt.add<double2>(prm.nR); zt.add<double2>(fft_work_elems(tab.fft_nR64));
+    zt.add<double2>((size_t)eta * N);                                    // strengths
+    zt.add<double2>((size_t)eta * prm.ns);                               // grids
+    zt.add<double2>((size_t)eta * fft_work_elems(tab.fft_ns64));
     zt.add<double2>(P); zt.add<double2>(fft_work_elems(tab.fft_P64));
-    zt.add<double2>(prm.ns); zt.add<double2>(fft_work_elems(tab.fft_ns64));
-    zt.add<double2>(N);                                       // modulation, sorted order
     zt.add<unsigned long long>(1);
     Arena tmp;
     if ((st = tmp.reserve(zt.used, s)) != NUFFT_OK) return st;
     int* geo = tmp.take<int>(geo_ints);
-    gR.srt_perm = tmp.take<int>(N); gR.srt_cell = tmp.take<int>(N); gR.srt_frac = tmp.take<double>(N);
-    gR.ext_perm = tmp.take<int>(2 * N); gR.ext_cell = tmp.take<int>(2 * N); gR.ext_frac = tmp.take<double>(2 * N);
-    gR.cstart = tmp.take<int>(prm.nR + prm.ks_plan.w + 1);
-    gR.dup_flag = tmp.take<int>(1);
-    double2* strR = tmp.take<double2>(2 * N);
-    double2* gridR = tmp.take<double2>(prm.nR);
-    double2* workR = tmp.take<double2>(fft_work_elems(tab.fft_nR64));
+    double2* str = tmp.take<double2>((size_t)eta * N);
+    double2* grid = tmp.take<double2>((size_t)eta * prm.ns);
+    double2* gwork = tmp.take<double2>((size_t)eta * fft_work_elems(tab.fft_ns64));
     double2* vecP = tmp.take<double2>(P);
     double2* workP = tmp.take<double2>(fft_work_elems(tab.fft_P64));
-    double2* gridS = tmp.take<double2>(prm.ns);
-    double2* workS = tmp.take<double2>(fft_work_elems(tab.fft_ns64));
-    double2* modp = tmp.take<double2>(N);
     unsigned long long* sumT = tmp.take<unsigned long long>(1);
 
     // nodes: exact turns; sum t_p mod 1 for the constant phase of Eq. 29
     launch_canon(x_dev, N, pl->T, s);
     launch_sum_turns(pl->T, N, sumT, s);
-    // geometry of the length-R type-1 grid and of the transforms' grid
-    if ((st = build_geometry(gR, pl->T, N, prm.nR, prm.ks_plan.w, false, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
-    // v(q/P) (Eqs. 13, 19, 28): type-1 of unit strengths for k = 0..R-1,
-    // centred at K0R by the strengths e^{-j 2 pi K0R t_p}, folded by Eq. 7
-    launch_mod(pl->T, gR.ext_perm, 2 * N, gR.cstart + (prm.nR + prm.ks_plan.w), (uint64_t)prm.K0R, -1, strR, s);
-    launch_spread<double>(gR, prm.ks_plan, nullptr, 0, strR, gridR, 1, s);
-    double2* BR = nullptr;
-    if ((st = fft_exec<double>(tab.fft_nR64, gridR, workR, 1, -1, s, &BR)) != NUFFT_OK) { tmp.release(); return st; }
-    launch_fold(BR, prm.nR, prm.K0R, tab.fold, P, prm.eta, vecP, s);
+    // cell-sorted geometry on the transforms' grid (halo for the wider width)
+    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.halo, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
+    const int* ext_count = gs.cstart + (prm.ns + prm.halo);
+    launch_mod(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->modm64_ext, s);
+    launch_mod(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->modp64_srt, s);
+    // v(q/P) (Eqs. 13, 19, 28): the type-1 of unit strengths at k = P r + m,
+    // k < R = eta P, is the type-1 at m < P of the strengths
+    // e^{-j 2 pi P r t_p}, r < eta (one spread of eta right-hand sides and a
+    // batched FFT on the transforms' grid), folded by Eq. 7 with Eq. 41's
+    // coefficients and the deconvolution
+    launch_plan_strengths(pl->T, N, (uint64_t)P, eta, str, s);
+    launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s);
+    double2* B = nullptr;
+    if ((st = fft_exec<double>(tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
+    launch_fold(B, prm.ns, prm.K0s, tab.fold, P, eta, vecP, s);
     double2* v = nullptr;
     if ((st = fft_exec<double>(tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
     // K_q (Eq. 29)
@@ -361,20 +352,12 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     double2* dco = (F == vecP) ? workP : vecP;
     launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
     // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
-    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.halo, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
-    launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, gridS, prm.ns, 1, s);
-    double2* gs_sp = nullptr;
-    if ((st = fft_exec<double>(tab.fft_ns64, gridS, workS, 1, +1, s, &gs_sp)) != NUFFT_OK) { tmp.release(); return st; }
-    launch_mod(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, modp, s);
-    launch_interp<double>(gs, prm.ks_plan, gs_sp, modp, pl->D64, N, 1, s);
+    launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
+    double2* gsp = nullptr;
+    if ((st = fft_exec<double>(tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
+    launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
     launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
-    const int* ext_count = gs.cstart + (prm.ns + prm.halo);
-    if (prm.refine) {
-        // float64 modulations for the residual transforms of the refinement
-        NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->modp64_srt, modp, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
-        launch_mod(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->modm64_ext, s);
-    }
     if (f32) {
         launch_slot_weights<float>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
                                    (float2*)pl->wt1_ext, (float2*)pl->wt5_ext, s);
@@ -717,7 +700,7 @@ nufft_status nufft_plan_info(nufft_plan_t plan, nufft_plan_info_t* info) {
     info->N = p.N; info->prec = p.prec; info->tol = p.tol;
     info->gamma = p.gamma; info->a = p.a; info->rho = p.rho;
     info->eta = p.eta; info->R = p.R;
-    info->grid_solve = p.ns; info->grid_plan = p.nR;
+    info->grid_solve = p.ns; info->grid_plan = p.ns;
     info->w_solve = p.ks_solve.w; info->w_plan = p.ks_plan.w;
     info->beta_solve = p.ks_solve.beta; info->beta_plan = p.ks_plan.beta;
     info->batch_chunk = plan->chunk;

@@ -26,7 +26,8 @@ __device__ double phihat(double xi, int w, double beta, const GLRule& gl) {
 }
 
 // mode 0: 1/phihat; 1: rho^k/phihat; 2: rho^-k/(P phihat); 3: Lambda_k/phihat with
-// Lambda_k = -rho^k/k (Lambda_0 = 0, Eq. 41); 4: rho^k; 5: rho^-k/P
+// Lambda_k = -rho^k/k (Lambda_0 = 0, Eq. 41); 4: rho^k; 5: rho^-k/P;
+// 6: Lambda_k / phihat((k mod P) - K0), the fold of Eq. 7 over k = P r + m
 __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                         int64_t P, double* out_d, float* out_f) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,7 +35,10 @@ __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, in
     double v;
     if (mode == 4) v = exp((double)k * log_rho);
     else if (mode == 5) v = exp(-(double)k * log_rho) / (double)P;
-    else {
+    else if (mode == 6) {
+        const double ph = phihat((double)(k % P - K0) / (double)n, w, beta, gl);
+        v = k == 0 ? 0.0 : -exp((double)k * log_rho) / ((double)k * ph);
+    } else {
         const double ph = phihat((double)(k - K0) / (double)n, w, beta, gl);
         if (mode == 0) v = 1.0 / ph;
         else if (mode == 1) v = exp((double)k * log_rho) / ph;
@@ -55,20 +59,31 @@ __global__ void k_mod(const uint64_t* __restrict__ T, const int* __restrict__ pe
 }
 
 // Eq. 7 with Lambda = g's coefficients (Eq. 41), the deconvolution folded in:
-//   Y_m = sum_{r < eta} fac[P r + m] B[(P r + m - K0R) mod nR]
-__global__ void k_fold(const double2* __restrict__ B, int64_t nR, int64_t K0R, const double* __restrict__ fac,
+//   Y_m = sum_{r < eta} fac[P r + m] B_r[(m - K0) mod n],
+// B_r the spectrum of the strengths e^{-j 2 pi P r t_p} (grid n)
+__global__ void k_fold(const double2* __restrict__ B, int64_t n, int64_t K0, const double* __restrict__ fac,
                        int64_t P, int eta, double2* __restrict__ Y) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P) return;
     double2 acc = make_double2(0.0, 0.0);
+    const int64_t src = imod(m - K0, n);
     for (int r = 0; r < eta; ++r) {
         const int64_t k = P * r + m;
-        const double2 b = B[imod(k - K0R, nR)];
+        const double2 b = B[r * n + src];
         const double f = fac[k];
         acc.x = fma(f, b.x, acc.x);
         acc.y = fma(f, b.y, acc.y);
     }
     Y[m] = acc;
+}
+
+// strengths of the log-kernel type-1: out[r][p] = e^{-j 2 pi P r t_p}, r < eta
+__global__ void k_plan_strengths(const uint64_t* __restrict__ T, int64_t N, uint64_t P, int eta,
+                                 double2* __restrict__ out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const uint64_t t = T[p];
+    for (int r = 0; r < eta; ++r) out[(int64_t)r * N + p] = cis_turns(P * (uint64_t)r * t, -1);
 }
 
 // Eq. 29: K_q = exp(j P pi + j 2 pi sum_p t_p + v_q).  The constant phase is the
@@ -183,10 +198,15 @@ void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* coun
     k_mod<<<nblk(cap), kTB, 0, s>>>(T, perm, cap, count_dev, K0, sign, out);
 }
 
-void launch_fold(const double2* B, int64_t nR, int64_t K0R, const double* fac, int64_t P, int eta, double2* Y,
+void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, (double)eta * P * 24.0 + P * 16.0);
-    k_fold<<<nblk(P), kTB, 0, s>>>(B, nR, K0R, fac, P, eta, Y);
+    k_fold<<<nblk(P), kTB, 0, s>>>(B, n, K0, fac, P, eta, Y);
+}
+
+void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, double2* out, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, N * (8.0 + 16.0 * eta));
+    k_plan_strengths<<<nblk(N), kTB, 0, s>>>(T, N, P, eta, out);
 }
 
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
