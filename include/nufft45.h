@@ -175,6 +175,40 @@ nufft_status nufft_inv4_grad_nodes(nufft_plan_t plan, const void* w, const void*
  * complete (or ordered before that stream) when the plan is destroyed. */
 nufft_status nufft_destroy(nufft_plan_t plan);
 
+/*
+ * Batched inverses of many independent instances of uneven size in one
+ * persistent kernel launch (the paper has no counterpart: each instance is
+ * the method of Secs. III/IV, Figs. 1 and 2).  Each instance has its own
+ * nodes, size N (2 <= N <= 16384) and kind; data are complex64 and the
+ * node-dependent part is computed in float64 as in NUFFT_FP32 plans
+ * (gamma = 60, eta = 4, spreading widths 14 (plan) and 8 (transforms);
+ * relative L2 error ~1e-6 on well-conditioned nodes).  The whole pipeline
+ * (plan and inverse) runs on every nufft_batch_run, so new node values in the
+ * same buffers are picked up.
+ * nufft_batch_create: `inst` is a host array of `count` descriptors of device
+ *   buffers; the buffers must stay valid while the batch is used.  Allocates
+ *   the descriptors, per-CTA scratch and deconvolution tables (synchronises
+ *   `stream`).
+ * nufft_batch_run: two memsets and one kernel launch on `stream`; capturable
+ *   in a CUDA graph.
+ * nufft_batch_status: per-instance status of the last run (NUFFT_OK or
+ *   NUFFT_ERR_DUP_NODES), in the caller's instance order; synchronises.
+ */
+typedef struct {
+    int64_t N;
+    const double* x;   /* N nodes (radians), device */
+    const void* in;    /* N complex64: samples at the nodes (kind 5) or spectrum A(k) (kind 4), device */
+    void* out;         /* N complex64: coefficients (kind 5) or node amplitudes (kind 4), device */
+    int kind;          /* 5 or 4 */
+} nufft_instance_t;
+typedef struct nufft_batch_s* nufft_batch_t;
+
+nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, double tol, nufft_stream_t stream,
+                                nufft_batch_t* batch);
+nufft_status nufft_batch_run(nufft_batch_t batch, nufft_stream_t stream);
+nufft_status nufft_batch_status(nufft_batch_t batch, int* status, nufft_stream_t stream);
+nufft_status nufft_batch_destroy(nufft_batch_t batch);
+
 /* Parameters a plan chose (Sec. V).  rho = e^{-2 pi a}; gamma = rho^{-N}. */
 typedef struct {
     int64_t N;

@@ -13,7 +13,7 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "NufftError", "FP32", "FP64", "REFINE", "build", "library_path", "ProfileEntry", "check"]
+__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
@@ -53,6 +53,11 @@ class PlanInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("x", ctypes.c_void_p), ("inp", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("kind", ctypes.c_int)]
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -70,6 +75,12 @@ def lib():
         for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
+        L.nufft_batch_create.argtypes = [i64, ctypes.POINTER(Instance), dbl, vp, ctypes.POINTER(vp)]
+        L.nufft_batch_run.argtypes = [vp, vp]
+        L.nufft_batch_status.argtypes = [vp, vp, vp]
+        L.nufft_batch_destroy.argtypes = [vp]
+        for name in ("nufft_batch_create", "nufft_batch_run", "nufft_batch_status", "nufft_batch_destroy"):
+            getattr(L, name).restype = i32
         for name in ("nufft_inv5_grad_nodes", "nufft_inv4_grad_nodes"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp, vp]
             getattr(L, name).restype = i32
@@ -208,3 +219,47 @@ class Plan:
     def inv4_grad_nodes(self, w, a, stream=None):
         """dL/dx for a = inv4(A): w = gradient w.r.t. A (inv5 of dL/da), a the solution."""
         return self._grad_nodes("nufft_inv4_grad_nodes", w, a, stream)
+
+
+class Batch:
+    """Many independent type-5 / type-4 inverses of uneven size, one persistent
+    launch per run.  `items` is a list of (x, data, kind) with x float64 nodes
+    (N,), data complex64 (N,) on the GPU and kind 5 or 4; outputs are
+    allocated here.  run() re-plans and solves every instance."""
+
+    def __init__(self, items, tol=1e-5, stream=None):
+        import torch
+        self.keep = []
+        self.outs = []
+        arr = (Instance * len(items))()
+        for i, (x, d, kind) in enumerate(items):
+            x = x.to(torch.float64).contiguous()
+            d = d.to(torch.complex64).contiguous()
+            o = torch.empty_like(d)
+            self.keep += [x, d]
+            self.outs.append(o)
+            arr[i] = Instance(x.numel(), x.data_ptr(), d.data_ptr(), o.data_ptr(), int(kind))
+        self.count = len(items)
+        self._h = ctypes.c_void_p()
+        check(lib().nufft_batch_create(self.count, arr, float(tol), _stream_handle(stream), ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        check(lib().nufft_batch_run(self._h, _stream_handle(stream)))
+        return self.outs
+
+    def status(self, stream=None):
+        import torch
+        st = torch.empty(self.count, dtype=torch.int32)
+        check(lib().nufft_batch_status(self._h, ctypes.c_void_p(st.data_ptr()), _stream_handle(stream)))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().nufft_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

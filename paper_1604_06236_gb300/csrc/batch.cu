@@ -1,0 +1,662 @@
+// Batched type-4/5 inverses of many independent instances of uneven size in
+// one persistent kernel.
+//
+// Every CTA takes instances from a work queue (an atomic counter over the
+// descriptors, which the host orders by decreasing N) and runs the whole
+// method for one instance with all its threads: the float64 plan of Sec. III
+// (exact turns, counting sort by cell, the log-kernel type-1 as eta
+// type-1s of length N, the fold of Eq. 7, kernel samples (Eq. 29), Lagrange
+// coefficients (Eq. 43), L'(z_p) by a type-2 (Eq. 16), weights (Eqs. 27, 40))
+// followed by the float32 type-5 (Fig. 1) or type-4 (Fig. 2) inverse.
+// Stages are separated by block barriers; arrays live in a per-CTA scratch
+// slab.  Every FFT inside is a power of two: grids are rounded up to one, and
+// lengths N that are not use Bluestein's chirp-z on a power-of-two length, so
+// one table of W_{2^L} twiddles serves all instances.
+#include "internal.h"
+#include "fft_p2.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
+
+namespace nufft45 {
+namespace {
+
+constexpr int kMaxLog = 16;                 // largest power-of-two FFT inside: 2^16
+constexpr int kEta = 4;                     // log-kernel oversampling (Sec. V)
+constexpr double kGamma = 60.0;             // rho^-N (Sec. V, float32 transforms)
+constexpr int kWPlan = 14, kWSolve = 8;     // spreading widths (float64 plan, float32 transforms)
+
+struct Desc {
+    int64_t N;
+    const double* x;
+    const float2* in;
+    float2* out;
+    int kind;          // 5 or 4
+    int log_ns;        // transforms' grid 2^log_ns >= 2N
+    int log_m;         // FFT length for size-N transforms (N itself if a power of two, else Bluestein)
+    int pow2;          // N is a power of two
+    int64_t tab;       // offset of this grid's deconvolution tables
+    int64_t slot;      // index into the status array
+};
+
+struct Args {
+    const Desc* desc;
+    int count;
+    int* counter;
+    int* status;
+    char* scratch;
+    size_t scratch_per_cta;
+    const double2* tw64;     // W_{2^kMaxLog}^e
+    const float2* tw32;
+    const double* dec_plan;  // 1/phihat (plan width) per grid, centred index
+    const float* dec_solve;  // 1/phihat (transforms' width)
+    double beta_plan, beta_solve;
+};
+
+// ---------------------------------------------------------------- helpers
+template <typename X> __device__ __forceinline__ X* carve(char*& p, size_t count) {
+    X* r = reinterpret_cast<X*>(p);
+    p += (count * sizeof(X) + 255) & ~(size_t)255;
+    return r;
+}
+
+template <typename T> struct TwSel;
+template <> struct TwSel<double> { static __device__ const double2* get(const Args& a) { return a.tw64; } };
+template <> struct TwSel<float> { static __device__ const float2* get(const Args& a) { return a.tw32; } };
+
+// block-wide power-of-two Stockham FFT of length 2^logn over global scratch,
+// radix 8/4/2 stages; dir -1 forward, +1 inverse, unnormalised.  Returns the
+// buffer that holds the result.
+template <typename T>
+__device__ c2<T>* cta_fft(c2<T>* buf, c2<T>* work, int logn, int dir, const c2<T>* __restrict__ tw) {
+    const int n = 1 << logn;
+    c2<T>* src = buf;
+    c2<T>* dst = work;
+    int ns_log = 0;
+    while (ns_log < logn) {
+        const int rem = logn - ns_log;
+        const int rl = rem >= 3 ? 3 : rem;
+        const int r = 1 << rl;
+        const int nr = n >> rl;
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+            c2<T> v[8];
+            const int jm = j & ((1 << ns_log) - 1);
+            for (int k = 0; k < r; ++k) {
+                c2<T> x = src[j + k * nr];
+                if (jm && k) {
+                    // W_{Ns r}^{jm k} = W_{2^kMaxLog}^{jm k 2^(kMaxLog - log(Ns r))}
+                    c2<T> w = __ldg(&tw[(jm * k) << (kMaxLog - ns_log - rl)]);
+                    if (dir > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[k] = x;
+            }
+            if (r == 8) p2::dft_reg<8, T>(v, dir);
+            else if (r == 4) p2::dft_reg<4, T>(v, dir);
+            else p2::dft_reg<2, T>(v, dir);
+            c2<T>* d = dst + ((j >> ns_log) << (ns_log + rl)) + jm;
+            for (int m = 0; m < r; ++m) d[m << ns_log] = v[m];
+        }
+        __syncthreads();
+        c2<T>* t = src; src = dst; dst = t;
+        ns_log += rl;
+    }
+    return src;
+}
+
+// chirp c_k = e^{+j pi k^2 / N} (k^2 reduced exactly mod 2N)
+__device__ __forceinline__ double2 chirp64(int64_t k, int64_t N) {
+    const uint64_t e = ((uint64_t)k * (uint64_t)k) % (uint64_t)(2 * N);
+    double s, c;
+    sincospi((double)e / (double)N, &s, &c);
+    return make_double2(c, s);
+}
+
+// Bluestein context of one instance: chirps and filter spectra (forward: H,
+// inverse: conj(H(-k))), with the 1/M scaling folded in
+template <typename T> struct Blue {
+    const c2<T>* chirp;   // N
+    const c2<T>* H;       // M
+    c2<T>* A;             // M
+    c2<T>* W;             // M
+};
+
+// length-N DFT, dir -1: X_k = sum x_j e^{-j 2 pi jk/N}; +1 with e^{+}.
+// In place on x (N values); `w` is N (+) scratch when N is a power of two.
+template <typename T>
+__device__ void cta_dft(c2<T>* x, c2<T>* w, const Desc& d, int dir, const Blue<T>& bl, const c2<T>* tw) {
+    const int64_t N = d.N;
+    if (d.pow2) {
+        c2<T>* r = cta_fft<T>(x, w, d.log_m, dir, tw);
+        if (r != x)
+            for (int64_t i = threadIdx.x; i < N; i += blockDim.x) x[i] = r[i];
+        __syncthreads();
+        return;
+    }
+    const int64_t M = (int64_t)1 << d.log_m;
+    for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+        c2<T> v = mk<T>(0, 0);
+        if (i < N) v = dir < 0 ? cmulc(x[i], bl.chirp[i]) : cmul(x[i], bl.chirp[i]);
+        bl.A[i] = v;
+    }
+    __syncthreads();
+    c2<T>* r = cta_fft<T>(bl.A, bl.W, d.log_m, -1, tw);
+    for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+        c2<T> h = dir < 0 ? bl.H[i] : cconj(bl.H[i ? M - i : 0]);
+        r[i] = cmul(r[i], h);
+    }
+    __syncthreads();
+    c2<T>* r2 = cta_fft<T>(r, r == bl.A ? bl.W : bl.A, d.log_m, +1, tw);
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+        x[i] = dir < 0 ? cmulc(r2[i], bl.chirp[i]) : cmul(r2[i], bl.chirp[i]);
+    __syncthreads();
+}
+
+// block-wide exclusive scan of cnt[0..n) into out[0..n], out[n] = total
+__device__ void cta_scan(const int* cnt, int n, int* out, int* s_part) {
+    const int nt = blockDim.x;
+    const int per = (n + nt - 1) / nt;
+    const int a = threadIdx.x * per, b = min(n, a + per);
+    int sum = 0;
+    for (int i = a; i < b; ++i) sum += cnt[i];
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < nt; ++t) { const int v = s_part[t]; s_part[t] = acc; acc += v; }
+        out[n] = acc;
+    }
+    __syncthreads();
+    int acc = s_part[threadIdx.x];
+    for (int i = a; i < b; ++i) { const int v = cnt[i]; out[i] = acc; acc += v; }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(512) k_batch(Args a) {
+    __shared__ int s_item;
+    __shared__ int s_part[1024];
+    __shared__ unsigned long long s_sum[32];
+    char* const base = a.scratch + (size_t)blockIdx.x * a.scratch_per_cta;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= a.count) break;
+        const Desc d = a.desc[it];
+        const int64_t N = d.N;
+        const int ns = 1 << d.log_ns;
+        const int64_t M = (int64_t)1 << d.log_m;
+        const int64_t K0 = N / 2;
+        const double log_rho = -log(kGamma) / (double)N;
+        const double rhoN = 1.0 / kGamma;
+        const double* dec_p = a.dec_plan + d.tab;
+        const float* dec_s = a.dec_solve + d.tab;
+        // ---- scratch layout
+        char* p = base;
+        uint64_t* T = carve<uint64_t>(p, N);
+        int* cell = carve<int>(p, N);
+        double* frac = carve<double>(p, N);
+        int* perm = carve<int>(p, N);
+        int* cnt = carve<int>(p, ns + 1);
+        int* start = carve<int>(p, ns + 1);
+        double2* modm = carve<double2>(p, N);
+        double2* modp = carve<double2>(p, N);
+        double2* str = carve<double2>(p, (size_t)kEta * N);
+        double2* G = carve<double2>(p, (size_t)kEta * ns);
+        double2* GW = carve<double2>(p, (size_t)ns);
+        double2* v64 = carve<double2>(p, M);
+        double2* w64v = carve<double2>(p, M);
+        double2* K64 = carve<double2>(p, N);
+        double2* D64 = carve<double2>(p, N);
+        double2* chirp_d = carve<double2>(p, N);
+        double2* H_d = carve<double2>(p, M);
+        double2* A_d = carve<double2>(p, M);
+        double2* W_d = carve<double2>(p, M);
+        float2* chirp_f = carve<float2>(p, N);
+        float2* H_f = carve<float2>(p, M);
+        float2* A_f = carve<float2>(p, M);
+        float2* W_f = carve<float2>(p, M);
+        float2* K32 = carve<float2>(p, N);
+        float2* wm32 = carve<float2>(p, N);   // w e^{-+ j 2 pi K0 t} for the solve
+        float2* g32 = carve<float2>(p, ns);
+        float2* gw32 = carve<float2>(p, ns);
+        float2* vec32 = carve<float2>(p, M);
+        float2* vw32 = carve<float2>(p, M);
+        Blue<double> bd{chirp_d, H_d, A_d, W_d};
+        Blue<float> bf{chirp_f, H_f, A_f, W_f};
+
+        // ---- nodes: exact turns, their sum mod 2^64, cells on the grid
+        unsigned long long part = 0;
+        for (int64_t i = tid; i < N; i += nt) {
+            double u = d.x[i] / 6.283185307179586476925286766559;
+            u -= floor(u);
+            if (u >= 1.0) u = 0.0;
+            const uint64_t t = __double2ull_rz(u * 18446744073709551616.0);
+            T[i] = t;
+            part += t;
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if ((tid & 31) == 0) s_sum[tid >> 5] = part;
+        for (int64_t c = tid; c <= ns; c += nt) cnt[c] = 0;
+        __syncthreads();
+        unsigned long long sumT = 0;
+        for (int wv = 0; wv < (nt >> 5); ++wv) sumT += s_sum[wv];
+        for (int64_t i = tid; i < N; i += nt) {
+            const uint64_t t = T[i];
+            const int c = (int)__umul64hi(t, (uint64_t)ns);
+            cell[i] = c;
+            frac[i] = (double)(t * (uint64_t)ns) * 5.42101086242752217003726400434970855712890625e-20;
+            atomicAdd(&cnt[c], 1);
+            modm[i] = cis_turns((uint64_t)K0 * t, -1);
+            modp[i] = cis_turns((uint64_t)K0 * t, +1);
+            for (int r = 0; r < kEta; ++r)
+                str[(int64_t)r * N + i] = cmul(cis_turns((uint64_t)N * (uint64_t)r * t, -1), modm[i]);
+        }
+        __syncthreads();
+        cta_scan(cnt, ns, start, s_part);
+        for (int64_t c = tid; c <= ns; c += nt) cnt[c] = 0;
+        __syncthreads();
+        for (int64_t i = tid; i < N; i += nt) {
+            const int c = cell[i];
+            perm[start[c] + atomicAdd(&cnt[c], 1)] = (int)i;
+        }
+        __syncthreads();
+        // order each cell by (T, index); flag coincident neighbours
+        for (int64_t c = tid; c < ns; c += nt) {
+            const int lo = start[c], hi = start[c + 1];
+            for (int i = lo + 1; i < hi; ++i) {
+                const int q = perm[i];
+                const uint64_t tq = T[q];
+                int j = i - 1;
+                while (j >= lo && (T[perm[j]] > tq || (T[perm[j]] == tq && perm[j] > q))) { perm[j + 1] = perm[j]; --j; }
+                perm[j + 1] = q;
+            }
+        }
+        __syncthreads();
+        for (int64_t i = tid; i < N; i += nt) {
+            if (N > 1 && T[perm[i + 1 < N ? i + 1 : 0]] - T[perm[i]] < (1ull << 20)) a.status[d.slot] = NUFFT_ERR_DUP_NODES;
+        }
+
+        // ---- Bluestein chirps and filter spectra (float64, float32 copies)
+        if (!d.pow2) {
+            for (int64_t i = tid; i < M; i += nt) {
+                int64_t k = -1;
+                if (i < N) k = i; else if (i > M - N) k = M - i;
+                double2 c = make_double2(0.0, 0.0);
+                if (k >= 0) c = chirp64(k, N);
+                A_d[i] = c;
+                if (i < N) { chirp_d[i] = c; chirp_f[i] = make_float2((float)c.x, (float)c.y); }
+            }
+            __syncthreads();
+            double2* h = cta_fft<double>(A_d, W_d, d.log_m, -1, a.tw64);
+            const double invM = 1.0 / (double)M;
+            for (int64_t i = tid; i < M; i += nt) {
+                const double2 v = make_double2(h[i].x * invM, h[i].y * invM);
+                H_d[i] = v;
+                H_f[i] = make_float2((float)v.x, (float)v.y);
+            }
+            __syncthreads();
+        }
+
+        // ---- log-kernel spectrum: eta type-1s of length N on the grid (float64)
+        const double tow_p = 2.0 / kWPlan;
+        for (int g = tid; g < ns; g += nt) {
+            double2 acc[kEta];
+            for (int r = 0; r < kEta; ++r) acc[r] = make_double2(0.0, 0.0);
+            for (int j = 0; j < kWPlan; ++j) {
+                const int cu = g - kWPlan / 2 + j;                  // unwrapped cell
+                const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
+                for (int i = start[cw]; i < start[cw + 1]; ++i) {
+                    const int q = perm[i];
+                    const double ph = es_kernel<double>((double)(g - cu) - frac[q], tow_p, a.beta_plan);
+                    for (int r = 0; r < kEta; ++r) {
+                        const double2 sv = str[(int64_t)r * N + q];
+                        acc[r].x = fma(ph, sv.x, acc[r].x);
+                        acc[r].y = fma(ph, sv.y, acc[r].y);
+                    }
+                }
+            }
+            for (int r = 0; r < kEta; ++r) G[(int64_t)r * ns + g] = acc[r];
+        }
+        __syncthreads();
+        for (int r = 0; r < kEta; ++r) {
+            double2* res = cta_fft<double>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.tw64);
+            if (res != G + (int64_t)r * ns)
+                for (int g = tid; g < ns; g += nt) G[(int64_t)r * ns + g] = res[g];
+            __syncthreads();
+        }
+        // fold (Eq. 7) with Lambda_k = -rho^k / k (Eq. 41) and the deconvolution
+        for (int64_t m = tid; m < N; m += nt) {
+            const int64_t kc = m - K0;
+            const int64_t src = kc < 0 ? kc + ns : kc;
+            const double dec = dec_p[kc + ns / 2];
+            double2 acc = make_double2(0.0, 0.0);
+            for (int r = 0; r < kEta; ++r) {
+                const int64_t k = N * r + m;
+                if (k == 0) continue;
+                const double lam = -exp((double)k * log_rho) / (double)k * dec;
+                const double2 b = G[(int64_t)r * ns + src];
+                acc.x = fma(lam, b.x, acc.x);
+                acc.y = fma(lam, b.y, acc.y);
+            }
+            v64[m] = acc;
+        }
+        __syncthreads();
+        cta_dft<double>(v64, w64v, d, +1, bd, a.tw64);
+        // K_q (Eq. 29), then F = DFT(K) for Eq. 43
+        const uint64_t Cph = (uint64_t)sumT + (uint64_t)N * 0x8000000000000000ull;
+        for (int64_t q = tid; q < N; q += nt) {
+            const double2 vq = v64[q];
+            double s, c;
+            sincospi(vq.y / 3.141592653589793238462643383279502884 + 2.0 * turns_of(Cph), &s, &c);
+            const double mag = exp(vq.x);
+            const double2 k = make_double2(mag * c, mag * s);
+            K64[q] = k;
+            K32[q] = make_float2((float)k.x, (float)k.y);
+            v64[q] = k;
+        }
+        __syncthreads();
+        cta_dft<double>(v64, w64v, d, -1, bd, a.tw64);
+        // d_m = (m+1) L_{m+1}, L_k = F_k rho^-k / N (k >= 1), L_N = 1; placed on
+        // the grid with the plan's deconvolution (type-2, Eq. 16)
+        for (int g = tid; g < ns; g += nt) {
+            const int64_t kc = g < ns - K0 ? g : g - ns;
+            const int64_t m = kc + K0;
+            double2 v = make_double2(0.0, 0.0);
+            if (m >= 0 && m < N) {
+                const int64_t k = m + 1;
+                double2 L = make_double2(1.0, 0.0);
+                if (k < N) {
+                    const double sc = exp(-(double)k * log_rho) / (double)N;
+                    L = make_double2(v64[k].x * sc, v64[k].y * sc);
+                }
+                const double f = (double)k * dec_p[kc + ns / 2];
+                v = make_double2(L.x * f, L.y * f);
+            }
+            G[g] = v;
+        }
+        __syncthreads();
+        {
+            double2* gsp = cta_fft<double>(G, GW, d.log_ns, +1, a.tw64);
+            // L'(z_p) by interpolation; then w_p (Eqs. 27, 40)
+            for (int64_t i = tid; i < N; i += nt) {
+                const int c = cell[i];
+                const double f = frac[i];
+                double2 acc = make_double2(0.0, 0.0);
+                for (int m = 0; m < kWPlan; ++m) {
+                    int gi = c + 1 - kWPlan / 2 + m;
+                    gi = gi < 0 ? gi + ns : (gi >= ns ? gi - ns : gi);
+                    const double ph = es_kernel<double>((double)(m + 1 - kWPlan / 2) - f, tow_p, a.beta_plan);
+                    acc.x = fma(ph, gsp[gi].x, acc.x);
+                    acc.y = fma(ph, gsp[gi].y, acc.y);
+                }
+                const double2 Dp = cmul(acc, modp[i]);
+                D64[i] = Dp;
+                const uint64_t t = T[i];
+                const double2 e = cis_turns((uint64_t)N * t, -1);
+                const double2 z = cis_turns(t, +1);
+                const double2 h = make_double2(rhoN * e.x - 1.0, rhoN * e.y);
+                const double2 den = cmul(h, cmul(Dp, z));
+                const double nn = den.x * den.x + den.y * den.y;
+                const double2 w = make_double2(den.x / nn, -den.y / nn);
+                const double2 wm = cmul(w, d.kind == 5 ? modm[i] : modp[i]);
+                wm32[i] = make_float2((float)wm.x, (float)wm.y);
+            }
+        }
+        __syncthreads();
+
+        // ---- the float32 inverse
+        const float tow_s = 2.0f / kWSolve;
+        const float beta_s = (float)a.beta_solve;
+        if (d.kind == 5) {
+            // a_p = s_p w_p e^{-j 2 pi K0 t_p}: type-1 (gather), FFT, deconvolve x rho^k
+            for (int g = tid; g < ns; g += nt) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int j = 0; j < kWSolve; ++j) {
+                    const int cu = g - kWSolve / 2 + j;
+                    const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
+                    for (int i = start[cw]; i < start[cw + 1]; ++i) {
+                        const int q = perm[i];
+                        const float ph = es_kernel<float>((float)(g - cu) - (float)frac[q], tow_s, beta_s);
+                        const float2 sv = cmul(d.in[q], wm32[q]);
+                        acc.x = fmaf(ph, sv.x, acc.x);
+                        acc.y = fmaf(ph, sv.y, acc.y);
+                    }
+                }
+                g32[g] = acc;
+            }
+            __syncthreads();
+            float2* B = cta_fft<float>(g32, gw32, d.log_ns, -1, a.tw32);
+            for (int64_t k = tid; k < N; k += nt) {
+                const int64_t kc = k - K0;
+                const float f = (float)exp((double)k * log_rho) * dec_s[kc + ns / 2];
+                vec32[k] = cscale(B[kc < 0 ? kc + ns : kc], f);
+            }
+            __syncthreads();
+            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32);
+            for (int64_t q = tid; q < N; q += nt) vec32[q] = cmul(vec32[q], K32[q]);
+            __syncthreads();
+            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32);
+            for (int64_t m = tid; m < N; m += nt)
+                d.out[m] = cscale(vec32[m], (float)(exp(-(double)m * log_rho) / (double)N));
+            __syncthreads();
+        } else {
+            for (int64_t k = tid; k < N; k += nt) vec32[k] = cscale(d.in[k], (float)exp((double)k * log_rho));
+            __syncthreads();
+            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32);
+            for (int64_t q = tid; q < N; q += nt) vec32[q] = cmul(vec32[q], K32[q]);
+            __syncthreads();
+            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32);
+            for (int g = tid; g < ns; g += nt) {
+                const int64_t kc = g < ns - K0 ? g : g - ns;
+                const int64_t m = kc + K0;
+                float2 v = make_float2(0.f, 0.f);
+                if (m >= 0 && m < N)
+                    v = cscale(vec32[m], (float)(exp(-(double)m * log_rho) / (double)N) * dec_s[kc + ns / 2]);
+                g32[g] = v;
+            }
+            __syncthreads();
+            float2* gsp = cta_fft<float>(g32, gw32, d.log_ns, +1, a.tw32);
+            for (int64_t i = tid; i < N; i += nt) {
+                const int c = cell[i];
+                const float f = (float)frac[i];
+                float2 acc = make_float2(0.f, 0.f);
+                for (int m = 0; m < kWSolve; ++m) {
+                    int gi = c + 1 - kWSolve / 2 + m;
+                    gi = gi < 0 ? gi + ns : (gi >= ns ? gi - ns : gi);
+                    const float ph = es_kernel<float>((float)(m + 1 - kWSolve / 2) - f, tow_s, beta_s);
+                    acc.x = fmaf(ph, gsp[gi].x, acc.x);
+                    acc.y = fmaf(ph, gsp[gi].y, acc.y);
+                }
+                d.out[i] = cmul(acc, wm32[i]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_twiddle_table(int logn, double2* t64, float2* t32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1 << logn)) return;
+    double s, c;
+    sincospi(-2.0 * (double)i / (double)(1 << logn), &s, &c);
+    t64[i] = make_double2(c, s);
+    t32[i] = make_float2((float)c, (float)s);
+}
+
+size_t scratch_bytes(int64_t N, int log_ns, int log_m) {
+    const size_t ns = (size_t)1 << log_ns, M = (size_t)1 << log_m;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t s = 0;
+    s += al(8 * N) + al(4 * N) + al(8 * N) + al(4 * N) + 2 * al(4 * (ns + 1));
+    s += 2 * al(16 * N) + al(16 * kEta * N) + al(16 * kEta * ns) + al(16 * ns);
+    s += 2 * al(16 * M) + 2 * al(16 * N) + al(16 * N) + 3 * al(16 * M);
+    s += al(8 * N) + 3 * al(8 * M) + 2 * al(8 * N) + 2 * al(8 * ns) + 2 * al(8 * M);
+    return s;
+}
+
+int ceil_log2(int64_t v) {
+    int l = 0;
+    while (((int64_t)1 << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+}  // namespace nufft45
+
+using namespace nufft45;
+
+struct nufft_batch_s {
+    int count = 0;
+    Desc* desc = nullptr;            // device
+    int* counter = nullptr;
+    int* status = nullptr;
+    char* scratch = nullptr;
+    size_t scratch_per_cta = 0;
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    double* dec_plan = nullptr;
+    float* dec_solve = nullptr;
+    int grid = 0, threads = 0;
+    double tol = 0;
+};
+
+extern "C" {
+
+nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, double tol, nufft_stream_t stream,
+                                nufft_batch_t* out) {
+    if (!out) return fail(NUFFT_ERR_ARG, "null batch output pointer");
+    *out = nullptr;
+    if (count < 1 || count > (1 << 24)) return fail(NUFFT_ERR_ARG, "count %lld out of range", (long long)count);
+    if (!inst) return fail(NUFFT_ERR_ARG, "null instance array");
+    if (!(tol >= 1e-6) || tol > 0.1) return fail(tol < 1e-6 && tol > 0 ? NUFFT_ERR_ACCURACY : NUFFT_ERR_ARG,
+                                                 "batched tol %g outside [1e-6, 0.1]", tol);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Desc> h(count);
+    std::vector<int64_t> order(count);
+    for (int64_t i = 0; i < count; ++i) {
+        const nufft_instance_t& q = inst[i];
+        if (q.N < 2 || q.N > 16384) return fail(NUFFT_ERR_ARG, "instance %lld: N = %lld outside [2, 16384]",
+                                                (long long)i, (long long)q.N);
+        if (!q.x || !q.in || !q.out) return fail(NUFFT_ERR_ARG, "instance %lld: null pointer", (long long)i);
+        if (q.kind != 4 && q.kind != 5) return fail(NUFFT_ERR_ARG, "instance %lld: kind must be 4 or 5", (long long)i);
+        order[i] = i;
+    }
+    // largest instances first: the work queue then balances the tail
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return inst[a].N > inst[b].N; });
+    std::map<int, int64_t> tab_off;   // log_ns -> table offset
+    int64_t tab_total = 0;
+    size_t scratch = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const nufft_instance_t& q = inst[order[i]];
+        Desc& d = h[i];
+        d.N = q.N;
+        d.x = q.x;
+        d.in = (const float2*)q.in;
+        d.out = (float2*)q.out;
+        d.kind = q.kind;
+        d.log_ns = std::max(ceil_log2(2 * q.N), ceil_log2(2 * kWPlan));
+        d.pow2 = (q.N & (q.N - 1)) == 0;
+        d.log_m = d.pow2 ? ceil_log2(q.N) : ceil_log2(2 * q.N - 1);
+        d.slot = order[i];
+        if (!tab_off.count(d.log_ns)) { tab_off[d.log_ns] = tab_total; tab_total += (int64_t)1 << d.log_ns; }
+        d.tab = tab_off[d.log_ns];
+        scratch = std::max(scratch, scratch_bytes(d.N, d.log_ns, d.log_m));
+    }
+    nufft_batch_s* b = new nufft_batch_s();
+    b->count = (int)count;
+    b->tol = tol;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = std::max(1, sms);
+    b->threads = 512;
+    b->scratch_per_cta = (scratch + 4095) & ~(size_t)4095;
+    auto cleanup = [&](nufft_status st) { nufft_batch_destroy(b); return st; };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->desc, sizeof(Desc) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->status, sizeof(int) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->scratch, b->scratch_per_cta * b->grid)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->tw64, sizeof(double2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->tw32, sizeof(float2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->dec_plan, sizeof(double) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->dec_solve, sizeof(float) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMemcpyAsync(b->desc, h.data(), sizeof(Desc) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
+    {
+        Launch L(s, K_PLAN_TABLE, 24.0 * (1 << kMaxLog));
+        k_twiddle_table<<<(1 << kMaxLog) / 256, 256, 0, s>>>(kMaxLog, b->tw64, b->tw32);
+    }
+    // deconvolution tables per grid, indexed by the centred index k' + ns/2
+    GLRule glp, gls;
+    gauss_legendre_half(2 + (3 * kWPlan) / 2 + 4, glp);
+    gauss_legendre_half(2 + (3 * kWSolve) / 2 + 4, gls);
+    for (auto& kv : tab_off) {
+        const int64_t ns = (int64_t)1 << kv.first;
+        launch_table(KernelShape{kWPlan, 2.30 * kWPlan}, glp, ns, ns / 2, ns, 0.0, 0, ns, b->dec_plan + kv.second,
+                     nullptr, s);
+        launch_table(KernelShape{kWSolve, 2.30 * kWSolve}, gls, ns, ns / 2, ns, 0.0, 0, ns, nullptr,
+                     b->dec_solve + kv.second, s);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(cuda_fail(e, "table launch", __FILE__, __LINE__));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(cuda_fail(e, "batch set-up", __FILE__, __LINE__));
+    *out = b;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_batch_run(nufft_batch_t b, nufft_stream_t stream) {
+    if (!b) return fail(NUFFT_ERR_ARG, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    NUFFT_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), s));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(b->status, 0, sizeof(int) * b->count, s));
+    Args a;
+    a.desc = b->desc;
+    a.count = b->count;
+    a.counter = b->counter;
+    a.status = b->status;
+    a.scratch = b->scratch;
+    a.scratch_per_cta = b->scratch_per_cta;
+    a.tw64 = b->tw64;
+    a.tw32 = b->tw32;
+    a.dec_plan = b->dec_plan;
+    a.dec_solve = b->dec_solve;
+    a.beta_plan = 2.30 * kWPlan;
+    a.beta_solve = 2.30 * kWSolve;
+    {
+        Launch L(s, K_PLAN_STAGE, 0.0);
+        k_batch<<<b->grid, b->threads, 0, s>>>(a);
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+nufft_status nufft_batch_status(nufft_batch_t b, int* status, nufft_stream_t stream) {
+    if (!b || !status) return fail(NUFFT_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(status, b->status, sizeof(int) * b->count, cudaMemcpyDefault, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+nufft_status nufft_batch_destroy(nufft_batch_t b) {
+    if (!b) return NUFFT_OK;
+    cudaFree(b->desc);
+    cudaFree(b->counter);
+    cudaFree(b->status);
+    cudaFree(b->scratch);
+    cudaFree(b->tw64);
+    cudaFree(b->tw32);
+    cudaFree(b->dec_plan);
+    cudaFree(b->dec_solve);
+    delete b;
+    return NUFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+"""Batched inverses of uneven-size instances in one persistent launch.
+
+Each instance (own jittered nodes u ~ U(-0.4, 0.4), own N, type-5 or type-4)
+is checked against the oracle: Gaussian elimination for N <= 1024, known truth
+from exact-phase direct sums above.  Sizes include powers of two (direct FFT
+inside) and arbitrary N (Bluestein inside), the smallest and largest sizes the
+batch accepts, and a duplicate-node instance that must be flagged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1604_06236_gb300 as pkg  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg.build()
+    oracle.build()
+
+
+def _instances(sizes, seed):
+    g = synth.rng(seed)
+    items, truth = [], []
+    for i, N in enumerate(sizes):
+        N = int(N)
+        x = synth.jittered_nodes(N, 0.4, generator=g)
+        c = synth.cn01(N, generator=g)
+        kind = 5 if i % 2 == 0 else 4
+        data = oracle.type2(x, c) if kind == 5 else oracle.type1(x, c)
+        items.append((torch.from_numpy(x).cuda(), torch.from_numpy(data).to(torch.complex64).cuda(), kind))
+        truth.append(c)
+    return items, truth
+
+
+def test_batch_matches_oracle():
+    sizes = [2, 3, 64, 100, 128, 257, 1000, 1024, 2048, 3001, 4096, 777, 16384, 12345, 65, 5000]
+    items, truth = _instances(sizes, seed=3)
+    b = pkg.Batch(items)
+    outs = b.run()
+    torch.cuda.synchronize()
+    assert (b.status().numpy() == 0).all()
+    for (x, d, kind), o, c in zip(items, outs, truth):
+        got = o.cpu().numpy().astype(np.complex128)
+        assert oracle.rel_l2(got, c) <= TOL, (x.numel(), kind, oracle.rel_l2(got, c))
+    # a second run reuses the batch and gives the same results
+    outs2 = [o.clone() for o in outs]
+    b.run()
+    torch.cuda.synchronize()
+    for o, o2 in zip(b.outs, outs2):
+        assert torch.equal(o, o2)
+
+
+def test_batch_against_lu_on_random_data():
+    g = synth.rng(9)
+    sizes = synth.log_uniform_sizes(12, 64, 1024, generator=g)
+    items, refs = [], []
+    for i, N in enumerate(sizes):
+        N = int(N)
+        x = synth.jittered_nodes(N, 0.4, generator=g)
+        s = synth.cn01(N, generator=g).astype(np.complex64)
+        kind = 5 if i % 2 == 0 else 4
+        items.append((torch.from_numpy(x).cuda(), torch.from_numpy(s).cuda(), kind))
+        refs.append(oracle.inv5(x, s) if kind == 5 else oracle.inv4(x, s))
+    b = pkg.Batch(items)
+    outs = b.run()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert oracle.rel_l2(o.cpu().numpy().astype(np.complex128), r) <= TOL
+
+
+def test_batch_flags_duplicate_nodes():
+    items, _ = _instances([256, 300, 128], seed=5)
+    x = items[1][0].clone()
+    x[10] = x[11]
+    items[1] = (x, items[1][1], items[1][2])
+    b = pkg.Batch(items)
+    b.run()
+    st = b.status().numpy()
+    assert st[1] == 2 and st[0] == 0 and st[2] == 0
+
+
+def test_batch_under_cuda_graph():
+    items, truth = _instances([300, 4096, 100, 2000], seed=11)
+    b = pkg.Batch(items)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(stream=s)          # warm-up outside capture
+        s.synchronize()
+        for o in b.outs:
+            o.zero_()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.run(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for o, c in zip(b.outs, truth):
+        assert oracle.rel_l2(o.cpu().numpy().astype(np.complex128), c) <= TOL
