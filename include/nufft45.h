@@ -207,6 +207,13 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
                                 nufft_batch_t* batch);
 nufft_status nufft_batch_run(nufft_batch_t batch, nufft_stream_t stream);
 nufft_status nufft_batch_status(nufft_batch_t batch, int* status, nufft_stream_t stream);
+/* Autotuner: runs the batch under every launch shape (1-3 CTAs per SM, 256 or
+ * 512 threads, largest FFT radix 4 or 8), keeps the fastest (reported in
+ * *best_ms when not NULL) and caches it per (count, sum of N, largest N) for
+ * later batches of the same shape.  Synchronises; run it before capturing. */
+nufft_status nufft_batch_tune(nufft_batch_t batch, nufft_stream_t stream, double* best_ms);
+/* The launch shape in use: CTAs, threads per CTA, largest FFT radix. */
+nufft_status nufft_batch_config(nufft_batch_t batch, int* ctas, int* threads, int* max_radix);
 nufft_status nufft_batch_destroy(nufft_batch_t batch);
 
 /* Parameters a plan chose (Sec. V).  rho = e^{-2 pi a}; gamma = rho^{-N}. */

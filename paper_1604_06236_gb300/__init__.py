@@ -79,7 +79,10 @@ def lib():
         L.nufft_batch_run.argtypes = [vp, vp]
         L.nufft_batch_status.argtypes = [vp, vp, vp]
         L.nufft_batch_destroy.argtypes = [vp]
-        for name in ("nufft_batch_create", "nufft_batch_run", "nufft_batch_status", "nufft_batch_destroy"):
+        L.nufft_batch_tune.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+        L.nufft_batch_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        for name in ("nufft_batch_create", "nufft_batch_run", "nufft_batch_status", "nufft_batch_destroy",
+                     "nufft_batch_tune", "nufft_batch_config"):
             getattr(L, name).restype = i32
         for name in ("nufft_inv5_grad_nodes", "nufft_inv4_grad_nodes"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp, vp]
@@ -246,6 +249,14 @@ class Batch:
     def run(self, stream=None):
         check(lib().nufft_batch_run(self._h, _stream_handle(stream)))
         return self.outs
+
+    def tune(self, stream=None):
+        """Autotune the launch shape on this batch; returns (ms, ctas, threads, max_radix)."""
+        ms = ctypes.c_double()
+        check(lib().nufft_batch_tune(self._h, _stream_handle(stream), ctypes.byref(ms)))
+        c, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().nufft_batch_config(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(r)))
+        return ms.value, c.value, t.value, r.value
 
     def status(self, stream=None):
         import torch

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 namespace nufft45 {
@@ -54,6 +55,7 @@ struct Args {
     const double* dec_plan;  // 1/phihat (plan width) per grid, centred index
     const float* dec_solve;  // 1/phihat (transforms' width)
     double beta_plan, beta_solve;
+    int max_rl;              // largest FFT radix inside: 2^max_rl (2 or 3)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -71,14 +73,14 @@ template <> struct TwSel<float> { static __device__ const float2* get(const Args
 // radix 8/4/2 stages; dir -1 forward, +1 inverse, unnormalised.  Returns the
 // buffer that holds the result.
 template <typename T>
-__device__ c2<T>* cta_fft(c2<T>* buf, c2<T>* work, int logn, int dir, const c2<T>* __restrict__ tw) {
+__device__ c2<T>* cta_fft(c2<T>* buf, c2<T>* work, int logn, int dir, const c2<T>* __restrict__ tw, int max_rl) {
     const int n = 1 << logn;
     c2<T>* src = buf;
     c2<T>* dst = work;
     int ns_log = 0;
     while (ns_log < logn) {
         const int rem = logn - ns_log;
-        const int rl = rem >= 3 ? 3 : rem;
+        const int rl = rem >= max_rl ? max_rl : rem;
         const int r = 1 << rl;
         const int nr = n >> rl;
         for (int j = threadIdx.x; j < nr; j += blockDim.x) {
@@ -127,10 +129,10 @@ template <typename T> struct Blue {
 // length-N DFT, dir -1: X_k = sum x_j e^{-j 2 pi jk/N}; +1 with e^{+}.
 // In place on x (N values); `w` is N (+) scratch when N is a power of two.
 template <typename T>
-__device__ void cta_dft(c2<T>* x, c2<T>* w, const Desc& d, int dir, const Blue<T>& bl, const c2<T>* tw) {
+__device__ void cta_dft(c2<T>* x, c2<T>* w, const Desc& d, int dir, const Blue<T>& bl, const c2<T>* tw, int max_rl) {
     const int64_t N = d.N;
     if (d.pow2) {
-        c2<T>* r = cta_fft<T>(x, w, d.log_m, dir, tw);
+        c2<T>* r = cta_fft<T>(x, w, d.log_m, dir, tw, max_rl);
         if (r != x)
             for (int64_t i = threadIdx.x; i < N; i += blockDim.x) x[i] = r[i];
         __syncthreads();
@@ -143,13 +145,13 @@ __device__ void cta_dft(c2<T>* x, c2<T>* w, const Desc& d, int dir, const Blue<T
         bl.A[i] = v;
     }
     __syncthreads();
-    c2<T>* r = cta_fft<T>(bl.A, bl.W, d.log_m, -1, tw);
+    c2<T>* r = cta_fft<T>(bl.A, bl.W, d.log_m, -1, tw, max_rl);
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
         c2<T> h = dir < 0 ? bl.H[i] : cconj(bl.H[i ? M - i : 0]);
         r[i] = cmul(r[i], h);
     }
     __syncthreads();
-    c2<T>* r2 = cta_fft<T>(r, r == bl.A ? bl.W : bl.A, d.log_m, +1, tw);
+    c2<T>* r2 = cta_fft<T>(r, r == bl.A ? bl.W : bl.A, d.log_m, +1, tw, max_rl);
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
         x[i] = dir < 0 ? cmulc(r2[i], bl.chirp[i]) : cmul(r2[i], bl.chirp[i]);
     __syncthreads();
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 if (i < N) { chirp_d[i] = c; chirp_f[i] = make_float2((float)c.x, (float)c.y); }
             }
             __syncthreads();
-            double2* h = cta_fft<double>(A_d, W_d, d.log_m, -1, a.tw64);
+            double2* h = cta_fft<double>(A_d, W_d, d.log_m, -1, a.tw64, a.max_rl);
             const double invM = 1.0 / (double)M;
             for (int64_t i = tid; i < M; i += nt) {
                 const double2 v = make_double2(h[i].x * invM, h[i].y * invM);
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         }
         __syncthreads();
         for (int r = 0; r < kEta; ++r) {
-            double2* res = cta_fft<double>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.tw64);
+            double2* res = cta_fft<double>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.tw64, a.max_rl);
             if (res != G + (int64_t)r * ns)
                 for (int g = tid; g < ns; g += nt) G[(int64_t)r * ns + g] = res[g];
             __syncthreads();
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             v64[m] = acc;
         }
         __syncthreads();
-        cta_dft<double>(v64, w64v, d, +1, bd, a.tw64);
+        cta_dft<double>(v64, w64v, d, +1, bd, a.tw64, a.max_rl);
         // K_q (Eq. 29), then F = DFT(K) for Eq. 43
         const uint64_t Cph = (uint64_t)sumT + (uint64_t)N * 0x8000000000000000ull;
         for (int64_t q = tid; q < N; q += nt) {
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             v64[q] = k;
         }
         __syncthreads();
-        cta_dft<double>(v64, w64v, d, -1, bd, a.tw64);
+        cta_dft<double>(v64, w64v, d, -1, bd, a.tw64, a.max_rl);
         // d_m = (m+1) L_{m+1}, L_k = F_k rho^-k / N (k >= 1), L_N = 1; placed on
         // the grid with the plan's deconvolution (type-2, Eq. 16)
         for (int g = tid; g < ns; g += nt) {
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         }
         __syncthreads();
         {
-            double2* gsp = cta_fft<double>(G, GW, d.log_ns, +1, a.tw64);
+            double2* gsp = cta_fft<double>(G, GW, d.log_ns, +1, a.tw64, a.max_rl);
             // L'(z_p) by interpolation; then w_p (Eqs. 27, 40)
             for (int64_t i = tid; i < N; i += nt) {
                 const int c = cell[i];
@@ -432,27 +434,27 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 g32[g] = acc;
             }
             __syncthreads();
-            float2* B = cta_fft<float>(g32, gw32, d.log_ns, -1, a.tw32);
+            float2* B = cta_fft<float>(g32, gw32, d.log_ns, -1, a.tw32, a.max_rl);
             for (int64_t k = tid; k < N; k += nt) {
                 const int64_t kc = k - K0;
                 const float f = (float)exp((double)k * log_rho) * dec_s[kc + ns / 2];
                 vec32[k] = cscale(B[kc < 0 ? kc + ns : kc], f);
             }
             __syncthreads();
-            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32);
+            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32, a.max_rl);
             for (int64_t q = tid; q < N; q += nt) vec32[q] = cmul(vec32[q], K32[q]);
             __syncthreads();
-            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32);
+            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32, a.max_rl);
             for (int64_t m = tid; m < N; m += nt)
                 d.out[m] = cscale(vec32[m], (float)(exp(-(double)m * log_rho) / (double)N));
             __syncthreads();
         } else {
             for (int64_t k = tid; k < N; k += nt) vec32[k] = cscale(d.in[k], (float)exp((double)k * log_rho));
             __syncthreads();
-            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32);
+            cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32, a.max_rl);
             for (int64_t q = tid; q < N; q += nt) vec32[q] = cmul(vec32[q], K32[q]);
             __syncthreads();
-            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32);
+            cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32, a.max_rl);
             for (int g = tid; g < ns; g += nt) {
                 const int64_t kc = g < ns - K0 ? g : g - ns;
                 const int64_t m = kc + K0;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 g32[g] = v;
             }
             __syncthreads();
-            float2* gsp = cta_fft<float>(g32, gw32, d.log_ns, +1, a.tw32);
+            float2* gsp = cta_fft<float>(g32, gw32, d.log_ns, +1, a.tw32, a.max_rl);
             for (int64_t i = tid; i < N; i += nt) {
                 const int c = cell[i];
                 const float f = (float)frac[i];
@@ -523,9 +525,18 @@ struct nufft_batch_s {
     float2* tw32 = nullptr;
     double* dec_plan = nullptr;
     float* dec_solve = nullptr;
-    int grid = 0, threads = 0;
+    int grid = 0, threads = 0, max_rl = 3;
+    int sms = 1;
+    size_t scratch_cap = 0;          // CTAs the scratch slab can hold
     double tol = 0;
+    int64_t key_total = 0, key_max = 0;
 };
+
+namespace {
+// autotuner cache: (count, sum N, max N) -> (CTAs, threads, radix)
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t>, std::tuple<int, int, int>> g_tune;
+}
 
 extern "C" {
 
@@ -575,15 +586,26 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = std::max(1, sms);
+    b->sms = std::max(1, sms);
+    b->grid = b->sms;
     b->threads = 512;
     b->scratch_per_cta = (scratch + 4095) & ~(size_t)4095;
+    b->scratch_cap = (size_t)b->sms * 3;   // room for up to three CTAs per SM
+    int64_t tot = 0, mx = 0;
+    for (int64_t i = 0; i < count; ++i) { tot += inst[i].N; mx = std::max<int64_t>(mx, inst[i].N); }
+    b->key_total = tot;
+    b->key_max = mx;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(std::make_tuple((int64_t)count, tot, mx));
+        if (it != g_tune.end()) std::tie(b->grid, b->threads, b->max_rl) = it->second;
+    }
     auto cleanup = [&](nufft_status st) { nufft_batch_destroy(b); return st; };
     cudaError_t e;
     if ((e = cudaMalloc(&b->desc, sizeof(Desc) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->status, sizeof(int) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
-    if ((e = cudaMalloc(&b->scratch, b->scratch_per_cta * b->grid)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->scratch, b->scratch_per_cta * b->scratch_cap)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->tw64, sizeof(double2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->tw32, sizeof(float2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->dec_plan, sizeof(double) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
@@ -629,11 +651,62 @@ nufft_status nufft_batch_run(nufft_batch_t b, nufft_stream_t stream) {
     a.dec_solve = b->dec_solve;
     a.beta_plan = 2.30 * kWPlan;
     a.beta_solve = 2.30 * kWSolve;
+    a.max_rl = b->max_rl;
     {
         Launch L(s, K_PLAN_STAGE, 0.0);
         k_batch<<<b->grid, b->threads, 0, s>>>(a);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+// Autotuner: times every (CTAs per SM, threads per CTA, largest FFT radix)
+// candidate on this batch with CUDA events and keeps the fastest; the choice
+// is cached per (count, sum N, max N) for later batches of the same shape.
+nufft_status nufft_batch_tune(nufft_batch_t b, nufft_stream_t stream, double* best_ms) {
+    if (!b) return fail(NUFFT_ERR_ARG, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    NUFFT_CUDA_TRY(cudaEventCreate(&e0));
+    NUFFT_CUDA_TRY(cudaEventCreate(&e1));
+    const int keep_g = b->grid, keep_t = b->threads, keep_r = b->max_rl;
+    float best = 1e30f;
+    int bg = keep_g, bt = keep_t, br = keep_r;
+    nufft_status st = NUFFT_OK;
+    for (int per_sm = 1; per_sm <= 3 && st == NUFFT_OK; ++per_sm)
+        for (int th : {256, 512})
+            for (int rl : {2, 3}) {
+                b->grid = b->sms * per_sm;
+                b->threads = th;
+                b->max_rl = rl;
+                if ((st = nufft_batch_run(b, stream)) != NUFFT_OK) break;   // warm
+                cudaEventRecord(e0, s);
+                if ((st = nufft_batch_run(b, stream)) != NUFFT_OK) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bg = b->grid; bt = th; br = rl; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->grid = bg;
+    b->threads = bt;
+    b->max_rl = br;
+    if (st != NUFFT_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[std::make_tuple((int64_t)b->count, b->key_total, b->key_max)] = std::make_tuple(bg, bt, br);
+    }
+    if (best_ms) *best_ms = best;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_batch_config(nufft_batch_t b, int* ctas, int* threads, int* max_radix) {
+    if (!b) return fail(NUFFT_ERR_ARG, "null batch");
+    if (ctas) *ctas = b->grid;
+    if (threads) *threads = b->threads;
+    if (max_radix) *max_radix = 1 << b->max_rl;
     return NUFFT_OK;
 }
 
