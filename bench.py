@@ -464,6 +464,104 @@ def run_batched(args):
     return 0
 
 
+def _timed_steps(fn, steps, warmup, stream, flush):
+    import torch
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for i in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        fn(warmup + i)
+        ev1.record(stream)
+        ev1.synchronize()
+        total += ev0.elapsed_time(ev1)
+    return total
+
+
+def run_clustered(args):
+    """Type-5 inverse at N = 2^20 with 1% of the nodes within 0.01-0.05 grid
+    spacings of a neighbour, complex64 samples, float64 weights; plain and
+    refined (Sec. V).  Step = plan + inverse of one vector."""
+    import torch
+    import synth
+    import paper_1604_06236_gb300 as pkg
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    N = 1 << 20
+    x = torch.from_numpy(synth.clustered_nodes(N, 0.45, 0.01, 0.01, 0.05, seed=2)).to(dev)
+    f = torch.from_numpy(synth.cn01(N, seed=7)).to(torch.complex64).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, prec in (("plain", pkg.FP32), ("refined", pkg.FP32 | pkg.REFINE)):
+        def step(i):
+            p = pkg.Plan(x, prec=prec)
+            p.inv5(f)
+            p.close()
+        ms = _timed_steps(step, args.steps, args.warmup, stream, flush)
+        p = pkg.Plan(x, prec=prec)
+        def solve(i):
+            p.inv5(f)
+        ms_s = _timed_steps(solve, args.steps, args.warmup, stream, flush)
+        out[name] = {"ms_per_step": ms / args.steps, "solve_ms": ms_s / args.steps}
+    r = out["refined"]
+    result = {
+        "metric": METRIC, "value": 1.0 / (r["ms_per_step"] / 1e3), "unit": "transforms/s",
+        "mpoints_per_s": N / (r["ms_per_step"] / 1e3) / 1e6, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 transforms (complex64 data), f64 plan", "data": "synthetic",
+        "config": {"workload": "type-5 inverse, N=2^20, u~U(-0.45,0.45), 1% of nodes within 0.01-0.05 grid "
+                               "spacings of a neighbour (seed 2), plan + refined inverse per step",
+                   "l2": "512 MiB buffer written between timed steps (outside the events)"},
+        "paths": out,
+    }
+    print(json.dumps(result), flush=True)
+    return 0
+
+
+def run_autograd(args):
+    """Differentiable type-5 inverse at N = 262144, 64 instances with their own
+    nodes, complex64; loss ||c_hat - c_target||^2; forward + backward with
+    gradients w.r.t. the samples and the nodes."""
+    import torch
+    import synth
+    import paper_1604_06236_gb300 as pkg
+    from paper_1604_06236_gb300 import autograd as ag
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    N, B = 262144, args.autograd_batch
+    x = torch.from_numpy(np.stack([synth.jittered_nodes(N, 0.45, seed=4 + i) for i in range(B)])).to(dev)
+    f = torch.from_numpy(synth.cn01((B, N), seed=50)).to(torch.complex64).to(dev)
+    ct = torch.from_numpy(synth.cn01((B, N), seed=51)).to(torch.complex64).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    xr = x.clone().requires_grad_(True)
+    fr = f.clone().requires_grad_(True)
+
+    def step(i):
+        xr.grad = None
+        fr.grad = None
+        loss = (ag.inv5(fr, xr) - ct).abs().pow(2).sum()
+        loss.backward()
+    ms = _timed_steps(step, args.steps, args.warmup, stream, flush)
+    result = {
+        "metric": METRIC, "value": B / (ms / args.steps / 1e3), "unit": "transforms/s (forward + backward)",
+        "mpoints_per_s": B * N / (ms / args.steps / 1e3) / 1e6, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 transforms (complex64 data), f64 plan", "data": "synthetic",
+        "config": {"workload": "autograd type-5 inverse, N=262144, %d instances with own nodes (seeds 4+i), "
+                               "loss ||c_hat - c_target||^2, grads w.r.t. samples and nodes; plans rebuilt in "
+                               "the backward pass" % B,
+                   "l2": "512 MiB buffer written between timed steps (outside the events)"},
+    }
+    print(json.dumps(result), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,8 +573,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="main timed region only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="n65536", choices=["n65536", "batched"],
-                    help="n65536: the headline workload (default); batched: uneven-N instances")
+    ap.add_argument("--workload", default="n65536", choices=["n65536", "batched", "clustered", "autograd"],
+                    help="n65536: the headline workload (default); batched: uneven-N instances; clustered: "
+                         "N=2^20 with near-coincident nodes; autograd: forward+backward at N=262144")
+    ap.add_argument("--autograd-batch", type=int, default=64)
     ap.add_argument("--instances", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -485,6 +585,10 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "clustered":
+        return run_clustered(args)
+    if args.workload == "autograd":
+        return run_autograd(args)
     return run_gpu(args)
 
 

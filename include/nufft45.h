@@ -233,6 +233,10 @@ typedef struct {
 
 nufft_status nufft_plan_info(nufft_plan_t plan, nufft_plan_info_t* info);
 
+/* Right-hand sides processed per pass of the transforms (default: set by
+ * nufft_plan from the device's L2 size and the per-vector scratch). */
+nufft_status nufft_plan_set_batch_chunk(nufft_plan_t plan, int64_t chunk);
+
 /*
  * nufft_plan_export -- copy a node-dependent quantity of the plan, as N
  * complex128 values, into dst (device or host):

@@ -75,6 +75,8 @@ def lib():
         for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
+        L.nufft_plan_set_batch_chunk.argtypes = [vp, i64]
+        L.nufft_plan_set_batch_chunk.restype = i32
         L.nufft_batch_create.argtypes = [i64, ctypes.POINTER(Instance), dbl, vp, ctypes.POINTER(vp)]
         L.nufft_batch_run.argtypes = [vp, vp]
         L.nufft_batch_status.argtypes = [vp, vp, vp]
@@ -156,6 +158,9 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_batch_chunk(self, chunk):
+        check(lib().nufft_plan_set_batch_chunk(self._h, int(chunk)))
 
     def info(self):
         inf = PlanInfo()

@@ -109,10 +109,10 @@ static KernelShape es_shape(int w) { return KernelShape{w, 2.30 * w}; }
 // Sec. V: the truncation of Eq. 42 at R = eta P leaves a relative error close
 // to mu ~ gamma^-eta (Eq. 49 with gamma = e^{2 pi P a}); round-off in the
 // scaling by e^{2 pi p a} of Eqs. 31 and 43 grows with gamma.  float64:
-// gamma = 1000 and eta from tol; float32 transforms: gamma = 30, eta = 5, so
-// that the float64 plan is accurate to ~1e-8 and the float32 stages dominate
-// (gamma = 60, eta = 4 keeps R = 4N, so a power-of-two N gets a power-of-two
-// length-R grid).
+// gamma = 1000 and eta from tol; float32 transforms: gamma = 100, eta = 3 and
+// plan width 12, which leave the float64 plan accurate to ~1e-7 (truncation
+// 0.4 gamma^-eta ~ 4e-7, kernel error ~1e-11) while the float32 stages bring
+// ~2e-6; the plan's float64 work is what these choices keep small.
 static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
     p.N = N;
     p.prec = prec;
@@ -125,9 +125,9 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
         w_plan = w_solve = tol < 1e-8 ? 16 : 12;
     } else {
         if (tol < 1e-6) return fail(NUFFT_ERR_ACCURACY, "tol %g below what the float32 path attains (1e-6)", tol);
-        p.gamma = 60.0;
-        p.eta = 4;
-        w_plan = 14;
+        p.gamma = 100.0;
+        p.eta = 3;
+        w_plan = 12;
         w_solve = 8;
     }
     p.log_rho = -std::log(p.gamma) / (double)N;
@@ -691,6 +691,12 @@ nufft_status nufft_destroy(nufft_plan_t plan) {
     // its buffers; kernels hold no reference to the host-side object
     plan->mem.release();
     delete plan;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_plan_set_batch_chunk(nufft_plan_t plan, int64_t chunk) {
+    if (!plan || chunk < 1) return fail(NUFFT_ERR_ARG, "bad plan or chunk");
+    plan->chunk = chunk;
     return NUFFT_OK;
 }
 

@@ -125,3 +125,40 @@ def test_gradients_vs_finite_differences(kind):
         vt = torch.from_numpy(v).cuda()
         fd = (loss(x0 + h * vt, d0) - loss(x0 - h * vt, d0)) / (2 * h)
         assert abs(fd - gx @ v) <= 1e-4 * np.linalg.norm(gx)
+
+
+def test_full_size_finite_differences():
+    """The N = 262144 differentiable workload (instances with their own nodes,
+    seeds 4 + i), float64 path: central differences (h = 1e-6) on 8 node
+    coordinates and 2 random directions per instance against autograd."""
+    N, B = 262144, 2
+    x = np.stack([synth.jittered_nodes(N, 0.45, seed=4 + i) for i in range(B)])
+    f = synth.cn01((B, N), seed=50)
+    ct = synth.cn01((B, N), seed=51)
+    ctt = torch.from_numpy(ct).cuda()
+    x0 = torch.from_numpy(x).cuda()
+    f0 = torch.from_numpy(f).cuda()
+
+    def loss(xv):
+        with torch.no_grad():
+            return float((ag.inv5(f0, xv, prec=pkg.FP64) - ctt).abs().pow(2).sum().item())
+
+    xt = x0.clone().requires_grad_(True)
+    (ag.inv5(f0, xt, prec=pkg.FP64) - ctt).abs().pow(2).sum().backward()
+    gx = xt.grad.cpu().numpy()
+    h = 1e-6
+    g = synth.rng(12)
+    for b in range(B):
+        scale = np.abs(gx[b]).max()
+        for q in g.choice(N, 8, replace=False):
+            e = torch.zeros((B, N), dtype=torch.float64, device="cuda")
+            e[b, q] = h
+            fd = (loss(x0 + e) - loss(x0 - e)) / (2 * h)
+            assert abs(fd - gx[b, q]) <= 1e-3 * scale, (b, q, fd, gx[b, q])
+        for _ in range(2):
+            v = np.zeros((B, N))
+            v[b] = g.normal(size=N)
+            v /= np.linalg.norm(v)
+            vt = torch.from_numpy(v).cuda()
+            fd = (loss(x0 + h * vt) - loss(x0 - h * vt)) / (2 * h)
+            assert abs(fd - (gx * v).sum()) <= 1e-3 * np.linalg.norm(gx[b])

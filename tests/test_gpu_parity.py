@@ -5,8 +5,9 @@ Tolerances (relative L2, the paper's error measure of Sec. VI):
   * float32 path: 1e-5 for the inverses, 1e-6 for types 1, 2 (the float32
     rounding of the data is ~6e-8; spreading width 8 leaves ~4e-7);
   * plan quantities K_q, L'(z_p), w_p are always float64: 1e-10 for the
-    float64 plan (gamma = 1000, eta = 4), 1e-7 for the float32 path's plan
-    (gamma = 60, eta = 4: truncation ~0.4 gamma^-eta ~ 3e-8, Sec. V).
+    float64 plan (gamma = 1000, eta = 4), 2e-6 for the float32 path's plan
+    (gamma = 100, eta = 3: truncation ~0.4 gamma^-eta ~ 4e-7 in K, Sec. V;
+    the weights add the width-12 kernel error through L'(z_p)).
 Sizes span one to many CTA tiles and FFT passes, ragged tails, prime and
 non-smooth N (Bluestein), and the N = 65536 workload in full.
 """
@@ -26,7 +27,7 @@ import paper_1604_06236_gb300 as pkg  # noqa: E402
 FP32, FP64 = pkg.FP32, pkg.FP64
 TOL_INV = {FP32: 1e-5, FP64: 1e-10}
 TOL_FWD = {FP32: 1e-6, FP64: 1e-12}
-TOL_PLAN = {FP32: 1e-7, FP64: 1e-10}
+TOL_PLAN = {FP32: 2e-6, FP64: 1e-10}
 CDT = {FP32: torch.complex64, FP64: torch.complex128}
 
 
