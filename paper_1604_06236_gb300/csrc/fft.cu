@@ -190,6 +190,15 @@ __global__ void __launch_bounds__(kThreads) k_fft_pass(const c2<T>* in, c2<T>* o
     }
 }
 
+__global__ void k_make_twiddles_full(int64_t n, double2* out_d, float2* out_f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)i / (double)n, &s, &c);
+    if (out_d) out_d[i] = make_double2(c, s);
+    if (out_f) out_f[i] = make_float2((float)c, (float)s);
+}
+
 __global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d, double2* hi_d,
                                 float2* lo_f, float2* hi_f) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,6 +384,45 @@ nufft_status launch_p2(int rlog, const c2<T>* in, c2<T>* out, p2::Args a, const 
     return NUFFT_OK;
 }
 
+template <typename T, int A, int B>
+nufft_status launch_p2s_one(const c2<T>* in, c2<T>* out, p2::SArgs a, const c2<T>* tw, int dir, cudaStream_t s) {
+    using G = p2::SCfg<T, A, B>;
+    auto kern = p2::k_fft_p2s<T, A, B>;
+    const size_t smem = 2 * (size_t)G::R * G::C * sizeof(c2<T>);
+    static int per_sm = 0;   // resident CTAs per SM for this instantiation (device-independent enough)
+    if (!per_sm) {
+        NUFFT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        NUFFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, G::TH, smem));
+        per_sm = std::max(1, b);
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(a.ntiles, per_sm * std::max(1, sms));
+    kern<<<grid, G::TH, smem, s>>>(in, out, a, tw, dir);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template <typename T>
+nufft_status launch_p2s(int rlog, const c2<T>* in, c2<T>* out, p2::SArgs a, const c2<T>* tw, int dir,
+                        cudaStream_t s) {
+    switch (rlog) {
+        case 4: return launch_p2s_one<T, 4, 4>(in, out, a, tw, dir, s);
+        case 5: return launch_p2s_one<T, 8, 4>(in, out, a, tw, dir, s);
+        case 6: return launch_p2s_one<T, 8, 8>(in, out, a, tw, dir, s);
+        case 7: return launch_p2s_one<T, 16, 8>(in, out, a, tw, dir, s);
+        case 8: return launch_p2s_one<T, 16, 16>(in, out, a, tw, dir, s);
+        default:
+            if constexpr (sizeof(T) == 4) {
+                if (rlog == 9) return launch_p2s_one<T, 32, 16>(in, out, a, tw, dir, s);
+                if (rlog == 10) return launch_p2s_one<T, 32, 32>(in, out, a, tw, dir, s);
+            }
+            return fail(NUFFT_ERR_ARG, "no streaming pass for radix 2^%d", rlog);
+    }
+}
+
 template <typename T>
 nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
                      c2<T>** result) {
@@ -394,9 +442,27 @@ nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, i
         a.C_log = p2_C_log<T>(rl);
         a.total = (int)(batch << (L - rl));
         a.shift = p.shift;
+        a.tw_full = p.tw_full;
+        a.lop = a.sop = 0;
+        a.src = a.fac_in = a.mulc = a.fac_out = nullptr;
+        a.src_bs = a.ns = a.K0 = 0;
         {
             Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
-            nufft_status st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            const int clog = p2_C_log<T>(rl);
+            nufft_status st;
+            // float64 passes stream tiles through shared memory (their float64
+            // arithmetic is the limit; prefetching the next tile hides the loads);
+            // float32 passes load straight into registers from many resident CTAs
+            if (sizeof(T) == 8 && p.tw_full && p.p2_rlog.size() > 1 && rl >= 4 && clog <= L - rl) {
+                p2::SArgs sa;
+                sa.n_log = L;
+                sa.R_log = rl;
+                sa.Ns_log = ns_log;
+                sa.ntiles = (int)((batch << (L - rl)) >> clog);
+                st = launch_p2s<T>(rl, src, dst, sa, static_cast<const c2<T>*>(p.tw_full), dir, s);
+            } else {
+                st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            }
             if (st != NUFFT_OK) return st;
         }
         ns_log += rl;
@@ -475,7 +541,74 @@ nufft_status exec_passes(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batc
     return NUFFT_OK;
 }
 
+template <typename T>
+nufft_status exec_p2_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T>* out, int64_t batch, int dir,
+                            const FFTHooks& h, cudaStream_t s) {
+    const c2<T>* lo = static_cast<const c2<T>*>(p.tw_lo);
+    const c2<T>* hi = static_cast<const c2<T>*>(p.tw_hi);
+    int L = 0;
+    while (((int64_t)1 << L) < p.n) ++L;
+    const int k = (int)p.p2_rlog.size();
+    const c2<T>* src = in;
+    int ns_log = 0;
+    for (int i = 0; i < k; ++i) {
+        const int rl = p.p2_rlog[i];
+        c2<T>* dst = ((k - 1 - i) % 2 == 0) ? out : work;
+        p2::Args a;
+        a.n_log = L;
+        a.R_log = rl;
+        a.Ns_log = ns_log;
+        a.C_log = p2_C_log<T>(rl);
+        a.total = (int)(batch << (L - rl));
+        a.shift = p.shift;
+        a.tw_full = p.tw_full;
+        a.lop = (i == 0) ? h.lop : 0;
+        a.sop = (i == k - 1) ? h.sop : 0;
+        a.src = h.src;
+        a.src_bs = h.src_bs;
+        a.ns = h.ns;
+        a.K0 = h.K0;
+        a.fac_in = h.fac_in;
+        a.mulc = h.mulc;
+        a.fac_out = h.fac_out;
+        {
+            // algorithmic bytes: one read and one write of the vectors
+            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
+            nufft_status st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            if (st != NUFFT_OK) return st;
+        }
+        ns_log += rl;
+        src = dst;
+    }
+    return NUFFT_OK;
+}
+
 }  // namespace
+
+template <typename T>
+bool fft_hooks_supported(const FFTPlan& p) {
+    if (p.p2_rlog.size() < 2) return false;
+    int L = 0;
+    while (((int64_t)1 << L) < p.n) ++L;
+    for (int rl : p.p2_rlog)
+        if (p2_C_log<T>(rl) > L - rl) return false;
+    return true;
+}
+
+template <typename T>
+nufft_status fft_exec_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T>* out, int64_t batch, int dir,
+                             const FFTHooks& h, cudaStream_t s) {
+    if (!fft_hooks_supported<T>(p)) return fail(NUFFT_ERR_ARG, "fused FFT stages need a multi-pass power-of-two plan");
+    if (batch <= 0) return NUFFT_OK;
+    return exec_p2_hooked<T>(p, in, work, out, batch, dir, h, s);
+}
+
+template bool fft_hooks_supported<float>(const FFTPlan&);
+template bool fft_hooks_supported<double>(const FFTPlan&);
+template nufft_status fft_exec_hooked<float>(const FFTPlan&, const float2*, float2*, float2*, int64_t, int,
+                                             const FFTHooks&, cudaStream_t);
+template nufft_status fft_exec_hooked<double>(const FFTPlan&, const double2*, double2*, double2*, int64_t, int,
+                                              const FFTHooks&, cudaStream_t);
 
 bool is_smooth(int64_t n) {
     if (n < 1) return false;
@@ -490,6 +623,7 @@ int64_t next_smooth(int64_t n) {
 }
 
 FFTPlan::~FFTPlan() {
+    cudaFree(tw_full);
     cudaFree(tw_lo);
     cudaFree(tw_hi);
     cudaFree(chirp);
@@ -559,6 +693,13 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
         n, B, nhi, prec == 2 ? (double2*)p.tw_lo : nullptr, prec == 2 ? (double2*)p.tw_hi : nullptr,
         prec == 2 ? nullptr : (float2*)p.tw_lo, prec == 2 ? nullptr : (float2*)p.tw_hi);
     NUFFT_CUDA_TRY(cudaGetLastError());
+    if (n >= 2 && (n & (n - 1)) == 0 && n <= ((int64_t)1 << 24)) {
+        NUFFT_CUDA_TRY(cudaMalloc(&p.tw_full, es * n));
+        Launch Lf(s, K_PLAN_TABLE, 16.0 * n);
+        k_make_twiddles_full<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            n, prec == 2 ? (double2*)p.tw_full : nullptr, prec == 2 ? nullptr : (float2*)p.tw_full);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+    }
     return prec == 2 ? make_passes<double>(p) : make_passes<float>(p);
 }
 

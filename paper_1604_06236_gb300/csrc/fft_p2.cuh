@@ -94,6 +94,19 @@ struct Args {
     int C_log;                 // C = 2^C_log butterflies per CTA
     int total;                 // batch * n / R butterflies
     int shift;                 // two-level twiddle table split
+    const void* tw_full;       // W_n^e for all e < n, or null (then the two-level table)
+    // fused element-wise work on the first pass's loads and the last pass's
+    // stores, indexed by the element's position idx in its length-n vector:
+    //   lop 1: x = src[b * src_bs + ((idx - K0) mod ns)] * fac_in[idx]  (a
+    //          deconvolved, scaled selection from an oversampled spectrum)
+    //   lop 2: x = in[idx] * fac_in[idx];
+    //   sop 1: y *= mulc[idx];  sop 2: y *= fac_out[idx]
+    int lop, sop;
+    const void* src;
+    int64_t src_bs, ns, K0;
+    const void* fac_in;
+    const void* mulc;
+    const void* fac_out;
 };
 
 template <typename T>
@@ -102,6 +115,18 @@ __device__ __forceinline__ c2<T> tw2(const c2<T>* __restrict__ lo, const c2<T>* 
     c2<T> w = cmul(__ldg(&lo[e & ((1u << shift) - 1)]), __ldg(&hi[e >> shift]));
     if (dir > 0) w.y = -w.y;
     return w;
+}
+
+// W_n^e from the full table when there is one (one load), else two-level
+template <typename T>
+__device__ __forceinline__ c2<T> twn(const Args& a, const c2<T>* __restrict__ lo, const c2<T>* __restrict__ hi,
+                                     uint32_t e, int dir) {
+    if (a.tw_full) {
+        c2<T> w = __ldg(&static_cast<const c2<T>*>(a.tw_full)[e]);
+        if (dir > 0) w.y = -w.y;
+        return w;
+    }
+    return tw2<T>(lo, hi, a.shift, e, dir);
 }
 
 // compile-time tile: C butterflies per CTA, C * R2 threads
@@ -138,16 +163,33 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
         const int g = g0 + ca;
         const bool ok = g < a.total;
         const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
-        const c2<T>* src = in + ((size_t)b << a.n_log) + j;
+        if (a.lop == 1) {
+            const c2<T>* gsrc = static_cast<const c2<T>*>(a.src) + (size_t)b * a.src_bs;
+            const T* fac = static_cast<const T*>(a.fac_in);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1)
-            v[k1] = ok ? src[(size_t)(k1 * R2 + k2) << nR_log] : mk<T>(0, 0);
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int64_t idx = (int64_t)j + ((int64_t)(k1 * R2 + k2) << nR_log);
+                int64_t si = idx - a.K0;
+                si = si < 0 ? si + a.ns : si;
+                v[k1] = ok ? cscale(gsrc[si], __ldg(&fac[idx])) : mk<T>(0, 0);
+            }
+        } else {
+            const c2<T>* src = in + ((size_t)b << a.n_log) + j;
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1)
+                v[k1] = ok ? src[(size_t)(k1 * R2 + k2) << nR_log] : mk<T>(0, 0);
+            if (a.lop == 2) {
+                const T* fac = static_cast<const T*>(a.fac_in) + j;
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) v[k1] = cscale(v[k1], __ldg(&fac[(size_t)(k1 * R2 + k2) << nR_log]));
+            }
+        }
         const uint32_t jm = j & (Ns - 1);
         if (jm != 0) {
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) {
                 const uint32_t k = (uint32_t)(k1 * R2 + k2);
-                if (k != 0) v[k1] = cmul(v[k1], tw2<T>(lo, hi, a.shift, (jm * k) << tw_shift, dir));
+                if (k != 0) v[k1] = cmul(v[k1], twn<T>(a, lo, hi, (jm * k) << tw_shift, dir));
             }
         }
     } else {
@@ -173,7 +215,7 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
     if (k2 != 0) {
 #pragma unroll
         for (int m1 = 1; m1 < R1; ++m1)
-            v[m1] = cmul(v[m1], tw2<T>(lo, hi, a.shift, (uint32_t)(m1 * k2) << inner_shift, dir));
+            v[m1] = cmul(v[m1], twn<T>(a, lo, hi, (uint32_t)(m1 * k2) << inner_shift, dir));
     }
     {
         c2<T>* col = sm + ca * PR + k2;
@@ -202,10 +244,26 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
             const int g = g0 + c;
             if (g < a.total) {
                 const uint32_t b = (uint32_t)g >> nR_log, j = (uint32_t)g & (nR - 1);
-                c2<T>* dst = out + ((size_t)b << a.n_log) + ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) +
-                             (j & (Ns - 1));
+                const size_t o0 = ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) + (j & (Ns - 1));
+                c2<T>* dst = out + ((size_t)b << a.n_log) + o0;
+                if (a.sop == 1) {
+                    const c2<T>* mc = static_cast<const c2<T>*>(a.mulc) + o0;
 #pragma unroll
-                for (int m2 = 0; m2 < R2; ++m2) dst[(size_t)(m1 + R1 * m2) << a.Ns_log] = w[q][m2];
+                    for (int m2 = 0; m2 < R2; ++m2) {
+                        const size_t o = (size_t)(m1 + R1 * m2) << a.Ns_log;
+                        dst[o] = cmul(w[q][m2], __ldg(&mc[o]));
+                    }
+                } else if (a.sop == 2) {
+                    const T* fo = static_cast<const T*>(a.fac_out) + o0;
+#pragma unroll
+                    for (int m2 = 0; m2 < R2; ++m2) {
+                        const size_t o = (size_t)(m1 + R1 * m2) << a.Ns_log;
+                        dst[o] = cscale(w[q][m2], __ldg(&fo[o]));
+                    }
+                } else {
+#pragma unroll
+                    for (int m2 = 0; m2 < R2; ++m2) dst[(size_t)(m1 + R1 * m2) << a.Ns_log] = w[q][m2];
+                }
             }
         }
     } else {
@@ -232,6 +290,168 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
             const int c = (blk << a.Ns_log) + (rem & (Ns - 1));
             if (g0 + c < a.total) out[base + e] = sm[c * PR + m];
         }
+    }
+}
+
+}  // namespace p2
+}  // namespace nufft45
+
+namespace nufft45 {
+namespace p2 {
+
+// ---- streaming variant for multi-pass plans (n/R >= C) ----------------------
+// A grid of a few CTAs per SM walks over the tiles of C butterflies; while a
+// tile is transformed, the next one is fetched into the other half of a
+// double buffer with cp.async (global -> shared, no registers).  The shared
+// tile is [k][c] (c contiguous); both register-DFT steps read rows of C
+// consecutive columns with the thread's column index fastest, so neither needs
+// padding.  Twiddles come from a single table of W_n (one load each).
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T, int R1, int R2> struct SCfg {
+    static constexpr int R = R1 * R2;
+    static constexpr int kElems = sizeof(T) == 4 ? 4096 : 2048;
+    static constexpr int C = (kElems / R < 256 / R2) ? kElems / R : 256 / R2;
+    static constexpr int TH = C * R2;
+    static constexpr int NB = R1 / R2;
+    static constexpr int EPC = 16 / (int)sizeof(c2<T>);   // elements per 16-byte copy
+    // resident CTAs per SM the register budget must allow (shared memory
+    // holds two tiles of C*R elements: 64 KB for float, 64 KB for double)
+    static constexpr int kMinBlocks = (TH >= 256) ? 3 : 4;
+};
+
+struct SArgs {
+    int n_log, R_log, Ns_log;
+    int ntiles;          // batch * n / R / C
+};
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void s_issue(const c2<T>* __restrict__ in, c2<T>* stage, int tile, const SArgs& a) {
+    using G = SCfg<T, R1, R2>;
+    constexpr int C = G::C, R = G::R, EPC = G::EPC;
+    const int nR_log = a.n_log - a.R_log;
+    const int g0 = tile * C;
+    const uint32_t b = (uint32_t)g0 >> nR_log, j0 = (uint32_t)g0 & ((1u << nR_log) - 1);
+    const c2<T>* src = in + ((size_t)b << a.n_log) + j0;
+    constexpr int CP = C / EPC;                 // 16-byte copies per row
+    constexpr int ITER = R * CP / G::TH;        // copies per thread (exact)
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int e = threadIdx.x + i * G::TH;
+        const int k = e / CP, cc = (e % CP) * EPC;
+        cp_async16(stage + k * C + cc, src + ((size_t)k << nR_log) + cc);
+    }
+}
+
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBlocks) k_fft_p2s(const c2<T>* __restrict__ in,
+                                                                 c2<T>* __restrict__ out, SArgs a,
+                                                                 const c2<T>* __restrict__ tw, int dir) {
+    using G = SCfg<T, R1, R2>;
+    constexpr int R = G::R, C = G::C, NB = G::NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c2<T>* stage0 = reinterpret_cast<c2<T>*>(smem_raw);
+    c2<T>* stage1 = stage0 + R * C;
+    const int tid = threadIdx.x;
+    const int nR_log = a.n_log - a.R_log;
+    const uint32_t nR = 1u << nR_log;
+    const uint32_t Ns = 1u << a.Ns_log;
+    const int tw_shift = a.n_log - a.Ns_log - a.R_log;
+    const int inner_shift = a.n_log - a.R_log;
+    const int ca = tid % C, k2 = tid / C;       // step A thread
+    int tile = blockIdx.x;
+    if (tile >= a.ntiles) return;
+    s_issue<T, R1, R2>(in, stage0, tile, a);
+    cp_async_commit();
+    int buf = 0;
+    for (; tile < a.ntiles; tile += gridDim.x, buf ^= 1) {
+        c2<T>* st = buf ? stage1 : stage0;
+        const int next = tile + gridDim.x;
+        if (next < a.ntiles) s_issue<T, R1, R2>(in, buf ? stage0 : stage1, next, a);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int g0 = tile * C;
+        // step A: k = k1 R2 + k2 for column ca, pass twiddle, DFT over k1, inner twiddle
+        {
+            const uint32_t j = ((uint32_t)(g0 + ca)) & (nR - 1);
+            const uint32_t jm = j & (Ns - 1);
+            c2<T> v[R1];
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int k = k1 * R2 + k2;
+                c2<T> x = st[k * C + ca];
+                if (jm != 0 && k != 0) {
+                    c2<T> w = __ldg(&tw[(jm * (uint32_t)k) << tw_shift]);
+                    if (dir > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[k1] = x;
+            }
+            dft_reg<R1, T>(v, dir);
+            if (k2 != 0) {
+#pragma unroll
+                for (int m1 = 1; m1 < R1; ++m1) {
+                    c2<T> w = __ldg(&tw[(uint32_t)(m1 * k2) << inner_shift]);
+                    if (dir > 0) w.y = -w.y;
+                    v[m1] = cmul(v[m1], w);
+                }
+            }
+#pragma unroll
+            for (int m1 = 0; m1 < R1; ++m1) st[(m1 * R2 + k2) * C + ca] = v[m1];
+        }
+        __syncthreads();
+        // step B: (c, m1) -> X[m1 + R1 m2]
+        c2<T> w2[NB][R2];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int t = tid + q * G::TH;
+            const int c = t % C, m1 = t / C;
+#pragma unroll
+            for (int kk = 0; kk < R2; ++kk) w2[q][kk] = st[(m1 * R2 + kk) * C + c];
+            dft_reg<R2, T>(w2[q], dir);
+        }
+        if (Ns >= (uint32_t)C) {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int t = tid + q * G::TH;
+                const int c = t % C, m1 = t / C;
+                const uint32_t g = (uint32_t)(g0 + c);
+                const uint32_t b = g >> nR_log, j = g & (nR - 1);
+                c2<T>* dst = out + ((size_t)b << a.n_log) + ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) +
+                             (j & (Ns - 1));
+#pragma unroll
+                for (int m2 = 0; m2 < R2; ++m2) dst[(size_t)(m1 + R1 * m2) << a.Ns_log] = w2[q][m2];
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int t = tid + q * G::TH;
+                const int c = t % C, m1 = t / C;
+#pragma unroll
+                for (int m2 = 0; m2 < R2; ++m2) st[(m1 + R1 * m2) * C + c] = w2[q][m2];
+            }
+            __syncthreads();
+            const uint32_t b0 = (uint32_t)g0 >> nR_log, j0 = (uint32_t)g0 & (nR - 1);
+            const size_t base = ((size_t)b0 << a.n_log) + ((size_t)(j0 >> a.Ns_log) << (a.Ns_log + a.R_log));
+#pragma unroll
+            for (int i = 0; i < R1; ++i) {
+                const int e = tid + i * G::TH;
+                const int blk = e >> (a.Ns_log + a.R_log);
+                const int rem = e & ((1 << (a.Ns_log + a.R_log)) - 1);
+                const int m = rem >> a.Ns_log;
+                const int c = (blk << a.Ns_log) + (rem & (Ns - 1));
+                out[base + e] = st[m * C + c];
+            }
+        }
+        __syncthreads();
     }
 }
 

@@ -56,6 +56,7 @@ struct FFTPlan {
     int shift = 0;
     void* tw_lo = nullptr;
     void* tw_hi = nullptr;
+    void* tw_full = nullptr;            // W_n^e for every e < n (power-of-two plans)
     // Bluestein (n has a prime factor > 7): length-m convolution
     bool bluestein = false;
     int64_t m = 0;
@@ -77,6 +78,26 @@ int64_t fft_work_elems(const FFTPlan& p);
 template <typename T>
 nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir,
                       cudaStream_t s, c2<T>** result);
+
+// Element-wise work fused into the first pass's loads (lop) and the last
+// pass's stores (sop) of a multi-pass power-of-two FFT; idx is the element's
+// position in its length-n vector:
+//   lop 1: x[idx] = src[b * src_bs + ((idx - K0) mod ns)] * fac_in[idx]
+//   lop 2: x[idx] = in[idx] * fac_in[idx]
+//   sop 1: y[idx] *= mulc[idx];   sop 2: y[idx] *= fac_out[idx]
+struct FFTHooks {
+    int lop = 0, sop = 0;
+    const void* src = nullptr;
+    int64_t src_bs = 0, ns = 0, K0 = 0;
+    const void* fac_in = nullptr;
+    const void* mulc = nullptr;
+    const void* fac_out = nullptr;
+};
+template <typename T> bool fft_hooks_supported(const FFTPlan& p);
+// in -> out (never writes `in`; `work` and `out` are the ping-pong buffers)
+template <typename T>
+nufft_status fft_exec_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T>* out, int64_t batch, int dir,
+                             const FFTHooks& h, cudaStream_t s);
 
 // ------------------------------------------------------- node geometry ----
 // Nodes sorted by cell of a grid of size n (counting sort, ties by index),

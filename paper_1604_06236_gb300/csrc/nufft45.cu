@@ -400,9 +400,25 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
         launch_pointwise<T>(r1, P, r1, P, P, K, nullptr, bc, s);
         return fft_exec<T>(tab.fft_P, r1, r1 == vA ? vW : vA, bc, -1, s, res);
     };
+    const bool fused = fft_hooks_supported<T>(tab.fft_P);
     switch (op) {
         case OP_INV5: {
             launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
+            if (fused) {
+                // grid -> FFT; then Eq. 37 (selection, deconvolution, rho^k) on
+                // the loads of the inverse length-N FFT, Eq. 30 (x K) on its
+                // stores, and Eq. 31 (rho^-m / N) on the stores of the forward
+                // FFT, which writes the result
+                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+                FFTHooks h1;
+                h1.lop = 1; h1.src = r; h1.src_bs = ns; h1.ns = ns; h1.K0 = prm.K0s; h1.fac_in = fac5;
+                h1.sop = 1; h1.mulc = K;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                FFTHooks h2;
+                h2.sop = 2; h2.fac_out = sneg;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
+                break;
+            }
             if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
             launch_select<T>(r, ns, vA, P, P, prm.K0s, fac5, bc, s);
             if ((st = middle(&r)) != NUFFT_OK) return st;
@@ -410,6 +426,21 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
             break;
         }
         case OP_INV4: {
+            if (fused) {
+                // Eq. 37's rho^k on the loads and Eq. 30's x K on the stores of
+                // the inverse FFT; forward FFT; Eq. 31 and the deconvolution in
+                // the placement on the grid; type-2; x w (Eq. 40)
+                FFTHooks h1;
+                h1.lop = 2; h1.fac_in = rpos;
+                h1.sop = 1; h1.mulc = K;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                FFTHooks h2;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, gW, vW, bc, -1, h2, s)) != NUFFT_OK) return st;
+                launch_place<T>(vW, P, P, prm.K0s, fac4, gA, ns, bc, s);
+                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+                launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
+                break;
+            }
             launch_pointwise<T>(in, N, vA, P, P, nullptr, rpos, bc, s);
             if ((st = middle(&r)) != NUFFT_OK) return st;
             launch_place<T>(r, P, P, prm.K0s, fac4, gA, ns, bc, s);
