@@ -34,6 +34,9 @@ template <typename V> __host__ __device__ __forceinline__ V cfma(V acc, V a, V b
     return acc;
 }
 
+// read-only-path load (the double-float types specialise it)
+template <typename X> __device__ __forceinline__ X ldg(const X* p) { return __ldg(p); }
+
 template <typename To, typename From> __host__ __device__ __forceinline__ c2<To> ccast(From a) {
     return mk<To>((To)a.x, (To)a.y);
 }

@@ -10,6 +10,7 @@
 // the transform in natural order.  Lengths with a larger prime factor use
 // Bluestein's chirp-z convolution on a smooth length m >= 2n - 1.
 #include "internal.h"
+#include "df.cuh"
 #include "fft_p2.cuh"
 
 #include <algorithm>
@@ -24,6 +25,7 @@ constexpr int kThreads = 256;
 template <typename T> struct FftLimits;
 template <> struct FftLimits<float> { static constexpr int kElems = 8192; static constexpr int kLmax = 512; };
 template <> struct FftLimits<double> { static constexpr int kElems = 4096; static constexpr int kLmax = 256; };
+template <> struct FftLimits<dd> { static constexpr int kElems = 4096; static constexpr int kLmax = 256; };
 
 struct PassArgs {
     int64_t n, nR, Ns, total;  // total = batch * n / R butterflies
@@ -37,7 +39,7 @@ struct PassArgs {
 template <typename T>
 __device__ __forceinline__ c2<T> twiddle(const c2<T>* __restrict__ lo, const c2<T>* __restrict__ hi, int shift,
                                          int64_t mask, int64_t e, int dir) {
-    c2<T> w = cmul(__ldg(&lo[e & mask]), __ldg(&hi[e >> shift]));
+    c2<T> w = cmul(ldg(&lo[e & mask]), ldg(&hi[e >> shift]));
     if (dir > 0) w.y = -w.y;
     return w;
 }
@@ -190,23 +192,46 @@ __global__ void __launch_bounds__(kThreads) k_fft_pass(const c2<T>* in, c2<T>* o
     }
 }
 
-__global__ void k_make_twiddles_full(int64_t n, double2* out_d, float2* out_f) {
+__device__ __forceinline__ cdd to_cdd(double re, double im) {
+    cdd r;
+    r.x = dd_from_double(re);
+    r.y = dd_from_double(im);
+    return r;
+}
+
+__global__ void k_make_twiddles_full(int64_t n, double2* out_d, float2* out_f, cdd* out_x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s, c;
     sincospi(-2.0 * (double)i / (double)n, &s, &c);
     if (out_d) out_d[i] = make_double2(c, s);
     if (out_f) out_f[i] = make_float2((float)c, (float)s);
+    if (out_x) out_x[i] = to_cdd(c, s);
+}
+
+// in-place representation changes for the double-float FFTs (16 bytes either way)
+__global__ void k_to_dd(double2* buf, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = buf[i];
+    reinterpret_cast<cdd*>(buf)[i] = to_cdd(v.x, v.y);
+}
+__global__ void k_from_dd(double2* buf, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const cdd v = reinterpret_cast<const cdd*>(buf)[i];
+    buf[i] = make_double2(dd_to_double(v.x), dd_to_double(v.y));
 }
 
 __global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d, double2* hi_d,
-                                float2* lo_f, float2* hi_f) {
+                                float2* lo_f, float2* hi_f, cdd* lo_x, cdd* hi_x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {
         double s, c;
         sincospi(-2.0 * (double)i / (double)n, &s, &c);
         if (lo_d) lo_d[i] = make_double2(c, s);
         if (lo_f) lo_f[i] = make_float2((float)c, (float)s);
+        if (lo_x) lo_x[i] = to_cdd(c, s);
     }
     if (i < nhi) {
         // exponent i*B mod n, exact in integers before the division
@@ -215,13 +240,15 @@ __global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d
         sincospi(-2.0 * (double)e / (double)n, &s, &c);
         if (hi_d) hi_d[i] = make_double2(c, s);
         if (hi_f) hi_f[i] = make_float2((float)c, (float)s);
+        if (hi_x) hi_x[i] = to_cdd(c, s);
     }
 }
 
 // ---- Bluestein --------------------------------------------------------------
 // chirp c_k = e^{+j pi k^2/n}; forward filter h_m = c_m (m in (-n, n)),
 // inverse filter conj(h).  Phases are reduced exactly: k^2 mod 2n.
-__global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chirp_f, double2* hf, double2* hi) {
+__global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chirp_f, cdd* chirp_x, double2* hf,
+                             double2* hi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int64_t k = -1;
@@ -235,19 +262,21 @@ __global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chi
         if (i < n) {
             if (chirp_d) chirp_d[i] = c;
             if (chirp_f) chirp_f[i] = make_float2((float)co, (float)s);
+            if (chirp_x) chirp_x[i] = to_cdd(co, s);
         }
     }
     hf[i] = c;
     hi[i] = make_double2(c.x, -c.y);
 }
 
-__global__ void k_scale_c128_to(const double2* in, int64_t m, double s, double2* out_d, float2* out_f) {
+__global__ void k_scale_c128_to(const double2* in, int64_t m, double s, double2* out_d, float2* out_f, cdd* out_x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     double2 v = in[i];
     v.x *= s; v.y *= s;
     if (out_d) out_d[i] = v;
     if (out_f) out_f[i] = make_float2((float)v.x, (float)v.y);
+    if (out_x) out_x[i] = to_cdd(v.x, v.y);
 }
 
 template <typename T>
@@ -315,6 +344,7 @@ std::vector<int> sub_radices(int64_t R) {
 template <typename T> struct P2Limits;
 template <> struct P2Limits<float> { static constexpr int kElems = 4096; static constexpr int kRlogMax = 10; };
 template <> struct P2Limits<double> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 8; };
+template <> struct P2Limits<dd> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 8; };
 
 inline int r1_log_of(int rlog) { return (rlog + 1) / 2; }   // R1 >= R2, R1 <= 2 R2
 
@@ -648,14 +678,15 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
         NUFFT_CUDA_TRY(cudaMalloc(&hf, sizeof(double2) * m));
         NUFFT_CUDA_TRY(cudaMalloc(&hi, sizeof(double2) * m));
         NUFFT_CUDA_TRY(cudaMalloc(&work, sizeof(double2) * fft_work_elems(*p.sub)));
-        const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+        const size_t es = prec >= 2 ? sizeof(double2) : sizeof(float2);
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp, es * n));
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_fwd, es * m));
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_inv, es * m));
         const int tb = 256;
         Launch Lc(s, K_PLAN_TABLE, 48.0 * m);
         k_blue_chirp<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
-            n, m, prec == 2 ? (double2*)p.chirp : nullptr, prec == 2 ? nullptr : (float2*)p.chirp, hf, hi);
+            n, m, prec == 2 ? (double2*)p.chirp : nullptr, prec == 1 ? (float2*)p.chirp : nullptr,
+            prec == 3 ? (cdd*)p.chirp : nullptr, hf, hi);
         NUFFT_CUDA_TRY(cudaGetLastError());
         // the filter spectra are always formed in float64
         FFTPlan p64;
@@ -669,7 +700,8 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
             void* dst = which == 0 ? p.chirp_hat_fwd : p.chirp_hat_inv;
             Launch Ls(s, K_PLAN_TABLE, 32.0 * m);
             k_scale_c128_to<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
-                res, m, 1.0 / (double)m, prec == 2 ? (double2*)dst : nullptr, prec == 2 ? nullptr : (float2*)dst);
+                res, m, 1.0 / (double)m, prec == 2 ? (double2*)dst : nullptr, prec == 1 ? (float2*)dst : nullptr,
+                prec == 3 ? (cdd*)dst : nullptr);
             NUFFT_CUDA_TRY(cudaGetLastError());
         }
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -684,23 +716,25 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     p.shift = shift;
     const int64_t B = (int64_t)1 << shift;
     const int64_t nhi = (n + B - 1) / B;
-    const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+    const size_t es = prec >= 2 ? sizeof(double2) : sizeof(float2);
     NUFFT_CUDA_TRY(cudaMalloc(&p.tw_lo, es * B));
     NUFFT_CUDA_TRY(cudaMalloc(&p.tw_hi, es * nhi));
     const int64_t cnt = std::max(B, nhi);
     Launch Lt(s, K_PLAN_TABLE, 16.0 * (B + nhi));
     k_make_twiddles<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
         n, B, nhi, prec == 2 ? (double2*)p.tw_lo : nullptr, prec == 2 ? (double2*)p.tw_hi : nullptr,
-        prec == 2 ? nullptr : (float2*)p.tw_lo, prec == 2 ? nullptr : (float2*)p.tw_hi);
+        prec == 1 ? (float2*)p.tw_lo : nullptr, prec == 1 ? (float2*)p.tw_hi : nullptr,
+        prec == 3 ? (cdd*)p.tw_lo : nullptr, prec == 3 ? (cdd*)p.tw_hi : nullptr);
     NUFFT_CUDA_TRY(cudaGetLastError());
     if (n >= 2 && (n & (n - 1)) == 0 && n <= ((int64_t)1 << 24)) {
         NUFFT_CUDA_TRY(cudaMalloc(&p.tw_full, es * n));
         Launch Lf(s, K_PLAN_TABLE, 16.0 * n);
         k_make_twiddles_full<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-            n, prec == 2 ? (double2*)p.tw_full : nullptr, prec == 2 ? nullptr : (float2*)p.tw_full);
+            n, prec == 2 ? (double2*)p.tw_full : nullptr, prec == 1 ? (float2*)p.tw_full : nullptr,
+            prec == 3 ? (cdd*)p.tw_full : nullptr);
         NUFFT_CUDA_TRY(cudaGetLastError());
     }
-    return prec == 2 ? make_passes<double>(p) : make_passes<float>(p);
+    return prec == 1 ? make_passes<float>(p) : prec == 2 ? make_passes<double>(p) : make_passes<dd>(p);
 }
 
 template <typename T>
@@ -737,6 +771,29 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
 }
 
 template nufft_status fft_exec<float>(const FFTPlan&, float2*, float2*, int64_t, int, cudaStream_t, float2**);
+template nufft_status fft_exec<dd>(const FFTPlan&, cdd*, cdd*, int64_t, int, cudaStream_t, cdd**);
+
+// float64 data through a double-float plan: convert in place, transform,
+// convert the result back in place
+nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
+                         double2** result) {
+    const int64_t cnt = p.n * batch;
+    const unsigned nb = (unsigned)((cnt + 255) / 256);
+    {
+        Launch L(s, K_FFT, 32.0 * cnt, true);
+        k_to_dd<<<nb, 256, 0, s>>>(buf, cnt);
+    }
+    cdd* r = nullptr;
+    nufft_status st = fft_exec<dd>(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r);
+    if (st != NUFFT_OK) return st;
+    {
+        Launch L(s, K_FFT, 32.0 * cnt, true);
+        k_from_dd<<<nb, 256, 0, s>>>(reinterpret_cast<double2*>(r), cnt);
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    *result = reinterpret_cast<double2*>(r);
+    return NUFFT_OK;
+}
 template nufft_status fft_exec<double>(const FFTPlan&, double2*, double2*, int64_t, int, cudaStream_t, double2**);
 
 }  // namespace nufft45

@@ -112,7 +112,7 @@ struct Args {
 template <typename T>
 __device__ __forceinline__ c2<T> tw2(const c2<T>* __restrict__ lo, const c2<T>* __restrict__ hi, int shift,
                                      uint32_t e, int dir) {
-    c2<T> w = cmul(__ldg(&lo[e & ((1u << shift) - 1)]), __ldg(&hi[e >> shift]));
+    c2<T> w = cmul(ldg(&lo[e & ((1u << shift) - 1)]), ldg(&hi[e >> shift]));
     if (dir > 0) w.y = -w.y;
     return w;
 }
@@ -122,7 +122,7 @@ template <typename T>
 __device__ __forceinline__ c2<T> twn(const Args& a, const c2<T>* __restrict__ lo, const c2<T>* __restrict__ hi,
                                      uint32_t e, int dir) {
     if (a.tw_full) {
-        c2<T> w = __ldg(&static_cast<const c2<T>*>(a.tw_full)[e]);
+        c2<T> w = ldg(&static_cast<const c2<T>*>(a.tw_full)[e]);
         if (dir > 0) w.y = -w.y;
         return w;
     }
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
                 const int64_t idx = (int64_t)j + ((int64_t)(k1 * R2 + k2) << nR_log);
                 int64_t si = idx - a.K0;
                 si = si < 0 ? si + a.ns : si;
-                v[k1] = ok ? cscale(gsrc[si], __ldg(&fac[idx])) : mk<T>(0, 0);
+                v[k1] = ok ? cscale(gsrc[si], ldg(&fac[idx])) : mk<T>(0, 0);
             }
         } else {
             const c2<T>* src = in + ((size_t)b << a.n_log) + j;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
             if (a.lop == 2) {
                 const T* fac = static_cast<const T*>(a.fac_in) + j;
 #pragma unroll
-                for (int k1 = 0; k1 < R1; ++k1) v[k1] = cscale(v[k1], __ldg(&fac[(size_t)(k1 * R2 + k2) << nR_log]));
+                for (int k1 = 0; k1 < R1; ++k1) v[k1] = cscale(v[k1], ldg(&fac[(size_t)(k1 * R2 + k2) << nR_log]));
             }
         }
         const uint32_t jm = j & (Ns - 1);
@@ -251,14 +251,14 @@ __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, 
 #pragma unroll
                     for (int m2 = 0; m2 < R2; ++m2) {
                         const size_t o = (size_t)(m1 + R1 * m2) << a.Ns_log;
-                        dst[o] = cmul(w[q][m2], __ldg(&mc[o]));
+                        dst[o] = cmul(w[q][m2], ldg(&mc[o]));
                     }
                 } else if (a.sop == 2) {
                     const T* fo = static_cast<const T*>(a.fac_out) + o0;
 #pragma unroll
                     for (int m2 = 0; m2 < R2; ++m2) {
                         const size_t o = (size_t)(m1 + R1 * m2) << a.Ns_log;
-                        dst[o] = cscale(w[q][m2], __ldg(&fo[o]));
+                        dst[o] = cscale(w[q][m2], ldg(&fo[o]));
                     }
                 } else {
 #pragma unroll
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBloc
                 const int k = k1 * R2 + k2;
                 c2<T> x = st[k * C + ca];
                 if (jm != 0 && k != 0) {
-                    c2<T> w = __ldg(&tw[(jm * (uint32_t)k) << tw_shift]);
+                    c2<T> w = ldg(&tw[(jm * (uint32_t)k) << tw_shift]);
                     if (dir > 0) w.y = -w.y;
                     x = cmul(x, w);
                 }
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBloc
             if (k2 != 0) {
 #pragma unroll
                 for (int m1 = 1; m1 < R1; ++m1) {
-                    c2<T> w = __ldg(&tw[(uint32_t)(m1 * k2) << inner_shift]);
+                    c2<T> w = ldg(&tw[(uint32_t)(m1 * k2) << inner_shift]);
                     if (dir > 0) w.y = -w.y;
                     v[m1] = cmul(v[m1], w);
                 }

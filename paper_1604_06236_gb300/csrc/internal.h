@@ -49,7 +49,7 @@ struct FFTPass {
 
 struct FFTPlan {
     int64_t n = 0;
-    int prec = 0;                       // 1 = float, 2 = double
+    int prec = 0;                       // 1 = float, 2 = double, 3 = double-float
     std::vector<FFTPass> passes;
     std::vector<int> p2_rlog;           // power-of-two plan: log2 radix of each pass
     // two-level table of W_n^e = e^{-j 2 pi e / n}: lo[e & (B-1)] * hi[e >> shift]
@@ -78,6 +78,10 @@ int64_t fft_work_elems(const FFTPlan& p);
 template <typename T>
 nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir,
                       cudaStream_t s, c2<T>** result);
+// float64 vectors through a double-float plan (prec 3): ~2^-48 relative
+// accuracy with the arithmetic on the float32 pipes
+nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
+                         double2** result);
 
 // Element-wise work fused into the first pass's loads (lop) and the last
 // pass's stores (sop) of a multi-pass power-of-two FFT; idx is the element's

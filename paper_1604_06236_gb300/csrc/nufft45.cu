@@ -149,7 +149,7 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
 struct Tables {
     Params prm;
     FFTPlan fft_ns, fft_P;          // solve precision
-    FFTPlan fft_ns64, fft_P64;
+    FFTPlan fft_ns64, fft_P64;      // float64-accuracy transforms in double-float arithmetic
     // float64 plan tables
     double* fold = nullptr;         // Lambda_k / phihat((k mod P) - K0), k < R
     double* plan_place = nullptr;   // 1/phihat (plan width, grid ns), k < P
@@ -193,8 +193,10 @@ static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& ou
     const int sp = prm.prec == NUFFT_FP64 ? 2 : 1;
     if ((st = fft_make(t->fft_ns, prm.ns, sp, s)) != NUFFT_OK) return st;
     if ((st = fft_make(t->fft_P, P, sp, s)) != NUFFT_OK) return st;
-    if ((st = fft_make(t->fft_ns64, prm.ns, 2, s)) != NUFFT_OK) return st;
-    if ((st = fft_make(t->fft_P64, P, 2, s)) != NUFFT_OK) return st;
+    // the plan's float64-accuracy FFTs run in double-float arithmetic: GB300
+    // issues float32 at 64x its float64 rate
+    if ((st = fft_make(t->fft_ns64, prm.ns, 3, s)) != NUFFT_OK) return st;
+    if ((st = fft_make(t->fft_P64, P, 3, s)) != NUFFT_OK) return st;
     GLRule glR, glS;
     gauss_legendre_half(2 + (3 * prm.ks_plan.w) / 2 + 4, glR);
     gauss_legendre_half(2 + (3 * prm.ks_solve.w) / 2 + 4, glS);
@@ -338,23 +340,23 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     launch_plan_strengths(pl->T, N, (uint64_t)P, eta, str, s);
     launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s);
     double2* B = nullptr;
-    if ((st = fft_exec<double>(tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
     launch_fold(B, prm.ns, prm.K0s, tab.fold, P, eta, vecP, s);
     double2* v = nullptr;
-    if ((st = fft_exec<double>(tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = fft_exec_dd(tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
     // K_q (Eq. 29)
     launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, s);
     if (!f32) NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->Ks, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
     // L_m (Eq. 43) and the coefficients (m+1) L_{m+1} of L' (Eq. 16)
     NUFFT_CUDA_TRY(cudaMemcpyAsync(vecP, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
     double2* F = nullptr;
-    if ((st = fft_exec<double>(tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = fft_exec_dd(tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
     double2* dco = (F == vecP) ? workP : vecP;
     launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
     // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
     launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
     double2* gsp = nullptr;
-    if ((st = fft_exec<double>(tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
     launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
     launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
@@ -502,11 +504,11 @@ nufft_status forward64(const nufft_plan_s* pl, bool type2, const double2* x, dou
     nufft_status st;
     if (type2) {
         launch_place<double>(x, N, N, prm.K0s, tab.plan_place, g, prm.ns, bc, s);
-        if ((st = fft_exec<double>(tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
+        if ((st = fft_exec_dd(tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
         launch_interp<double>(pl->gs, prm.ks_plan, r, pl->modp64_srt, y, N, bc, s);
     } else {
         launch_spread<double>(pl->gs, prm.ks_plan, x, N, pl->modm64_ext, g, bc, s);
-        if ((st = fft_exec<double>(tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
+        if ((st = fft_exec_dd(tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
         launch_select<double>(r, prm.ns, y, N, N, prm.K0s, tab.plan_place, bc, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());
@@ -777,19 +779,21 @@ const char* nufft_last_error_message(void) { return g_msg; }
 
 // Test hook (not part of the public header): run the library's FFT of length
 // n on `batch` contiguous device vectors in place (prec 1: complex64, 2:
-// complex128; dir -1 forward, +1 inverse, unnormalised).  Synchronises.
+// complex128, 3: complex128 data through the double-float FFT; dir -1
+// forward, +1 inverse, unnormalised).  Synchronises.
 nufft_status nufft_debug_fft(int64_t n, int prec, int dir, int64_t batch, void* buf, nufft_stream_t stream) {
-    if (n < 1 || batch < 1 || !buf || (prec != 1 && prec != 2) || (dir != 1 && dir != -1))
+    if (n < 1 || batch < 1 || !buf || prec < 1 || prec > 3 || (dir != 1 && dir != -1))
         return fail(NUFFT_ERR_ARG, "bad FFT test arguments");
     cudaStream_t s = (cudaStream_t)stream;
     FFTPlan p;
     nufft_status st = fft_make(p, n, prec, s);
     if (st != NUFFT_OK) return st;
-    const size_t es = prec == 2 ? sizeof(double2) : sizeof(float2);
+    const size_t es = prec >= 2 ? sizeof(double2) : sizeof(float2);
     void* work = nullptr;
     NUFFT_CUDA_TRY(cudaMalloc(&work, es * (size_t)fft_work_elems(p) * (size_t)batch));
     void* res = nullptr;
-    if (prec == 2) st = fft_exec<double>(p, (double2*)buf, (double2*)work, batch, dir, s, (double2**)&res);
+    if (prec == 3) st = fft_exec_dd(p, (double2*)buf, (double2*)work, batch, dir, s, (double2**)&res);
+    else if (prec == 2) st = fft_exec<double>(p, (double2*)buf, (double2*)work, batch, dir, s, (double2**)&res);
     else st = fft_exec<float>(p, (float2*)buf, (float2*)work, batch, dir, s, (float2**)&res);
     if (st == NUFFT_OK && res != buf)
         st = cudaMemcpyAsync(buf, res, es * n * batch, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? NUFFT_OK : NUFFT_ERR_CUDA;
