@@ -128,7 +128,8 @@ def measured_peaks():
 
 def committed_traffic(kernel):
     """dram bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source is unchanged since it was captured."""
+    kernel's sources (the pass kernels and their launcher) are unchanged since
+    the counters were taken."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         with open(path) as fh:
@@ -139,12 +140,13 @@ def committed_traffic(kernel):
     if not ent:
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_1604_06236_gb300", "csrc", ent["source"])
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    return ent["dram_bytes_per_launch"] if sha == ent["source_sha256_16"] else None
+    h = hashlib.sha256()
+    for name in ent["sources"]:
+        try:
+            h.update(open(os.path.join(ROOT, "paper_1604_06236_gb300", "csrc", name), "rb").read())
+        except OSError:
+            return None
+    return ent["dram_bytes_per_launch"] if h.hexdigest()[:16] == ent["sources_sha256_16"] else None
 
 
 # ------------------------------------------------------------ reference ----
