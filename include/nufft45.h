@@ -247,6 +247,18 @@ nufft_status nufft_plan_set_batch_chunk(nufft_plan_t plan, int64_t chunk);
  */
 nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_stream_t stream);
 
+/*
+ * nufft_stream_check -- no counterpart in the paper.  Synchronises `stream`
+ * and reports whether a bounded wait inside one of the library's kernels on
+ * the current device gave up since the last call: the TMA-fed FFT passes wait
+ * on shared-memory barriers for their input tiles with an iteration limit,
+ * and on expiry count the event, let their copies land and return without
+ * writing that tile.  Returns NUFFT_ERR_TIMEOUT (and clears the count) if
+ * that happened, NUFFT_ERR_CUDA on a CUDA error, else NUFFT_OK.  Results of
+ * the calls in between are then not to be trusted.
+ */
+nufft_status nufft_stream_check(nufft_stream_t stream);
+
 /* Drop the cache of node-independent tables (deconvolution and scaling
  * factors, FFT twiddles) kept per (N, precision, tolerance).  Plans that are
  * alive keep their own reference. */

@@ -92,6 +92,7 @@ def lib():
         L.nufft_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         L.nufft_plan_export.argtypes = [vp, i32, vp, vp]
         L.nufft_cache_clear.argtypes = []
+        L.nufft_stream_check.argtypes = [vp]
         L.nufft_profile_enable.argtypes = [i32]
         L.nufft_profile_enable.restype = i32
         L.nufft_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
@@ -104,7 +105,7 @@ def lib():
         L.nufft_last_error_message.restype = ctypes.c_char_p
         for name in ("nufft_plan", "nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv",
                      "nufft_destroy",
-                     "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear"):
+                     "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear", "nufft_stream_check"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -120,6 +121,12 @@ def _stream_handle(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def stream_check(stream=None):
+    """Synchronise the stream; raise NufftError(NUFFT_ERR_TIMEOUT) if a bounded
+    wait inside a library kernel gave up since the last check."""
+    check(lib().nufft_stream_check(_stream_handle(stream)))
 
 
 def _ptr(t):

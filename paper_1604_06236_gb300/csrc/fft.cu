@@ -12,6 +12,9 @@
 #include "internal.h"
 #include "df.cuh"
 #include "fft_p2.cuh"
+#include "fft_p2t.cuh"
+
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -453,6 +456,91 @@ nufft_status launch_p2s(int rlog, const c2<T>* in, c2<T>* out, p2::SArgs a, cons
     }
 }
 
+// ---- TMA-fed float32 passes ------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+template <int R1, int R2>
+nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta, int64_t batch, const float2* tw,
+                            int dir, cudaStream_t s) {
+    using G = p2t::TCfg<R1, R2>;
+    // the pass's inputs as a 4-D array (j, k2, k1, vector): x[v n + j + (k1 R2 + k2) n/R]
+    const uint64_t nR = 1ull << (ta.n_log - ta.R_log);
+    CUtensorMap tm;
+    cuuint64_t dims[4] = {nR, (cuuint64_t)R2, (cuuint64_t)R1, (cuuint64_t)batch};
+    cuuint64_t strides[3] = {nR * sizeof(float2), (cuuint64_t)R2 * nR * sizeof(float2),
+                             (1ull << ta.n_log) * sizeof(float2)};
+    cuuint32_t box[4] = {(cuuint32_t)G::C, (cuuint32_t)R2, (cuuint32_t)R1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (tma_encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<float2*>(in), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(NUFFT_ERR_CUDA, "tensor map for a %d x %d FFT pass rejected", R1, R2);
+    auto kern = p2t::k_fft_p2t<R1, R2>;
+    constexpr size_t smem = p2t::smem_bytes<R1, R2>();
+    static int per_sm = 0;
+    if (!per_sm) {
+        NUFFT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        NUFFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, G::TH, smem));
+        per_sm = std::max(1, b);
+    }
+    int dev = 0, sms = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(ta.ntiles, per_sm * std::max(1, sms));
+    kern<<<grid, G::TH, smem, s>>>(tm, out, ta, tw, dir);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+// Run one float32 pass on the TMA-fed kernel when it applies (radix 256 or
+// 512 in a multi-pass plan, whole tiles inside a vector, no gather on the
+// loads); *done tells whether it ran.
+template <typename T>
+nufft_status try_p2t(const FFTPlan& p, const c2<T>* in, c2<T>* out, const p2::Args& a, int64_t batch, int dir,
+                     cudaStream_t s, bool* done) {
+    *done = false;
+    if constexpr (sizeof(T) != 4) {
+        return NUFFT_OK;
+    } else {
+        if (!p.tw_full || p.p2_rlog.size() < 2 || (a.R_log != 8 && a.R_log != 9)) return NUFFT_OK;
+        if (a.lop != 0 && a.lop != 2) return NUFFT_OK;
+        if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) return NUFFT_OK;
+        const int clog = p2_C_log<float>(a.R_log);
+        if (clog > a.n_log - a.R_log) return NUFFT_OK;                       // a tile stays inside one vector
+        if (a.Ns_log != 0 && a.Ns_log < clog) return NUFFT_OK;                // stores: direct or one contiguous block
+        if (a.Ns_log < clog && a.sop != 0) return NUFFT_OK;
+        if (batch > (1ll << 31) / ((1ll << (a.n_log - a.R_log)) >> clog)) return NUFFT_OK;
+        if (!tma_encoder()) return NUFFT_OK;
+        p2t::TArgs ta;
+        ta.n_log = a.n_log;
+        ta.R_log = a.R_log;
+        ta.Ns_log = a.Ns_log;
+        ta.C_log = clog;
+        ta.ntiles = (int)((batch << (a.n_log - a.R_log)) >> clog);
+        ta.lop = a.lop;
+        ta.sop = a.sop;
+        ta.fac_in = static_cast<const float*>(a.fac_in);
+        ta.mulc = static_cast<const float2*>(a.mulc);
+        ta.fac_out = static_cast<const float*>(a.fac_out);
+        const float2* tw = static_cast<const float2*>(p.tw_full);
+        nufft_status st = (a.R_log == 8) ? launch_p2t_one<16, 16>(in, out, ta, batch, tw, dir, s)
+                                         : launch_p2t_one<32, 16>(in, out, ta, batch, tw, dir, s);
+        *done = (st == NUFFT_OK);
+        return st;
+    }
+}
+
 template <typename T>
 nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
                      c2<T>** result) {
@@ -479,19 +567,24 @@ nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, i
         {
             Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             const int clog = p2_C_log<T>(rl);
-            nufft_status st;
-            // float64 passes stream tiles through shared memory (their float64
-            // arithmetic is the limit; prefetching the next tile hides the loads);
-            // float32 passes load straight into registers from many resident CTAs
-            if (sizeof(T) == 8 && p.tw_full && p.p2_rlog.size() > 1 && rl >= 4 && clog <= L - rl) {
-                p2::SArgs sa;
-                sa.n_log = L;
-                sa.R_log = rl;
-                sa.Ns_log = ns_log;
-                sa.ntiles = (int)((batch << (L - rl)) >> clog);
-                st = launch_p2s<T>(rl, src, dst, sa, static_cast<const c2<T>*>(p.tw_full), dir, s);
-            } else {
-                st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            // float32 radix-256/512 passes of multi-pass plans: TMA-fed tiles;
+            // float64 passes stream tiles through shared memory with cp.async
+            // (their float64 arithmetic is the limit; prefetching the next tile
+            // hides the loads); other float32 passes load straight into
+            // registers from many resident CTAs
+            bool done = false;
+            nufft_status st = try_p2t<T>(p, src, dst, a, batch, dir, s, &done);
+            if (st == NUFFT_OK && !done) {
+                if (sizeof(T) == 8 && p.tw_full && p.p2_rlog.size() > 1 && rl >= 4 && clog <= L - rl) {
+                    p2::SArgs sa;
+                    sa.n_log = L;
+                    sa.R_log = rl;
+                    sa.Ns_log = ns_log;
+                    sa.ntiles = (int)((batch << (L - rl)) >> clog);
+                    st = launch_p2s<T>(rl, src, dst, sa, static_cast<const c2<T>*>(p.tw_full), dir, s);
+                } else {
+                    st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+                }
             }
             if (st != NUFFT_OK) return st;
         }
@@ -604,7 +697,9 @@ nufft_status exec_p2_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T
         {
             // algorithmic bytes: one read and one write of the vectors
             Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
-            nufft_status st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            bool done = false;
+            nufft_status st = try_p2t<T>(p, src, dst, a, batch, dir, s, &done);
+            if (st == NUFFT_OK && !done) st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
             if (st != NUFFT_OK) return st;
         }
         ns_log += rl;
@@ -662,6 +757,17 @@ FFTPlan::~FFTPlan() {
 }
 
 int64_t fft_work_elems(const FFTPlan& p) { return p.bluestein ? 2 * p.m : p.n; }
+
+nufft_status fft_wait_status(cudaStream_t s) {
+    int expired = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyFromSymbolAsync(&expired, g_wait_expired, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (expired == 0) return NUFFT_OK;
+    const int zero = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyToSymbolAsync(g_wait_expired, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(NUFFT_ERR_TIMEOUT, "%d FFT pass tile wait(s) expired", expired);
+}
 
 nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     p.n = n;

@@ -72,6 +72,9 @@ int64_t next_smooth(int64_t n);            // smallest smooth m >= n
 nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s);
 // scratch elements (complex) fft_exec needs besides its buffer, per batch item
 int64_t fft_work_elems(const FFTPlan& p);
+// NUFFT_ERR_TIMEOUT if a bounded in-kernel wait of an FFT pass expired since
+// the last call (synchronises s, then clears the count), else NUFFT_OK
+nufft_status fft_wait_status(cudaStream_t s);
 // In-place-by-result: transforms `buf` (batch contiguous items of n) with
 // dir = -1 (sum x e^{-j2pi jk/n}) or +1 (sum x e^{+j2pi jk/n}), unnormalised.
 // Returns the pointer that holds the result (buf or work).

@@ -756,6 +756,8 @@ nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_st
     return NUFFT_OK;
 }
 
+nufft_status nufft_stream_check(nufft_stream_t stream) { return fft_wait_status((cudaStream_t)stream); }
+
 nufft_status nufft_cache_clear(void) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_cache.clear();

@@ -51,3 +51,19 @@ def test_double_float_fft_matches_numpy(n):
         got = _run(n, 3, dir_, x)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err < 2e-13, (n, dir_, err)
+
+
+@pytest.mark.parametrize("n,batch", [(65536, 64), (131072, 40), (1 << 18, 9), (32768, 70)])
+def test_tma_fed_passes_many_tiles(n, batch):
+    """float32 power-of-two plans whose radix-256/512 passes run on the
+    TMA-fed persistent kernel, with batches large enough that every CTA walks
+    several tiles through its ring of stages (32768 = 256 x 128 mixes it with
+    the register-loading pass)."""
+    x = synth.cn01((batch, n), seed=n + batch)
+    xr = x.astype(np.complex64).astype(np.complex128)
+    for dir_ in (-1, 1):
+        ref = np.fft.fft(xr, axis=1) if dir_ < 0 else np.fft.ifft(xr, axis=1) * n
+        got = _run(n, 1, dir_, x)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 3e-6, (n, batch, dir_, err)
+    pkg.stream_check()   # no bounded wait gave up
