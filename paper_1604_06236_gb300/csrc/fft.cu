@@ -347,7 +347,9 @@ std::vector<int> sub_radices(int64_t R) {
 template <typename T> struct P2Limits;
 template <> struct P2Limits<float> { static constexpr int kElems = 4096; static constexpr int kRlogMax = 10; };
 template <> struct P2Limits<double> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 8; };
-template <> struct P2Limits<dd> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 8; };
+// double-float plans use radix <= 64: their transforms are few (batch 1 to
+// eta), so more, lighter threads per pass beat fewer passes
+template <> struct P2Limits<dd> { static constexpr int kElems = 2048; static constexpr int kRlogMax = 6; };
 
 inline int r1_log_of(int rlog) { return (rlog + 1) / 2; }   // R1 >= R2, R1 <= 2 R2
 
@@ -541,9 +543,20 @@ nufft_status try_p2t(const FFTPlan& p, const c2<T>* in, c2<T>* out, const p2::Ar
     }
 }
 
+// every pass of the plan runs on the streaming kernel (8-byte scalars)
+template <typename T>
+bool p2s_all(const FFTPlan& p) {
+    if (sizeof(T) != 8 || !p.tw_full || p.p2_rlog.size() < 2) return false;
+    int L = 0;
+    while (((int64_t)1 << L) < p.n) ++L;
+    for (int rl : p.p2_rlog)
+        if (rl < 4 || p2_C_log<T>(rl) > L - rl) return false;
+    return true;
+}
+
 template <typename T>
 nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir, cudaStream_t s,
-                     c2<T>** result) {
+                     c2<T>** result, int cvt_in = 0, int cvt_out = 0) {
     const c2<T>* lo = static_cast<const c2<T>*>(p.tw_lo);
     const c2<T>* hi = static_cast<const c2<T>*>(p.tw_hi);
     int L = 0;
@@ -581,6 +594,8 @@ nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, i
                     sa.R_log = rl;
                     sa.Ns_log = ns_log;
                     sa.ntiles = (int)((batch << (L - rl)) >> clog);
+                    sa.cvt_in = (i == 0) ? cvt_in : 0;
+                    sa.cvt_out = (i + 1 == p.p2_rlog.size()) ? cvt_out : 0;
                     st = launch_p2s<T>(rl, src, dst, sa, static_cast<const c2<T>*>(p.tw_full), dir, s);
                 } else {
                     st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
@@ -883,6 +898,15 @@ template nufft_status fft_exec<dd>(const FFTPlan&, cdd*, cdd*, int64_t, int, cud
 // convert the result back in place
 nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
                          double2** result) {
+    if (batch > 0 && p2s_all<dd>(p)) {
+        // the first pass converts on its loads, the last on its stores
+        cdd* r = nullptr;
+        nufft_status st = exec_p2<dd>(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r,
+                                      1, 1);
+        if (st != NUFFT_OK) return st;
+        *result = reinterpret_cast<double2*>(r);
+        return NUFFT_OK;
+    }
     const int64_t cnt = p.n * batch;
     const unsigned nb = (unsigned)((cnt + 255) / 256);
     {

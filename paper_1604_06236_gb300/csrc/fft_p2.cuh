@@ -15,6 +15,7 @@
 // arithmetic is shifts and masks.
 #pragma once
 #include "common.cuh"
+#include "df.cuh"
 
 namespace nufft45 {
 namespace p2 {
@@ -329,7 +330,27 @@ template <typename T, int R1, int R2> struct SCfg {
 struct SArgs {
     int n_log, R_log, Ns_log;
     int ntiles;          // batch * n / R / C
+    // double-float passes only: the input holds float64 pairs (converted on
+    // load) / the output is written as float64 pairs
+    int cvt_in, cvt_out;
 };
+
+// element load / store with an optional float64 <-> double-float conversion;
+// a complex double-float has the size of a double2, so a buffer can hold either
+template <typename T> __device__ __forceinline__ c2<T> ld_cvt(const c2<T>* p, int) { return *p; }
+template <> __device__ __forceinline__ cdd ld_cvt<dd>(const cdd* p, int cvt) {
+    if (!cvt) return *p;
+    const double2 d = *reinterpret_cast<const double2*>(p);
+    cdd r;
+    r.x = dd_from_double(d.x);
+    r.y = dd_from_double(d.y);
+    return r;
+}
+template <typename T> __device__ __forceinline__ void st_cvt(c2<T>* p, const c2<T>& v, int) { *p = v; }
+template <> __device__ __forceinline__ void st_cvt<dd>(cdd* p, const cdd& v, int cvt) {
+    if (cvt) *reinterpret_cast<double2*>(p) = make_double2(dd_to_double(v.x), dd_to_double(v.y));
+    else *p = v;
+}
 
 template <typename T, int R1, int R2>
 __device__ __forceinline__ void s_issue(const c2<T>* __restrict__ in, c2<T>* stage, int tile, const SArgs& a) {
@@ -386,7 +407,7 @@ __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBloc
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) {
                 const int k = k1 * R2 + k2;
-                c2<T> x = st[k * C + ca];
+                c2<T> x = ld_cvt<T>(&st[k * C + ca], a.cvt_in);
                 if (jm != 0 && k != 0) {
                     c2<T> w = ldg(&tw[(jm * (uint32_t)k) << tw_shift]);
                     if (dir > 0) w.y = -w.y;
@@ -427,7 +448,7 @@ __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBloc
                 c2<T>* dst = out + ((size_t)b << a.n_log) + ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) +
                              (j & (Ns - 1));
 #pragma unroll
-                for (int m2 = 0; m2 < R2; ++m2) dst[(size_t)(m1 + R1 * m2) << a.Ns_log] = w2[q][m2];
+                for (int m2 = 0; m2 < R2; ++m2) st_cvt<T>(&dst[(size_t)(m1 + R1 * m2) << a.Ns_log], w2[q][m2], a.cvt_out);
             }
         } else {
             __syncthreads();
@@ -448,7 +469,7 @@ __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBloc
                 const int rem = e & ((1 << (a.Ns_log + a.R_log)) - 1);
                 const int m = rem >> a.Ns_log;
                 const int c = (blk << a.Ns_log) + (rem & (Ns - 1));
-                out[base + e] = st[m * C + c];
+                st_cvt<T>(&out[base + e], st[m * C + c], a.cvt_out);
             }
         }
         __syncthreads();
