@@ -55,7 +55,13 @@ typedef enum {
      * b - F x1, formed by a float64 type-2 (resp. type-1) transform, and the
      * correction is added, taking the relative error from eps to about eps^2
      * (Eqs. 44-46).  For ill-conditioned node sets (near-coincident nodes). */
-    NUFFT_REFINE = 0x100
+    NUFFT_REFINE = 0x100,
+    /* OR-ed into the precision (no counterpart in the paper): nufft_plan
+     * returns as soon as the plan's kernels are enqueued instead of waiting
+     * for them to read back the duplicate-node check.  The check still runs
+     * on the device; nufft_plan_check reports it.  Device node arrays must
+     * then stay valid until the plan's kernels have run (stream order). */
+    NUFFT_DEFER_CHECK = 0x200
 } nufft_prec;
 
 /*
@@ -72,7 +78,8 @@ typedef enum {
  * tol    target relative L2 error: NUFFT_FP64 accepts [1e-12, 1e-1],
  *        NUFFT_FP32 accepts [1e-6, 1e-1]; tighter values return
  *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
- * prec   NUFFT_FP32 or NUFFT_FP64, optionally | NUFFT_REFINE.
+ * prec   NUFFT_FP32 or NUFFT_FP64, optionally | NUFFT_REFINE and/or
+ *        | NUFFT_DEFER_CHECK.
  * plan   receives the plan; owned by the caller, release with nufft_destroy.
  * The call synchronises `stream` once to check for coincident nodes: two
  * nodes whose turns t differ by less than 2^-44 modulo 1 make the systems of
@@ -246,6 +253,15 @@ nufft_status nufft_plan_set_batch_chunk(nufft_plan_t plan, int64_t chunk);
  * Synchronises `stream`.
  */
 nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_stream_t stream);
+
+/*
+ * nufft_plan_check -- no counterpart in the paper.  Waits for the plan's
+ * kernels on its stream and returns NUFFT_ERR_DUP_NODES if two nodes coincide
+ * modulo 2 pi (the inverse does not exist; results of the plan are not to be
+ * used), else NUFFT_OK.  For plans made with NUFFT_DEFER_CHECK this is where
+ * that condition surfaces; for the others nufft_plan already reported it.
+ */
+nufft_status nufft_plan_check(nufft_plan_t plan);
 
 /*
  * nufft_stream_check -- no counterpart in the paper.  Synchronises `stream`

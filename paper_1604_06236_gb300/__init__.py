@@ -13,11 +13,12 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "build", "library_path", "ProfileEntry", "check"]
+__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "DEFER_CHECK", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
 REFINE = 0x100   # OR into the precision: one refinement step per inverse (Sec. V)
+DEFER_CHECK = 0x200   # OR into the precision: the plan call does not wait for the duplicate-node check
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libnufft45.so")
@@ -93,6 +94,7 @@ def lib():
         L.nufft_plan_export.argtypes = [vp, i32, vp, vp]
         L.nufft_cache_clear.argtypes = []
         L.nufft_stream_check.argtypes = [vp]
+        L.nufft_plan_check.argtypes = [vp]
         L.nufft_profile_enable.argtypes = [i32]
         L.nufft_profile_enable.restype = i32
         L.nufft_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), i32, ctypes.POINTER(ctypes.c_int)]
@@ -105,7 +107,7 @@ def lib():
         L.nufft_last_error_message.restype = ctypes.c_char_p
         for name in ("nufft_plan", "nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv",
                      "nufft_destroy",
-                     "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear", "nufft_stream_check"):
+                     "nufft_plan_info", "nufft_plan_export", "nufft_cache_clear", "nufft_stream_check", "nufft_plan_check"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -154,6 +156,11 @@ class Plan:
         self._h = ctypes.c_void_p()
         self._x_keep = x
         check(lib().nufft_plan(self.N, _ptr(x), float(tol), int(prec), _stream_handle(stream), ctypes.byref(self._h)))
+
+    def check(self):
+        """Wait for the plan; raise NufftError(NUFFT_ERR_DUP_NODES) if two nodes
+        coincide (the way a DEFER_CHECK plan reports it)."""
+        check(lib().nufft_plan_check(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -275,6 +282,11 @@ class Batch:
         st = torch.empty(self.count, dtype=torch.int32)
         check(lib().nufft_batch_status(self._h, ctypes.c_void_p(st.data_ptr()), _stream_handle(stream)))
         return st
+
+    def check(self):
+        """Wait for the plan; raise NufftError(NUFFT_ERR_DUP_NODES) if two nodes
+        coincide (the way a DEFER_CHECK plan reports it)."""
+        check(lib().nufft_plan_check(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -260,6 +260,15 @@ bool is_device_ptr(const void* p) {
 
 size_t solve_elem(const Params& p) { return p.prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2); }
 
+// wait for the plan's kernels and read the duplicate-node flag they set
+nufft_status plan_dup_check(nufft_plan_s* pl) {
+    int dup = 0;
+    cudaError_t e = cudaMemcpyAsync(&dup, pl->gs.dup_flag, sizeof(int), cudaMemcpyDeviceToHost, pl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "plan synchronisation", __FILE__, __LINE__);
+    return dup ? fail(NUFFT_ERR_DUP_NODES, "two nodes coincide modulo 2 pi") : NUFFT_OK;
+}
+
 int64_t per_item_elems(const nufft_plan_s* pl) {
     const Tables& t = *pl->tab;
     return pl->prm.ns + fft_work_elems(t.fft_ns) + pl->prm.N + fft_work_elems(t.fft_P);
@@ -642,9 +651,11 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     if (N < 1 || N > ((int64_t)1 << 28)) return fail(NUFFT_ERR_ARG, "N = %lld out of range [1, 2^28]", (long long)N);
     if (!x) return fail(NUFFT_ERR_ARG, "null node pointer");
     const bool refine = (prec & NUFFT_REFINE) != 0;
-    prec &= ~NUFFT_REFINE;
+    const bool defer = (prec & NUFFT_DEFER_CHECK) != 0;
+    prec &= ~(NUFFT_REFINE | NUFFT_DEFER_CHECK);
     if (prec != NUFFT_FP32 && prec != NUFFT_FP64)
-        return fail(NUFFT_ERR_ARG, "precision %d is not NUFFT_FP32/NUFFT_FP64 (optionally | NUFFT_REFINE)", prec);
+        return fail(NUFFT_ERR_ARG,
+                    "precision %d is not NUFFT_FP32/NUFFT_FP64 (optionally | NUFFT_REFINE | NUFFT_DEFER_CHECK)", prec);
     if (!(tol > 0.0) || !std::isfinite(tol) || tol > 0.1) return fail(NUFFT_ERR_ARG, "tol %g out of range (0, 0.1]", tol);
     Params prm;
     nufft_status st = choose_params(N, tol, prec, prm);
@@ -674,13 +685,7 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     }
     st = run_plan(pl, xd);
     xs.release();
-    int dup = 0;
-    if (st == NUFFT_OK) {
-        cudaError_t e = cudaMemcpyAsync(&dup, pl->gs.dup_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "plan synchronisation", __FILE__, __LINE__);
-    }
-    if (st == NUFFT_OK && dup) st = fail(NUFFT_ERR_DUP_NODES, "two nodes coincide modulo 2 pi");
+    if (st == NUFFT_OK && !defer) st = plan_dup_check(pl);
     if (st != NUFFT_OK) {
         pl->mem.release();
         cudaStreamSynchronize(s);
@@ -689,6 +694,11 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     }
     *plan = pl;
     return NUFFT_OK;
+}
+
+nufft_status nufft_plan_check(nufft_plan_t plan) {
+    if (!plan) return fail(NUFFT_ERR_ARG, "null plan");
+    return plan_dup_check(plan);
 }
 
 nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream) {

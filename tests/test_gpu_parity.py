@@ -169,6 +169,30 @@ def test_duplicate_nodes_rejected():
     assert e.value.status == "NUFFT_ERR_DUP_NODES"
 
 
+def test_deferred_duplicate_check():
+    """NUFFT_DEFER_CHECK: the plan call returns without waiting; the
+    duplicate-node condition surfaces in nufft_plan_check, and a plan of
+    distinct nodes gives bit-identical results to a checked one."""
+    N = 100
+    x = synth.jittered_nodes(N, 0.45, seed=15)
+    x[40] = x[41] + 2 * np.pi
+    p = pkg.Plan(torch.from_numpy(x).cuda(), prec=FP64 | pkg.DEFER_CHECK)
+    with pytest.raises(pkg.NufftError) as e:
+        p.check()
+    assert e.value.status == "NUFFT_ERR_DUP_NODES"
+    p.close()
+    N = 4096
+    x = synth.jittered_nodes(N, 0.45, seed=18)
+    f = synth.cn01((2, N), seed=19)
+    for prec in (FP32, FP64):
+        pd = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec | pkg.DEFER_CHECK)
+        out_d = _np(pd.inv5(_dev(f, prec)))
+        pd.check()
+        pc = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+        pc.check()
+        np.testing.assert_array_equal(out_d, _np(pc.inv5(_dev(f, prec))))
+
+
 def test_host_buffers_match_device():
     N = 2048
     x = synth.jittered_nodes(N, 0.45, seed=16)
