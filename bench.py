@@ -412,8 +412,10 @@ def run_gpu(args):
         d2h = 2 * B * N * 8
         result["e2e"] = {"value": 2 * B * args.steps * ws / e2e_s, "unit": "transforms/s",
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                         "how": "nufft_plan/nufft_inv5/nufft_inv4 given pinned host buffers; the library copies "
-                                "in and out on the stream; wall clock over the steps"}
+                         "how": "nufft_plan/nufft_inv5/nufft_inv4 given pinned host buffers (nodes, data, "
+                                "results); the library stages them through device memory on its copy streams, "
+                                "overlapping the transforms; each step ends with the plan's duplicate-node check; "
+                                "wall clock over the steps, closed by a device synchronisation"}
     time.sleep(0.3)
     clocks.stop()
     result["clocks"] = clocks.summary(t_wall0, t_wall1)

@@ -14,11 +14,17 @@
  *   complex128 (double re, im) for NUFFT_FP64 plans.  `batch` right-hand
  *   sides are contiguous with stride N elements.  Out-of-place only: the
  *   input and output buffers must not overlap.
- * Pointers.  Device pointers, or host pointers (pinned or pageable): host
- *   buffers are staged through device memory with copies on `stream`, and the
- *   call returns after the result has been copied back.  For device buffers
- *   the call is asynchronous on `stream`.  Device buffers stay owned by the
- *   caller.
+ * Pointers.  Device pointers, or host pointers (pinned or pageable), staged
+ *   through device memory.  Pageable host buffers are copied on `stream` and
+ *   the call returns after the result has been copied back.  Pinned host
+ *   buffers (page-locked, e.g. cudaHostAlloc) are copied on the library's own
+ *   copy streams (one per direction and device), ordered after the work
+ *   queued on `stream` by events, so the copies overlap transforms queued
+ *   earlier or later: the call returns once the work is queued; the host
+ *   input must not change, and the host output is not complete, until
+ *   nufft_stream_check(stream) returns or the device is synchronised.  For
+ *   device buffers the call is asynchronous on `stream`.  Buffers stay owned
+ *   by the caller.
  * Stream.  A cudaStream_t (NULL = legacy default stream).
  * Errors.  Every call returns a status and never aborts or traps; the
  *   message of the last failure on the calling thread is available from
@@ -74,7 +80,10 @@ typedef enum {
  *   w_p = h(-P t_p + j P a) / (L'(z_p) z_p) (Eqs. 17, 23, 27, 40).
  *   The shift a and the oversampling eta follow Sec. V (Eq. 49) from `tol`.
  * N      number of nodes (= number of coefficients), 1 <= N <= 2^28.
- * x      N nodes in radians (float64), device or host.  Not retained.
+ * x      N nodes in radians (float64), device or host.  Not retained, but
+ *        with NUFFT_DEFER_CHECK a device or pinned host array must not change
+ *        before nufft_plan_check returns (its copy or its first use may still
+ *        be queued).
  * tol    target relative L2 error: NUFFT_FP64 accepts [1e-12, 1e-1],
  *        NUFFT_FP32 accepts [1e-6, 1e-1]; tighter values return
  *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
@@ -265,7 +274,8 @@ nufft_status nufft_plan_check(nufft_plan_t plan);
 
 /*
  * nufft_stream_check -- no counterpart in the paper.  Synchronises `stream`
- * and reports whether a bounded wait inside one of the library's kernels on
+ * and the library's copy streams of the current device (so pinned host
+ * outputs are complete) and reports whether a bounded wait inside one of the library's kernels on
  * the current device gave up since the last call: the TMA-fed FFT passes wait
  * on shared-memory barriers for their input tiles with an iteration limit,
  * and on expiry count the event, let their copies land and return without

@@ -126,8 +126,9 @@ def _stream_handle(stream=None):
 
 
 def stream_check(stream=None):
-    """Synchronise the stream; raise NufftError(NUFFT_ERR_TIMEOUT) if a bounded
-    wait inside a library kernel gave up since the last check."""
+    """Synchronise the stream and the library's copy streams (pinned host
+    outputs are then complete); raise NufftError(NUFFT_ERR_TIMEOUT) if a
+    bounded wait inside a library kernel gave up since the last check."""
     check(lib().nufft_stream_check(_stream_handle(stream)))
 
 

@@ -57,6 +57,11 @@ struct Arena {
         if (base) cudaFreeAsync(base, stream);
         base = nullptr;
     }
+    // free in the order of another stream (one that has waited for every use)
+    void release_on(cudaStream_t s) {
+        stream = s;
+        release();
+    }
 };
 
 // a size accumulator with the same alignment rule as Arena::take
@@ -248,25 +253,127 @@ struct nufft_plan_s {
     double2* modm64_ext = nullptr;   // float64 e^{-j 2 pi K0 t}, extended slot order
     double2* modp64_srt = nullptr;   // float64 e^{+j 2 pi K0 t}, sorted slot order
     int64_t chunk = 1;
+    int* dup_host = nullptr;         // pinned copy of the duplicate-node flag
+    cudaEvent_t dup_ev = nullptr;    // recorded after that copy
 };
 
 namespace {
 
-bool is_device_ptr(const void* p) {
+// Pinned host words for the duplicate-node flags: a plan's flag is copied
+// back asynchronously, so nufft_plan_check waits for the plan's own kernels
+// only, not for work queued after them.  A word returns to the pool once its
+// copy has landed.
+struct PinnedWords {
+    std::mutex mu;
+    std::vector<int*> free_;
+    std::vector<std::pair<int*, cudaEvent_t>> pending;   // released, copy maybe in flight
+    int* acquire() {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < pending.size();) {
+            if (cudaEventQuery(pending[i].second) != cudaErrorNotReady) {
+                cudaGetLastError();
+                cudaEventDestroy(pending[i].second);
+                free_.push_back(pending[i].first);
+                pending[i] = pending.back();
+                pending.pop_back();
+            } else {
+                ++i;
+            }
+        }
+        if (free_.empty()) {
+            int* block = nullptr;
+            if (cudaHostAlloc(reinterpret_cast<void**>(&block), 1024 * sizeof(int), cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            for (int i = 0; i < 1024; ++i) free_.push_back(block + i);
+        }
+        int* w = free_.back();
+        free_.pop_back();
+        return w;
+    }
+    void release(int* w, cudaEvent_t ev) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (ev) pending.emplace_back(w, ev);
+        else free_.push_back(w);
+    }
+};
+PinnedWords& pinned_words() {
+    static PinnedWords* p = new PinnedWords();   // outlives static destruction order
+    return *p;
+}
+
+}  // namespace
+
+namespace {
+
+enum MemLoc { LOC_DEVICE, LOC_PINNED, LOC_PAGEABLE };
+
+MemLoc mem_loc(const void* p) {
     cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return LOC_PAGEABLE; }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return LOC_DEVICE;
+    return at.type == cudaMemoryTypeHost ? LOC_PINNED : LOC_PAGEABLE;
+}
+
+bool is_device_ptr(const void* p) { return mem_loc(p) == LOC_DEVICE; }
+
+// per-device streams for host <-> device copies of pinned buffers, so that
+// they overlap the transforms queued on the caller's stream
+struct CopyStreams { cudaStream_t h2d = nullptr, d2h = nullptr; };
+nufft_status copy_streams(CopyStreams& out) {
+    static std::mutex mu;
+    static CopyStreams per_dev[64];
+    int dev = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(NUFFT_ERR_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    CopyStreams& c = per_dev[dev];
+    if (!c.h2d) NUFFT_CUDA_TRY(cudaStreamCreateWithFlags(&c.h2d, cudaStreamNonBlocking));
+    if (!c.d2h) NUFFT_CUDA_TRY(cudaStreamCreateWithFlags(&c.d2h, cudaStreamNonBlocking));
+    out = c;
+    return NUFFT_OK;
+}
+
+// make `waiter` wait for the work queued so far on `on`
+nufft_status order_after(cudaStream_t waiter, cudaStream_t on) {
+    cudaEvent_t e = nullptr;
+    NUFFT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, on);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(waiter, e, 0);
+    cudaEventDestroy(e);   // released once the recorded work completes
+    if (r != cudaSuccess) return cuda_fail(r, "stream ordering", __FILE__, __LINE__);
+    return NUFFT_OK;
 }
 
 size_t solve_elem(const Params& p) { return p.prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2); }
 
-// wait for the plan's kernels and read the duplicate-node flag they set
+// queue the copy of the duplicate-node flag behind the plan's kernels
+nufft_status plan_dup_queue(nufft_plan_s* pl) {
+    pl->dup_host = pinned_words().acquire();
+    if (!pl->dup_host) return fail(NUFFT_ERR_ALLOC, "pinned host word for the duplicate-node flag");
+    NUFFT_CUDA_TRY(cudaEventCreateWithFlags(&pl->dup_ev, cudaEventDisableTiming));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->dup_host, pl->gs.dup_flag, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+    NUFFT_CUDA_TRY(cudaEventRecord(pl->dup_ev, pl->stream));
+    return NUFFT_OK;
+}
+
+// wait for the plan's kernels (not for later work on its stream) and read
+// the duplicate-node flag they set
 nufft_status plan_dup_check(nufft_plan_s* pl) {
-    int dup = 0;
-    cudaError_t e = cudaMemcpyAsync(&dup, pl->gs.dup_flag, sizeof(int), cudaMemcpyDeviceToHost, pl->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "plan synchronisation", __FILE__, __LINE__);
-    return dup ? fail(NUFFT_ERR_DUP_NODES, "two nodes coincide modulo 2 pi") : NUFFT_OK;
+    if (!pl->dup_ev) return fail(NUFFT_ERR_ARG, "plan has no queued check");
+    NUFFT_CUDA_TRY(cudaEventSynchronize(pl->dup_ev));
+    return *pl->dup_host ? fail(NUFFT_ERR_DUP_NODES, "two nodes coincide modulo 2 pi") : NUFFT_OK;
+}
+
+void plan_dup_release(nufft_plan_s* pl) {
+    if (pl->dup_host) {
+        pinned_words().release(pl->dup_host, pl->dup_ev);
+    } else if (pl->dup_ev) {
+        cudaEventDestroy(pl->dup_ev);
+    }
+    pl->dup_host = nullptr;
+    pl->dup_ev = nullptr;
 }
 
 int64_t per_item_elems(const nufft_plan_s* pl) {
@@ -567,19 +674,38 @@ nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int
     const char* ib = (const char*)in;
     const char* ob = (const char*)out;
     if (ib < ob + bytes && ob < ib + bytes) return fail(NUFFT_ERR_ARG, "input and output overlap");
-    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    const MemLoc lin = mem_loc(in), lout = mem_loc(out);
+    const bool din = lin == LOC_DEVICE, dout = lout == LOC_DEVICE;
+    // pinned buffers are copied on the library's copy streams, ordered against
+    // `s` by events, and the call returns without waiting; pageable buffers
+    // are copied on `s` and the call waits for the result
+    const bool async_host = (din || lin == LOC_PINNED) && (dout || lout == LOC_PINNED);
+    CopyStreams cs;
+    if (async_host && (!din || !dout)) {
+        nufft_status e = copy_streams(cs);
+        if (e != NUFFT_OK) return e;
+    }
     const void* din_p = in;
     void* dout_p = out;
     Arena stage;
     if (!din || !dout) {
-        nufft_status st = stage.reserve(2 * bytes, s);
+        // pinned: staging memory and input copy in the copy stream's order, so
+        // the copy does not wait for the work already queued on s
+        nufft_status st = stage.reserve(2 * bytes, async_host ? cs.h2d : s);
         if (st != NUFFT_OK) return st;
         char* a = stage.take<char>(bytes);
         char* b = stage.take<char>(bytes);
-        if (!din) {
+        if (async_host) {
+            if (!din) {
+                cudaError_t r = cudaMemcpyAsync(a, in, bytes, cudaMemcpyHostToDevice, cs.h2d);
+                if (r != cudaSuccess) { stage.release(); return cuda_fail(r, "cudaMemcpyAsync", __FILE__, __LINE__); }
+            }
+            nufft_status e = order_after(s, cs.h2d);
+            if (e != NUFFT_OK) { stage.release(); return e; }
+        } else if (!din) {
             NUFFT_CUDA_TRY(cudaMemcpyAsync(a, in, bytes, cudaMemcpyHostToDevice, s));
-            din_p = a;
         }
+        if (!din) din_p = a;
         if (!dout) dout_p = b;
     }
     nufft_status st;
@@ -590,13 +716,30 @@ nufft_status run_public(nufft_plan_t plan, Op op, const void* in, void* out, int
     else
         st = refined ? run_refined<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s)
                      : run_op<float>(plan, op, (const float2*)din_p, (float2*)dout_p, batch, s);
+    if (st == NUFFT_OK && async_host) {
+        if (!dout) {
+            // the copy back runs behind the transforms on the copy stream and
+            // overlaps whatever is queued on s next; the staging memory is
+            // freed in that stream's order
+            st = order_after(cs.d2h, s);
+            if (st == NUFFT_OK) {
+                cudaError_t r = cudaMemcpyAsync(out, dout_p, bytes, cudaMemcpyDeviceToHost, cs.d2h);
+                if (r != cudaSuccess) st = cuda_fail(r, "cudaMemcpyAsync", __FILE__, __LINE__);
+            }
+            stage.release_on(st == NUFFT_OK ? cs.d2h : s);
+            return st;
+        }
+        stage.release_on(s);   // s has waited for the staged input
+        return st;
+    }
     if (st == NUFFT_OK && !dout) {
         NUFFT_CUDA_TRY(cudaMemcpyAsync(out, dout_p, bytes, cudaMemcpyDeviceToHost, s));
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     } else if (st == NUFFT_OK && !din) {
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // the staged input must outlive its use
     }
-    stage.release();
+    if (async_host) stage.release_on(s);   // s has waited for the staged copy
+    else stage.release();
     return st;
 }
 
@@ -676,19 +819,31 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     // nodes on the device (host arrays are staged)
     const double* xd = x;
     Arena xs;
-    if (!is_device_ptr(x)) {
-        if ((st = xs.reserve(sizeof(double) * N, s)) != NUFFT_OK) { delete pl; return st; }
+    const MemLoc xl = mem_loc(x);
+    if (xl != LOC_DEVICE) {
+        // pinned nodes travel on the host-to-device copy stream (not behind
+        // copies queued on s), pageable ones on s
+        CopyStreams cs;
+        cudaStream_t cp = s;
+        if (xl == LOC_PINNED) {
+            if ((st = copy_streams(cs)) != NUFFT_OK) { delete pl; return st; }
+            cp = cs.h2d;
+        }
+        if ((st = xs.reserve(sizeof(double) * N, cp)) != NUFFT_OK) { delete pl; return st; }
         double* d = xs.take<double>(N);
-        cudaError_t e = cudaMemcpyAsync(d, x, sizeof(double) * N, cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(d, x, sizeof(double) * N, cudaMemcpyHostToDevice, cp);
         if (e != cudaSuccess) { xs.release(); delete pl; return cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__); }
+        if (cp != s && (st = order_after(s, cp)) != NUFFT_OK) { xs.release(); delete pl; return st; }
         xd = d;
     }
     st = run_plan(pl, xd);
-    xs.release();
+    xs.release_on(s);
+    if (st == NUFFT_OK) st = plan_dup_queue(pl);
     if (st == NUFFT_OK && !defer) st = plan_dup_check(pl);
     if (st != NUFFT_OK) {
         pl->mem.release();
         cudaStreamSynchronize(s);
+        plan_dup_release(pl);
         delete pl;
         return st;
     }
@@ -733,6 +888,7 @@ nufft_status nufft_destroy(nufft_plan_t plan) {
     // stream-ordered release: work already queued on the plan's stream keeps
     // its buffers; kernels hold no reference to the host-side object
     plan->mem.release();
+    plan_dup_release(plan);
     delete plan;
     return NUFFT_OK;
 }
@@ -766,7 +922,14 @@ nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_st
     return NUFFT_OK;
 }
 
-nufft_status nufft_stream_check(nufft_stream_t stream) { return fft_wait_status((cudaStream_t)stream); }
+nufft_status nufft_stream_check(nufft_stream_t stream) {
+    CopyStreams cs;
+    nufft_status st = copy_streams(cs);
+    if (st != NUFFT_OK) return st;
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(cs.h2d));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(cs.d2h));
+    return fft_wait_status((cudaStream_t)stream);
+}
 
 nufft_status nufft_cache_clear(void) {
     std::lock_guard<std::mutex> lk(g_cache_mu);

@@ -169,6 +169,35 @@ def test_duplicate_nodes_rejected():
     assert e.value.status == "NUFFT_ERR_DUP_NODES"
 
 
+def test_pinned_host_buffers_stream_ordered():
+    """Pinned host buffers: the copies run on the library's copy streams and
+    the calls return without waiting; after nufft_stream_check every output
+    equals the device-buffer result, for pinned -> pinned, pinned -> device
+    and device -> pinned, with calls queued back to back."""
+    N = 4096
+    x = torch.from_numpy(synth.jittered_nodes(N, 0.45, seed=20)).cuda()
+    f = synth.cn01((5, N), seed=21)
+    A = synth.cn01((5, N), seed=22)
+    plan = pkg.Plan(x, prec=FP32)
+    ref5 = _np(plan.inv5(_dev(f, FP32)))
+    ref4 = _np(plan.inv4(_dev(A, FP32)))
+    fin = torch.from_numpy(f).to(torch.complex64).pin_memory()
+    Ain = torch.from_numpy(A).to(torch.complex64).pin_memory()
+    o5 = torch.empty_like(fin).pin_memory()
+    o4 = torch.empty_like(Ain).pin_memory()
+    d5 = torch.empty(5, N, dtype=torch.complex64, device="cuda")
+    d4 = torch.empty_like(d5)
+    o4b = torch.empty_like(Ain).pin_memory()
+    plan.inv5(fin, out=o5)
+    plan.inv4(Ain, out=o4)
+    plan.inv5(fin, out=d5)
+    plan.inv4(_dev(A, FP32), out=o4b)
+    plan.inv4(Ain, out=d4)
+    pkg.stream_check()
+    for got, ref in ((o5, ref5), (o4, ref4), (d5, ref5), (o4b, ref4), (d4, ref4)):
+        np.testing.assert_array_equal(_np(got), ref)
+
+
 def test_deferred_duplicate_check():
     """NUFFT_DEFER_CHECK: the plan call returns without waiting; the
     duplicate-node condition surfaces in nufft_plan_check, and a plan of
@@ -202,7 +231,8 @@ def test_host_buffers_match_device():
     dev = _np(plan_d.inv5(_dev(f, FP32)))
     host_in = torch.from_numpy(f).to(torch.complex64).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    plan_h.inv5(host_in, out=host_out)
+    plan_h.inv5(host_in, out=host_out)       # pinned: copied on the library's copy streams
+    pkg.stream_check()
     np.testing.assert_array_equal(host_out.numpy().astype(np.complex128), dev)
     pageable = torch.from_numpy(f).to(torch.complex64)
     np.testing.assert_array_equal(_np(plan_h.inv5(pageable)), dev)
