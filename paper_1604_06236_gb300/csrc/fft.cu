@@ -535,6 +535,9 @@ nufft_status try_p2t(const FFTPlan& p, const c2<T>* in, c2<T>* out, const p2::Ar
         ta.fac_in = static_cast<const float*>(a.fac_in);
         ta.mulc = static_cast<const float2*>(a.mulc);
         ta.fac_out = static_cast<const float*>(a.fac_out);
+        ta.out_bs = a.out_bs;
+        ta.off = a.sel_off;
+        ta.len = a.sel_len;
         const float2* tw = static_cast<const float2*>(p.tw_full);
         nufft_status st = (a.R_log == 8) ? launch_p2t_one<16, 16>(in, out, ta, batch, tw, dir, s)
                                          : launch_p2t_one<32, 16>(in, out, ta, batch, tw, dir, s);
@@ -577,6 +580,7 @@ nufft_status exec_p2(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, i
         a.lop = a.sop = 0;
         a.src = a.fac_in = a.mulc = a.fac_out = nullptr;
         a.src_bs = a.ns = a.K0 = 0;
+        a.out_bs = a.sel_off = a.sel_len = 0;
         {
             Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             const int clog = p2_C_log<T>(rl);
@@ -709,12 +713,21 @@ nufft_status exec_p2_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T
         a.fac_in = h.fac_in;
         a.mulc = h.mulc;
         a.fac_out = h.fac_out;
+        a.out_bs = h.out_bs;
+        a.sel_off = a.sel_len = 0;
+        if (a.sop == 3) { a.sel_off = h.K0; a.sel_len = h.P; }
+        if (a.sop == 4) { a.sel_off = h.K0; a.sel_len = h.ns; }
         {
-            // algorithmic bytes: one read and one write of the vectors
-            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
+            // algorithmic bytes: one read and one write of the vectors (the
+            // selecting store writes P of the n outputs)
+            const double wr = (a.sop == 3) ? (double)h.P : (double)p.n;
+            Launch Lk(s, K_FFT, ((double)p.n + wr) * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             bool done = false;
             nufft_status st = try_p2t<T>(p, src, dst, a, batch, dir, s, &done);
-            if (st == NUFFT_OK && !done) st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            if (st == NUFFT_OK && !done) {
+                if (a.sop >= 3) return fail(NUFFT_ERR_ARG, "scattering FFT stores need the TMA-fed pass");
+                st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
+            }
             if (st != NUFFT_OK) return st;
         }
         ns_log += rl;
@@ -724,6 +737,27 @@ nufft_status exec_p2_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T
 }
 
 }  // namespace
+
+template <typename T>
+bool fft_scatter_supported(const FFTPlan& p) {
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        if (p.p2_rlog.size() != 2 || !p.tw_full || !tma_encoder()) return false;
+        int L = 0;
+        while (((int64_t)1 << L) < p.n) ++L;
+        int ns_log = 0;
+        for (int rl : p.p2_rlog) {
+            if (rl != 8 && rl != 9) return false;
+            const int clog = p2_C_log<float>(rl);
+            if (clog > L - rl || (ns_log != 0 && ns_log < clog)) return false;
+            ns_log += rl;
+        }
+        return true;
+    }
+}
+template bool fft_scatter_supported<float>(const FFTPlan&);
+template bool fft_scatter_supported<double>(const FFTPlan&);
 
 template <typename T>
 bool fft_hooks_supported(const FFTPlan& p) {

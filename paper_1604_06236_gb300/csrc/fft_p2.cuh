@@ -108,6 +108,9 @@ struct Args {
     const void* fac_in;
     const void* mulc;
     const void* fac_out;
+    // scattering stores (sop 3, 4; TMA-fed pass only): batch stride of the
+    // destination, index offset and length
+    int64_t out_bs, sel_off, sel_len;
 };
 
 template <typename T>

@@ -44,11 +44,14 @@ constexpr int kPollLimit = 1 << 22;
 struct TArgs {
     int n_log, R_log, Ns_log, C_log;
     int ntiles;
-    // lop 2: x = in[idx] * fac_in[idx]; sop 1: y *= mulc[idx]; sop 2: y *= fac_out[idx]
+    // lop 2: x = in[idx] * fac_in[idx]; sop 1: y *= mulc[idx]; sop 2: y *= fac_out[idx];
+    // sop 3: k = (idx + off) mod n, if k < len: out[b out_bs + k] = y fac_out[k];
+    // sop 4: out[b out_bs + ((idx - off) mod len)] = y fac_out[idx]
     int lop, sop;
     const float* fac_in;
     const float2* mulc;
     const float* fac_out;
+    int64_t out_bs, off, len;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -199,7 +202,25 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
                 const uint32_t j = j0 + c;
                 const size_t o0 = ((size_t)(j >> a.Ns_log) << (a.Ns_log + a.R_log)) + (j & (Ns - 1));
                 float2* dst = out + ((size_t)b << a.n_log) + o0;
-                if (a.sop == 1) {
+                if (a.sop == 3) {
+                    const int64_t n = (int64_t)1 << a.n_log;
+                    float2* sd = out + (int64_t)b * a.out_bs;
+#pragma unroll
+                    for (int m2 = 0; m2 < R2; ++m2) {
+                        int64_t k = (int64_t)o0 + ((int64_t)(m1 + R1 * m2) << a.Ns_log) + a.off;
+                        k = k >= n ? k - n : k;
+                        if (k < a.len) sd[k] = cscale(w[q][m2], __ldg(&a.fac_out[k]));
+                    }
+                } else if (a.sop == 4) {
+                    float2* sd = out + (int64_t)b * a.out_bs;
+#pragma unroll
+                    for (int m2 = 0; m2 < R2; ++m2) {
+                        const int64_t o = (int64_t)o0 + ((int64_t)(m1 + R1 * m2) << a.Ns_log);
+                        int64_t g = o - a.off;
+                        g = g < 0 ? g + a.len : g;
+                        sd[g] = cscale(w[q][m2], __ldg(&a.fac_out[o]));
+                    }
+                } else if (a.sop == 1) {
                     const float2* mc = a.mulc + o0;
 #pragma unroll
                     for (int m2 = 0; m2 < R2; ++m2) {

@@ -92,6 +92,9 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
 //   lop 1: x[idx] = src[b * src_bs + ((idx - K0) mod ns)] * fac_in[idx]
 //   lop 2: x[idx] = in[idx] * fac_in[idx]
 //   sop 1: y[idx] *= mulc[idx];   sop 2: y[idx] *= fac_out[idx]
+// and two scattering stores, where `out` has batch stride out_bs:
+//   sop 3 (select): k = (idx + K0) mod n; if k < P: out[b out_bs + k] = y[idx] fac_out[k]
+//   sop 4 (place):  out[b out_bs + ((idx - K0) mod ns)] = y[idx] fac_out[idx]
 struct FFTHooks {
     int lop = 0, sop = 0;
     const void* src = nullptr;
@@ -99,8 +102,11 @@ struct FFTHooks {
     const void* fac_in = nullptr;
     const void* mulc = nullptr;
     const void* fac_out = nullptr;
+    int64_t out_bs = 0, P = 0;
 };
 template <typename T> bool fft_hooks_supported(const FFTPlan& p);
+// the scattering stores (sop 3, 4) run on this plan: float32, two TMA-fed passes
+template <typename T> bool fft_scatter_supported(const FFTPlan& p);
 // in -> out (never writes `in`; `work` and `out` are the ping-pong buffers)
 template <typename T>
 nufft_status fft_exec_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T>* out, int64_t batch, int dir,

@@ -519,9 +519,28 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
         return fft_exec<T>(tab.fft_P, r1, r1 == vA ? vW : vA, bc, -1, s, res);
     };
     const bool fused = fft_hooks_supported<T>(tab.fft_P);
+    // selection and placement as scattering stores of the FFT passes
+    const bool scatter = fft_scatter_supported<T>(tab.fft_ns) && fft_scatter_supported<T>(tab.fft_P);
+    const int64_t K0 = imod(prm.K0s, ns);
     switch (op) {
         case OP_INV5: {
             launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
+            if (scatter) {
+                // grid -> FFT whose last pass keeps only the N selected
+                // frequencies, deconvolved and scaled by rho^k (Eq. 37); then
+                // the inverse length-N FFT with Eq. 30's x K on its stores and
+                // the forward one with Eq. 31's rho^-m / N, which writes the result
+                FFTHooks hs;
+                hs.sop = 3; hs.K0 = K0; hs.P = P; hs.out_bs = P; hs.fac_out = fac5;
+                if ((st = fft_exec_hooked<T>(tab.fft_ns, gA, gW, vA, bc, -1, hs, s)) != NUFFT_OK) return st;
+                FFTHooks h1;
+                h1.sop = 1; h1.mulc = K;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                FFTHooks h2;
+                h2.sop = 2; h2.fac_out = sneg;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
+                break;
+            }
             if (fused) {
                 // grid -> FFT; then Eq. 37 (selection, deconvolution, rho^k) on
                 // the loads of the inverse length-N FFT, Eq. 30 (x K) on its
@@ -544,6 +563,29 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
             break;
         }
         case OP_INV4: {
+            if (scatter) {
+                // Eq. 37's rho^k on the loads and Eq. 30's x K on the stores of
+                // the inverse FFT; the forward FFT's last pass places its
+                // outputs on the grid with Eq. 31 and the deconvolution folded
+                // into fac4 (the other ns - N grid points are zeroed); grid
+                // FFT; type-2; x w (Eq. 40)
+                FFTHooks h1;
+                h1.lop = 2; h1.fac_in = rpos;
+                h1.sop = 1; h1.mulc = K;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                const int64_t g0 = imod(P - K0, ns), gap = ns - P;
+                const int64_t first = std::min(gap, ns - g0);
+                if (first > 0)
+                    NUFFT_CUDA_TRY(cudaMemset2DAsync(gA + g0, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * first, bc, s));
+                if (gap > first)
+                    NUFFT_CUDA_TRY(cudaMemset2DAsync(gA, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * (gap - first), bc, s));
+                FFTHooks h2;
+                h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
+                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
+                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+                launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
+                break;
+            }
             if (fused) {
                 // Eq. 37's rho^k on the loads and Eq. 30's x K on the stores of
                 // the inverse FFT; forward FFT; Eq. 31 and the deconvolution in
