@@ -13,6 +13,7 @@
 // lengths N that are not use Bluestein's chirp-z on a power-of-two length, so
 // one table of W_{2^L} twiddles serves all instances.
 #include "internal.h"
+#include "cis64.cuh"
 #include "fft_p2.cuh"
 
 #include <algorithm>
@@ -255,10 +256,10 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             cell[i] = c;
             frac[i] = (double)(t * (uint64_t)ns) * 5.42101086242752217003726400434970855712890625e-20;
             atomicAdd(&cnt[c], 1);
-            modm[i] = cis_turns((uint64_t)K0 * t, -1);
-            modp[i] = cis_turns((uint64_t)K0 * t, +1);
+            modm[i] = cis_turns_t((uint64_t)K0 * t, -1);
+            modp[i] = cis_turns_t((uint64_t)K0 * t, +1);
             for (int r = 0; r < kEta; ++r)
-                str[(int64_t)r * N + i] = cmul(cis_turns((uint64_t)N * (uint64_t)r * t, -1), modm[i]);
+                str[(int64_t)r * N + i] = cmul(cis_turns_t((uint64_t)N * (uint64_t)r * t, -1), modm[i]);
         }
         __syncthreads();
         cta_scan(cnt, ns, start, s_part);
@@ -401,8 +402,8 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 const double2 Dp = cmul(acc, modp[i]);
                 D64[i] = Dp;
                 const uint64_t t = T[i];
-                const double2 e = cis_turns((uint64_t)N * t, -1);
-                const double2 z = cis_turns(t, +1);
+                const double2 e = cis_turns_t((uint64_t)N * t, -1);
+                const double2 z = cis_turns_t(t, +1);
                 const double2 h = make_double2(rhoN * e.x - 1.0, rhoN * e.y);
                 const double2 den = cmul(h, cmul(Dp, z));
                 const double nn = den.x * den.x + den.y * den.y;
@@ -548,6 +549,10 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     if (!inst) return fail(NUFFT_ERR_ARG, "null instance array");
     if (!(tol >= 1e-6) || tol > 0.1) return fail(tol < 1e-6 && tol > 0 ? NUFFT_ERR_ACCURACY : NUFFT_ERR_ARG,
                                                  "batched tol %g outside [1e-6, 0.1]", tol);
+    {
+        nufft_status e = cis_table_ensure();   // before any graph capture of the batch kernel
+        if (e != NUFFT_OK) return e;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Desc> h(count);
     std::vector<int64_t> order(count);

@@ -136,18 +136,24 @@ struct Geometry {
 // ------------------------------------------------------------- launchers --
 struct KernelShape { int w; double beta; };
 
+// per-device tables the plan kernels read (call before the first plan on a device)
+nufft_status plan_kernels_init();
+
 void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s);
 nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n, int w,
                             bool want_float, int* scratch_int, cudaStream_t s);
 int64_t geometry_scratch_ints(int64_t N, int64_t n);
 void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s);
 
+// ktab (optional, N * ks.w values): the spread also stores every kernel value
+// it evaluates, by sorted slot and tap, and an interpolation on the same
+// geometry and kernel reads them instead of evaluating the kernel again
 template <typename T>
 void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs,
-                   const c2<T>* wt_ext, c2<T>* grid, int64_t batch, cudaStream_t s);
+                   const c2<T>* wt_ext, c2<T>* grid, int64_t batch, cudaStream_t s, T* ktab = nullptr);
 template <typename T>
 void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt,
-                   c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s);
+                   c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s, const T* ktab = nullptr);
 
 // out[b][k] = in[b][(k - K0) mod n] * fac[k], k < P
 template <typename T>

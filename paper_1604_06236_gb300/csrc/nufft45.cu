@@ -430,6 +430,8 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     zt.add<double2>((size_t)eta * fft_work_elems(tab.fft_ns64));
     zt.add<double2>(P); zt.add<double2>(fft_work_elems(tab.fft_P64));
     zt.add<unsigned long long>(1);
+    zt.add<double>((size_t)N * prm.ks_plan.w);                           // kernel values
+
     Arena tmp;
     if ((st = tmp.reserve(zt.used, s)) != NUFFT_OK) return st;
     int* geo = tmp.take<int>(geo_ints);
@@ -439,6 +441,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     double2* vecP = tmp.take<double2>(P);
     double2* workP = tmp.take<double2>(fft_work_elems(tab.fft_P64));
     unsigned long long* sumT = tmp.take<unsigned long long>(1);
+    double* ktab = tmp.take<double>((size_t)N * prm.ks_plan.w);
 
     // nodes: exact turns; sum t_p mod 1 for the constant phase of Eq. 29
     launch_canon(x_dev, N, pl->T, s);
@@ -454,7 +457,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     // batched FFT on the transforms' grid), folded by Eq. 7 with Eq. 41's
     // coefficients and the deconvolution
     launch_plan_strengths(pl->T, N, (uint64_t)P, eta, str, s);
-    launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s);
+    launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s, ktab);
     double2* B = nullptr;
     if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
     launch_fold(B, prm.ns, prm.K0s, tab.fold, P, eta, vecP, s);
@@ -473,7 +476,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
     double2* gsp = nullptr;
     if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
-    launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s);
+    launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s, ktab);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
     launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
     if (f32) {
@@ -850,6 +853,8 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     int dev = 0;
     NUFFT_CUDA_TRY(cudaGetDevice(&dev));
     init_pool_once();
+    nufft_status st0 = plan_kernels_init();
+    if (st0 != NUFFT_OK) return st0;
     cudaStream_t s = (cudaStream_t)stream;
     nufft_plan_s* pl = new nufft_plan_s();
     pl->prm = prm;

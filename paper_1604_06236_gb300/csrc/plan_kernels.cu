@@ -2,6 +2,7 @@
 // the log-kernel spectrum, kernel samples, Lagrange-kernel coefficients and
 // node weights (Secs. III-C to III-E).
 #include "internal.h"
+#include "cis64.cuh"
 
 #include <cmath>
 
@@ -55,7 +56,7 @@ __global__ void k_mod(const uint64_t* __restrict__ T, const int* __restrict__ pe
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
     if (i >= cnt) return;
-    out[i] = cis_turns(K0 * T[perm[i]], sign);
+    out[i] = cis_turns_t(K0 * T[perm[i]], sign);
 }
 
 // Eq. 7 with Lambda = g's coefficients (Eq. 41), the deconvolution folded in:
@@ -83,7 +84,7 @@ __global__ void k_plan_strengths(const uint64_t* __restrict__ T, int64_t N, uint
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const uint64_t t = T[p];
-    for (int r = 0; r < eta; ++r) out[(int64_t)r * N + p] = cis_turns(P * (uint64_t)r * t, -1);
+    for (int r = 0; r < eta; ++r) out[(int64_t)r * N + p] = cis_turns_t(P * (uint64_t)r * t, -1);
 }
 
 // Eq. 29: K_q = exp(j P pi + j 2 pi sum_p t_p + v_q).  The constant phase is the
@@ -125,8 +126,8 @@ __global__ void k_weights(const uint64_t* __restrict__ T, const double2* __restr
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const uint64_t t = T[p];
-    const double2 e = cis_turns((uint64_t)N * t, -1);
-    const double2 z = cis_turns(t, +1);
+    const double2 e = cis_turns_t((uint64_t)N * t, -1);
+    const double2 z = cis_turns_t(t, +1);
     const double2 h = make_double2(rhoP * e.x - 1.0, rhoP * e.y);
     const double2 den = cmul(h, cmul(D[p], z));
     const double nn = den.x * den.x + den.y * den.y;
@@ -144,7 +145,7 @@ __global__ void k_slot_weights(const uint64_t* __restrict__ T, const int* __rest
     const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
     if (i >= cnt) return;
     const int p = perm[i];
-    const double2 m = cis_turns(K0 * T[p], sign);
+    const double2 m = cis_turns_t(K0 * T[p], sign);
     mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
     const double2 wm = cmul(w_user[p], m);
     wmod_out[i] = mk<TS>((TS)wm.x, (TS)wm.y);
@@ -235,5 +236,7 @@ template void launch_slot_weights<float>(const uint64_t*, const int*, int64_t, c
                                          const double2*, float2*, float2*, cudaStream_t);
 template void launch_slot_weights<double>(const uint64_t*, const int*, int64_t, const int*, uint64_t, int,
                                           const double2*, double2*, double2*, cudaStream_t);
+
+nufft_status plan_kernels_init() { return cis_table_ensure(); }
 
 }  // namespace nufft45

@@ -212,12 +212,17 @@ template <> struct FracPtr<double> { static const double* ext(const Geometry& g)
 
 constexpr int kChunk = 256;
 
+// ktab (optional): every kernel value the gather evaluates is also stored at
+// ktab[s w + m], s the node's sorted slot and m its tap (grid point
+// cell + 1 - w/2 + m), for the interpolation on the same geometry and kernel;
+// pre_at points at the count of prepended halo slots, N is the node count.
 template <typename T, int BC>
 __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, T beta, const int* __restrict__ cstart,
                                                 const int* __restrict__ eperm, const int* __restrict__ ecell,
                                                 const T* __restrict__ efrac, const c2<T>* __restrict__ src,
                                                 int64_t src_bs, const c2<T>* __restrict__ wt, c2<T>* __restrict__ grid,
-                                                int64_t batch) {
+                                                int64_t batch, T* __restrict__ ktab, const int* __restrict__ pre_at,
+                                                int64_t N) {
     __shared__ int s_cell[kChunk];
     __shared__ T s_frac[kChunk];
     __shared__ c2<T> s_str[BC][kChunk];
@@ -251,10 +256,16 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
         }
         __syncthreads();
         const int a = max(lo, ch), z = min(hi, ch + cnt);
+        const bool keep = ktab != nullptr && blockIdx.y == 0;
+        const int pre = keep ? *pre_at : 0;
         for (int i = a; i < z; ++i) {
             const int e = i - ch;
             const T d = (T)(g - s_cell[e]) - s_frac[e];
             const T ph = es_kernel<T>(d, two_over_w, beta);
+            if (keep) {
+                const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
+                ktab[slot * w + (g - s_cell[e]) + w / 2 - 1] = ph;
+            }
 #pragma unroll
             for (int b = 0; b < BC; ++b) {
                 acc[b].x = fma(ph, s_str[b][e].x, acc[b].x);
@@ -269,12 +280,13 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
     }
 }
 
+// ktab (optional): the kernel values k_spread stored for this geometry and kernel
 template <typename T, int BC>
 __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T two_over_w, T beta,
                                                 const int* __restrict__ sperm, const int* __restrict__ scell,
                                                 const T* __restrict__ sfrac, const c2<T>* __restrict__ grid,
                                                 const c2<T>* __restrict__ wt, c2<T>* __restrict__ dst, int64_t dst_bs,
-                                                int64_t batch) {
+                                                int64_t batch, const T* __restrict__ ktab) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t b0 = (int64_t)blockIdx.y * BC;
@@ -282,8 +294,13 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
     const T f = sfrac[i];
     const int h = w / 2;
     T ker[16];
+    if (ktab) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<T>((T)(m + 1 - h) - f, two_over_w, beta) : (T)0;
+        for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? ktab[i * w + m] : (T)0;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<T>((T)(m + 1 - h) - f, two_over_w, beta) : (T)0;
+    }
     c2<T> acc[BC];
 #pragma unroll
     for (int b = 0; b < BC; ++b) acc[b] = mk<T>(0, 0);
@@ -471,7 +488,7 @@ nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n
 
 template <typename T>
 void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs, const c2<T>* wt_ext,
-                   c2<T>* grid, int64_t batch, cudaStream_t s) {
+                   c2<T>* grid, int64_t batch, cudaStream_t s, T* ktab) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* ef = FracPtr<T>::ext(g);
     // the extended list may carry a wider halo (g.w >= ks.w): cell starts are
@@ -483,21 +500,21 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
         k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch);
+                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
         k_spread<T, 4><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch);
+                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     } else {
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
         k_spread<T, 8><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch);
+                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     }
 }
 
 template <typename T>
 void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt, c2<T>* dst,
-                   int64_t dst_bs, int64_t batch, cudaStream_t s) {
+                   int64_t dst_bs, int64_t batch, cudaStream_t s, const T* ktab) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* sf = FracPtr<T>::srt(g);
     const double es = sizeof(c2<T>);
@@ -505,11 +522,11 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
     if (batch == 1) {
         dim3 gr(nblk(g.N), 1);
         k_interp<T, 1><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch);
+                                          dst_bs, batch, ktab);
     } else {
         dim3 gr(nblk(g.N), (unsigned)((batch + 3) / 4));
         k_interp<T, 4><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch);
+                                          dst_bs, batch, ktab);
     }
 }
 
@@ -537,9 +554,9 @@ void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs
 
 #define INST(T)                                                                                                  \
     template void launch_spread<T>(const Geometry&, KernelShape, const c2<T>*, int64_t, const c2<T>*, c2<T>*,   \
-                                   int64_t, cudaStream_t);                                                       \
+                                   int64_t, cudaStream_t, T*);                                                   \
     template void launch_interp<T>(const Geometry&, KernelShape, const c2<T>*, const c2<T>*, c2<T>*, int64_t,   \
-                                   int64_t, cudaStream_t);                                                       \
+                                   int64_t, cudaStream_t, const T*);                                             \
     template void launch_select<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, int64_t, const T*, int64_t, \
                                    cudaStream_t);                                                                \
     template void launch_place<T>(const c2<T>*, int64_t, int64_t, int64_t, const T*, c2<T>*, int64_t, int64_t,  \
