@@ -239,4 +239,26 @@ template void launch_slot_weights<double>(const uint64_t*, const int*, int64_t, 
 
 nufft_status plan_kernels_init() { return cis_table_ensure(); }
 
+namespace {
+__global__ void k_debug_cis(const uint64_t* __restrict__ T, int64_t n, double2* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cis_turns_t(T[i], +1);
+}
+}  // namespace
+
 }  // namespace nufft45
+
+// Test hook (not part of the public header): out[i] = e^{j 2 pi T[i] / 2^64}
+// by the plan kernels' table-driven evaluation; device arrays of n entries.
+extern "C" nufft_status nufft_debug_cis(int64_t n, const uint64_t* T, void* out, nufft_stream_t stream) {
+    using namespace nufft45;
+    if (n < 0 || (n > 0 && (!T || !out))) return fail(NUFFT_ERR_ARG, "bad cis test arguments");
+    nufft_status st = plan_kernels_init();
+    if (st != NUFFT_OK || n == 0) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_debug_cis<<<nblk(n), kTB, 0, s>>>(T, n, static_cast<double2*>(out));
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
