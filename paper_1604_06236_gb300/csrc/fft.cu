@@ -471,7 +471,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
     return fn;
 }
 
-template <int R1, int R2>
+template <int R1, int R2, bool FUSE = false>
 nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta, int64_t batch, const float2* tw,
                             int dir, cudaStream_t s) {
     using G = p2t::TCfg<R1, R2>;
@@ -487,7 +487,7 @@ nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail(NUFFT_ERR_CUDA, "tensor map for a %d x %d FFT pass rejected", R1, R2);
-    auto kern = p2t::k_fft_p2t<R1, R2>;
+    auto kern = p2t::k_fft_p2t<R1, R2, FUSE>;
     constexpr size_t smem = p2t::smem_bytes<R1, R2>();
     static int per_sm = 0;
     if (!per_sm) {
@@ -538,6 +538,7 @@ nufft_status try_p2t(const FFTPlan& p, const c2<T>* in, c2<T>* out, const p2::Ar
         ta.out_bs = a.out_bs;
         ta.off = a.sel_off;
         ta.len = a.sel_len;
+        ta.fmul = nullptr;
         const float2* tw = static_cast<const float2*>(p.tw_full);
         nufft_status st = (a.R_log == 8) ? launch_p2t_one<16, 16>(in, out, ta, batch, tw, dir, s)
                                          : launch_p2t_one<32, 16>(in, out, ta, batch, tw, dir, s);
@@ -758,6 +759,72 @@ bool fft_scatter_supported(const FFTPlan& p) {
 }
 template bool fft_scatter_supported<float>(const FFTPlan&);
 template bool fft_scatter_supported<double>(const FFTPlan&);
+
+template <typename T>
+bool fft_conv_supported(const FFTPlan& p) {
+    return sizeof(T) == 4 && p.p2_rlog.size() == 2 && p.p2_rlog[0] == 8 && p.p2_rlog[1] == 8 &&
+           fft_scatter_supported<T>(p);
+}
+template bool fft_conv_supported<float>(const FFTPlan&);
+template bool fft_conv_supported<double>(const FFTPlan&);
+
+template <typename T>
+nufft_status fft_exec_conv(const FFTPlan& p, const c2<T>* in, c2<T>* w1, c2<T>* w2, c2<T>* out, int64_t batch,
+                           int dir, const c2<T>* fmul, const FFTHooks& h, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return fail(NUFFT_ERR_ARG, "the fused transform pair is float32 only");
+    } else {
+        if (!fft_conv_supported<T>(p)) return fail(NUFFT_ERR_ARG, "the fused transform pair needs n = 256 x 256");
+        if (batch <= 0) return NUFFT_OK;
+        const int L = 16;
+        const double vec = (double)p.n * (double)batch * sizeof(c2<T>);
+        // first transform, pass 1 (loads hook h.lop)
+        FFTHooks h1;
+        h1.lop = h.lop; h1.fac_in = h.fac_in;
+        {
+            p2::Args a{};
+            a.n_log = L; a.R_log = 8; a.Ns_log = 0; a.C_log = p2_C_log<T>(8);
+            a.total = (int)(batch << 8); a.shift = p.shift; a.tw_full = p.tw_full;
+            a.lop = h.lop; a.sop = 0; a.fac_in = h.fac_in;
+            Launch Lk(s, K_FFT, 2.0 * vec);
+            bool done = false;
+            nufft_status st = try_p2t<T>(p, in, w1, a, batch, dir, s, &done);
+            if (st != NUFFT_OK) return st;
+            if (!done) return fail(NUFFT_ERR_ARG, "fused transform pair: TMA pass unavailable");
+        }
+        // first transform's pass 2, x fmul, second transform's pass 1
+        {
+            Launch Lk(s, K_FFT, 2.0 * vec);
+            p2t::TArgs ta{};
+            ta.n_log = L; ta.R_log = 8; ta.Ns_log = 8; ta.C_log = p2_C_log<float>(8);
+            ta.ntiles = (int)((batch << 8) >> ta.C_log);
+            ta.fmul = reinterpret_cast<const float2*>(fmul);
+            nufft_status st = launch_p2t_one<16, 16, true>(reinterpret_cast<const float2*>(w1),
+                                                           reinterpret_cast<float2*>(w2), ta, batch,
+                                                           static_cast<const float2*>(p.tw_full), dir, s);
+            if (st != NUFFT_OK) return st;
+        }
+        // second transform, pass 2 (stores hook h.sop)
+        {
+            p2::Args a{};
+            a.n_log = L; a.R_log = 8; a.Ns_log = 8; a.C_log = p2_C_log<T>(8);
+            a.total = (int)(batch << 8); a.shift = p.shift; a.tw_full = p.tw_full;
+            a.lop = 0; a.sop = h.sop; a.mulc = h.mulc; a.fac_out = h.fac_out; a.out_bs = h.out_bs;
+            if (a.sop == 3) { a.sel_off = h.K0; a.sel_len = h.P; }
+            if (a.sop == 4) { a.sel_off = h.K0; a.sel_len = h.ns; }
+            Launch Lk(s, K_FFT, 2.0 * vec);
+            bool done = false;
+            nufft_status st = try_p2t<T>(p, w2, out, a, batch, -dir, s, &done);
+            if (st != NUFFT_OK) return st;
+            if (!done) return fail(NUFFT_ERR_ARG, "fused transform pair: TMA pass unavailable");
+        }
+        return NUFFT_OK;
+    }
+}
+template nufft_status fft_exec_conv<float>(const FFTPlan&, const float2*, float2*, float2*, float2*, int64_t, int,
+                                           const float2*, const FFTHooks&, cudaStream_t);
+template nufft_status fft_exec_conv<double>(const FFTPlan&, const double2*, double2*, double2*, double2*, int64_t,
+                                            int, const double2*, const FFTHooks&, cudaStream_t);
 
 template <typename T>
 bool fft_hooks_supported(const FFTPlan& p) {

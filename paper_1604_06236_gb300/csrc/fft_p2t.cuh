@@ -16,6 +16,14 @@
 // of C R.  The inner twiddles W_R^{m1 k2} sit in shared memory for the
 // lifetime of the CTA.  Every wait is bounded: on expiry the kernel counts the
 // event in g_wait_expired, drains its copies in flight and returns.
+//
+// FUSE (radix 16 x 16, two-pass length n = R^2 only): the last pass of one
+// transform, a pointwise product and the first pass of a second transform of
+// the opposite direction in one kernel.  The tile of the last pass (columns j,
+// all outputs j + m n/R) holds exactly the inputs j + k n/R of the second
+// transform's first-pass butterflies j, and after step B thread (c, m1)
+// holds outputs m = m1 + R1 m2, which is the step-A layout (k2 = m1, k1 = m2)
+// of that pass: the data never leaves the SM between the two passes.
 #pragma once
 #include <cuda.h>
 
@@ -44,6 +52,7 @@ constexpr int kPollLimit = 1 << 22;
 struct TArgs {
     int n_log, R_log, Ns_log, C_log;
     int ntiles;
+    const float2* fmul;   // FUSE: the pointwise factor between the two transforms (length n)
     // lop 2: x = in[idx] * fac_in[idx]; sop 1: y *= mulc[idx]; sop 2: y *= fac_out[idx];
     // sop 3: k = (idx + off) mod n, if k < len: out[b out_bs + k] = y fac_out[k];
     // sop 4: out[b out_bs + ((idx - off) mod len)] = y fac_out[idx]
@@ -99,10 +108,11 @@ __device__ __forceinline__ void issue(const CUtensorMap* tm, float2* st, uint64_
 // reads at the minimum number of shared-memory wavefronts
 __device__ __forceinline__ int swz(int c) { return (c & 7) << 1; }
 
-template <int R1, int R2>
+template <int R1, int R2, bool FUSE = false>
 __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     k_fft_p2t(const __grid_constant__ CUtensorMap tm, float2* __restrict__ out, TArgs a,
               const float2* __restrict__ tw, int dir) {
+    static_assert(!FUSE || R1 == R2, "the fused pair needs R1 = R2");
     using G = TCfg<R1, R2>;
     constexpr int R = G::R, C = G::C, TH = G::TH, NB = G::NB, TILE = G::TILE, S = kStages;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -193,7 +203,28 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
             for (int kk = 0; kk < R2; ++kk) w[q][kk] = st[(m1 * R2 + kk) * C + c];
             p2::dft_reg<R2, float>(w[q], dir);
         }
-        if (a.Ns_log >= a.C_log) {
+        if constexpr (FUSE) {
+            // x fmul at the outputs o = j + m n/R of the finished transform, then
+            // the second transform's first pass (direction -dir, Ns = 1) from
+            // registers: thread (c, m1) is its step-A thread (ca = c, k2 = m1)
+            const float2* fm = a.fmul + (j0 + ca);
+            float2 u[R1];
+#pragma unroll
+            for (int m2 = 0; m2 < R2; ++m2) u[m2] = cmul(w[0][m2], __ldg(&fm[(size_t)(k2 + R1 * m2) << a.Ns_log]));
+            p2::dft_reg<R1, float>(u, -dir);
+            if (k2 != 0) {
+#pragma unroll
+                for (int m1 = 1; m1 < R1; ++m1) u[m1] = cmul(u[m1], cconj(wi[m1 * k2]));
+            }
+            __syncthreads();   // every step-B read of the first transform is done
+#pragma unroll
+            for (int m1 = 0; m1 < R1; ++m1) st[(m1 * R2 + k2) * C + ca] = u[m1];
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < R2; ++kk) w[0][kk] = st[(k2 * R2 + kk) * C + ca];
+            p2::dft_reg<R2, float>(w[0], -dir);
+        }
+        if (!FUSE && a.Ns_log >= a.C_log) {
             // direct stores: for fixed m a warp writes runs of C consecutive butterflies
 #pragma unroll
             for (int q = 0; q < NB; ++q) {

@@ -107,6 +107,14 @@ struct FFTHooks {
 template <typename T> bool fft_hooks_supported(const FFTPlan& p);
 // the scattering stores (sop 3, 4) run on this plan: float32, two TMA-fed passes
 template <typename T> bool fft_scatter_supported(const FFTPlan& p);
+// out = FFT_{-dir}( fmul * FFT_{dir}(in) ) for two-pass n = 256 x 256 float32
+// plans, in three launches (the middle one runs the first transform's last
+// pass, the product and the second transform's first pass); h.lop applies to
+// the first loads, h.sop to the last stores; in -> w1 -> w2 -> out
+template <typename T> bool fft_conv_supported(const FFTPlan& p);
+template <typename T>
+nufft_status fft_exec_conv(const FFTPlan& p, const c2<T>* in, c2<T>* w1, c2<T>* w2, c2<T>* out, int64_t batch,
+                           int dir, const c2<T>* fmul, const FFTHooks& h, cudaStream_t s);
 // in -> out (never writes `in`; `work` and `out` are the ping-pong buffers)
 template <typename T>
 nufft_status fft_exec_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T>* out, int64_t batch, int dir,

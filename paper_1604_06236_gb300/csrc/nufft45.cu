@@ -524,6 +524,8 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
     const bool fused = fft_hooks_supported<T>(tab.fft_P);
     // selection and placement as scattering stores of the FFT passes
     const bool scatter = fft_scatter_supported<T>(tab.fft_ns) && fft_scatter_supported<T>(tab.fft_P);
+    // the IDFT's last pass, x K and the DFT's first pass in one kernel
+    const bool conv = scatter && fft_conv_supported<T>(tab.fft_P);
     const int64_t K0 = imod(prm.K0s, ns);
     switch (op) {
         case OP_INV5: {
@@ -536,6 +538,12 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 FFTHooks hs;
                 hs.sop = 3; hs.K0 = K0; hs.P = P; hs.out_bs = P; hs.fac_out = fac5;
                 if ((st = fft_exec_hooked<T>(tab.fft_ns, gA, gW, vA, bc, -1, hs, s)) != NUFFT_OK) return st;
+                if (conv) {
+                    FFTHooks hc;
+                    hc.sop = 2; hc.fac_out = sneg;
+                    if ((st = fft_exec_conv<T>(tab.fft_P, vA, vW, vA, out, bc, +1, K, hc, s)) != NUFFT_OK) return st;
+                    break;
+                }
                 FFTHooks h1;
                 h1.sop = 1; h1.mulc = K;
                 if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
@@ -572,19 +580,26 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 // outputs on the grid with Eq. 31 and the deconvolution folded
                 // into fac4 (the other ns - N grid points are zeroed); grid
                 // FFT; type-2; x w (Eq. 40)
-                FFTHooks h1;
-                h1.lop = 2; h1.fac_in = rpos;
-                h1.sop = 1; h1.mulc = K;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
                 const int64_t g0 = imod(P - K0, ns), gap = ns - P;
                 const int64_t first = std::min(gap, ns - g0);
                 if (first > 0)
                     NUFFT_CUDA_TRY(cudaMemset2DAsync(gA + g0, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * first, bc, s));
                 if (gap > first)
                     NUFFT_CUDA_TRY(cudaMemset2DAsync(gA, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * (gap - first), bc, s));
-                FFTHooks h2;
-                h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
+                if (conv) {
+                    FFTHooks hc;
+                    hc.lop = 2; hc.fac_in = rpos;
+                    hc.sop = 4; hc.K0 = K0; hc.ns = ns; hc.out_bs = ns; hc.fac_out = fac4;
+                    if ((st = fft_exec_conv<T>(tab.fft_P, in, vW, vA, gA, bc, +1, K, hc, s)) != NUFFT_OK) return st;
+                } else {
+                    FFTHooks h1;
+                    h1.lop = 2; h1.fac_in = rpos;
+                    h1.sop = 1; h1.mulc = K;
+                    if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                    FFTHooks h2;
+                    h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
+                    if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
+                }
                 if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
                 break;
