@@ -34,6 +34,15 @@ template <typename V> __host__ __device__ __forceinline__ V cfma(V acc, V a, V b
     return acc;
 }
 
+// Programmatic dependent launch: the library launches every kernel as a
+// dependent of the previous one in its stream, so a kernel's launch and CTA
+// scheduling overlap its predecessor's tail.  Every kernel therefore starts
+// with pdl_wait(), which returns once the predecessor grid has completed and
+// its memory operations are visible (at once for an ordinary launch), and
+// then allows its own successor to be scheduled with pdl_trigger().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // read-only-path load (the double-float types specialise it)
 template <typename X> __device__ __forceinline__ X ldg(const X* p) { return __ldg(p); }
 

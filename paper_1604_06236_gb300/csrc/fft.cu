@@ -147,6 +147,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_fft_pass(const c2<T>* in, c2<T>* out,  // may alias (single pass)
                                                        PassArgs a, const c2<T>* __restrict__ lo,
                                                        const c2<T>* __restrict__ hi, int dir) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c2<T>* s0 = reinterpret_cast<c2<T>*>(smem_raw);
     c2<T>* s1 = s0 + (size_t)a.C * a.PR;
@@ -203,6 +205,8 @@ __device__ __forceinline__ cdd to_cdd(double re, double im) {
 }
 
 __global__ void k_make_twiddles_full(int64_t n, double2* out_d, float2* out_f, cdd* out_x) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s, c;
@@ -214,12 +218,16 @@ __global__ void k_make_twiddles_full(int64_t n, double2* out_d, float2* out_f, c
 
 // in-place representation changes for the double-float FFTs (16 bytes either way)
 __global__ void k_to_dd(double2* buf, int64_t n) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double2 v = buf[i];
     reinterpret_cast<cdd*>(buf)[i] = to_cdd(v.x, v.y);
 }
 __global__ void k_from_dd(double2* buf, int64_t n) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const cdd v = reinterpret_cast<const cdd*>(buf)[i];
@@ -228,6 +236,8 @@ __global__ void k_from_dd(double2* buf, int64_t n) {
 
 __global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d, double2* hi_d,
                                 float2* lo_f, float2* hi_f, cdd* lo_x, cdd* hi_x) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {
         double s, c;
@@ -252,6 +262,8 @@ __global__ void k_make_twiddles(int64_t n, int64_t B, int64_t nhi, double2* lo_d
 // inverse filter conj(h).  Phases are reduced exactly: k^2 mod 2n.
 __global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chirp_f, cdd* chirp_x, double2* hf,
                              double2* hi) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int64_t k = -1;
@@ -273,6 +285,8 @@ __global__ void k_blue_chirp(int64_t n, int64_t m, double2* chirp_d, float2* chi
 }
 
 __global__ void k_scale_c128_to(const double2* in, int64_t m, double s, double2* out_d, float2* out_f, cdd* out_x) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     double2 v = in[i];
@@ -285,6 +299,8 @@ __global__ void k_scale_c128_to(const double2* in, int64_t m, double s, double2*
 template <typename T>
 __global__ void k_blue_pre(const c2<T>* __restrict__ x, int64_t n, int64_t m, const c2<T>* __restrict__ chirp,
                            int dir, int64_t batch, c2<T>* __restrict__ a) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m * batch) return;
     const int64_t b = i / m, j = i - b * m;
@@ -298,6 +314,8 @@ __global__ void k_blue_pre(const c2<T>* __restrict__ x, int64_t n, int64_t m, co
 
 template <typename T>
 __global__ void k_blue_mul(c2<T>* __restrict__ a, const c2<T>* __restrict__ h, int64_t m, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m * batch) return;
     a[i] = cmul(a[i], h[i % m]);
@@ -306,6 +324,8 @@ __global__ void k_blue_mul(c2<T>* __restrict__ a, const c2<T>* __restrict__ h, i
 template <typename T>
 __global__ void k_blue_post(const c2<T>* __restrict__ a, int64_t n, int64_t m, const c2<T>* __restrict__ chirp,
                             int dir, int64_t batch, c2<T>* __restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * batch) return;
     const int64_t b = i / n, k = i - b * n;
@@ -391,7 +411,7 @@ nufft_status launch_p2(int rlog, const c2<T>* in, c2<T>* out, p2::Args a, const 
     case RL: {                                                                                              \
         auto kern = p2::k_fft_p2<T, A, B>;                                                                  \
         NUFFT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        kern<<<blocks, threads, smem, s>>>(in, out, a, lo, hi, dir);                                        \
+        launch_k(kern, blocks, threads, smem, s, in, out, a, lo, hi, dir);                                        \
         break;                                                                                              \
     }
     switch (rlog) {
@@ -435,7 +455,7 @@ nufft_status launch_p2s_one(const c2<T>* in, c2<T>* out, p2::SArgs a, const c2<T
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(a.ntiles, per_sm * std::max(1, sms));
-    kern<<<grid, G::TH, smem, s>>>(in, out, a, tw, dir);
+    launch_k(kern, grid, G::TH, smem, s, in, out, a, tw, dir);
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
@@ -500,7 +520,7 @@ nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta,
     NUFFT_CUDA_TRY(cudaGetDevice(&dev));
     NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::min(ta.ntiles, per_sm * std::max(1, sms));
-    kern<<<grid, G::TH, smem, s>>>(tm, out, ta, tw, dir);
+    launch_k(kern, grid, G::TH, smem, s, tm, out, ta, tw, dir);
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
@@ -674,7 +694,7 @@ nufft_status exec_passes(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batc
         NUFFT_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         {
             Launch L(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
-            k_fft_pass<T><<<(unsigned)blocks, kThreads, smem, s>>>(src, dst, a, lo, hi, dir);
+            launch_k(k_fft_pass<T>, (unsigned)blocks, kThreads, smem, s, src, dst, a, lo, hi, dir);
         }
         NUFFT_CUDA_TRY(cudaGetLastError());
         src = dst;
@@ -906,7 +926,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
         NUFFT_CUDA_TRY(cudaMalloc(&p.chirp_hat_inv, es * m));
         const int tb = 256;
         Launch Lc(s, K_PLAN_TABLE, 48.0 * m);
-        k_blue_chirp<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
+        launch_k(k_blue_chirp, (unsigned)((m + tb - 1) / tb), tb, 0, s, 
             n, m, prec == 2 ? (double2*)p.chirp : nullptr, prec == 1 ? (float2*)p.chirp : nullptr,
             prec == 3 ? (cdd*)p.chirp : nullptr, hf, hi);
         NUFFT_CUDA_TRY(cudaGetLastError());
@@ -921,7 +941,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
             if (st != NUFFT_OK) return st;
             void* dst = which == 0 ? p.chirp_hat_fwd : p.chirp_hat_inv;
             Launch Ls(s, K_PLAN_TABLE, 32.0 * m);
-            k_scale_c128_to<<<(unsigned)((m + tb - 1) / tb), tb, 0, s>>>(
+            launch_k(k_scale_c128_to, (unsigned)((m + tb - 1) / tb), tb, 0, s, 
                 res, m, 1.0 / (double)m, prec == 2 ? (double2*)dst : nullptr, prec == 1 ? (float2*)dst : nullptr,
                 prec == 3 ? (cdd*)dst : nullptr);
             NUFFT_CUDA_TRY(cudaGetLastError());
@@ -943,7 +963,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     NUFFT_CUDA_TRY(cudaMalloc(&p.tw_hi, es * nhi));
     const int64_t cnt = std::max(B, nhi);
     Launch Lt(s, K_PLAN_TABLE, 16.0 * (B + nhi));
-    k_make_twiddles<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(
+    launch_k(k_make_twiddles, (unsigned)((cnt + 255) / 256), 256, 0, s, 
         n, B, nhi, prec == 2 ? (double2*)p.tw_lo : nullptr, prec == 2 ? (double2*)p.tw_hi : nullptr,
         prec == 1 ? (float2*)p.tw_lo : nullptr, prec == 1 ? (float2*)p.tw_hi : nullptr,
         prec == 3 ? (cdd*)p.tw_lo : nullptr, prec == 3 ? (cdd*)p.tw_hi : nullptr);
@@ -951,7 +971,7 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     if (n >= 2 && (n & (n - 1)) == 0 && n <= ((int64_t)1 << 24)) {
         NUFFT_CUDA_TRY(cudaMalloc(&p.tw_full, es * n));
         Launch Lf(s, K_PLAN_TABLE, 16.0 * n);
-        k_make_twiddles_full<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        launch_k(k_make_twiddles_full, (unsigned)((n + 255) / 256), 256, 0, s, 
             n, prec == 2 ? (double2*)p.tw_full : nullptr, prec == 1 ? (float2*)p.tw_full : nullptr,
             prec == 3 ? (cdd*)p.tw_full : nullptr);
         NUFFT_CUDA_TRY(cudaGetLastError());
@@ -971,7 +991,7 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
     const c2<T>* chirp = static_cast<const c2<T>*>(p.chirp);
     const int tb = 256;
     { Launch L(s, K_BLUESTEIN, (double)batch * (n + m) * sizeof(c2<T>) + n * sizeof(c2<T>), sizeof(T) == 8);
-    k_blue_pre<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(buf, n, m, chirp, dir, batch, a); }
+    launch_k(k_blue_pre<T>, (unsigned)((m * batch + tb - 1) / tb), tb, 0, s, buf, n, m, chirp, dir, batch, a); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r = nullptr;
     nufft_status st = p.sub->p2_rlog.empty() ? exec_passes<T>(*p.sub, a, aw, batch, -1, s, &r)
@@ -979,14 +999,14 @@ nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, 
     if (st != NUFFT_OK) return st;
     const c2<T>* h = static_cast<const c2<T>*>(dir < 0 ? p.chirp_hat_fwd : p.chirp_hat_inv);
     { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * m * sizeof(c2<T>), sizeof(T) == 8);
-      k_blue_mul<T><<<(unsigned)((m * batch + tb - 1) / tb), tb, 0, s>>>(r, h, m, batch); }
+      launch_k(k_blue_mul<T>, (unsigned)((m * batch + tb - 1) / tb), tb, 0, s, r, h, m, batch); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     c2<T>* r2 = nullptr;
     st = p.sub->p2_rlog.empty() ? exec_passes<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2)
                                 : exec_p2<T>(*p.sub, r, r == a ? aw : a, batch, +1, s, &r2);
     if (st != NUFFT_OK) return st;
     { Launch L(s, K_BLUESTEIN, (2.0 * batch + 1.0) * n * sizeof(c2<T>), sizeof(T) == 8);
-      k_blue_post<T><<<(unsigned)((n * batch + tb - 1) / tb), tb, 0, s>>>(r2, n, m, chirp, dir, batch, buf); }
+      launch_k(k_blue_post<T>, (unsigned)((n * batch + tb - 1) / tb), tb, 0, s, r2, n, m, chirp, dir, batch, buf); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     *result = buf;
     return NUFFT_OK;
@@ -1012,14 +1032,14 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
     const unsigned nb = (unsigned)((cnt + 255) / 256);
     {
         Launch L(s, K_FFT, 32.0 * cnt, true);
-        k_to_dd<<<nb, 256, 0, s>>>(buf, cnt);
+        launch_k(k_to_dd, nb, 256, 0, s, buf, cnt);
     }
     cdd* r = nullptr;
     nufft_status st = fft_exec<dd>(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r);
     if (st != NUFFT_OK) return st;
     {
         Launch L(s, K_FFT, 32.0 * cnt, true);
-        k_from_dd<<<nb, 256, 0, s>>>(reinterpret_cast<double2*>(r), cnt);
+        launch_k(k_from_dd, nb, 256, 0, s, reinterpret_cast<double2*>(r), cnt);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());
     *result = reinterpret_cast<double2*>(r);

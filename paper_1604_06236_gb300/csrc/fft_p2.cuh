@@ -147,6 +147,8 @@ template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(Cfg<T, R1, R2>::TH) k_fft_p2(const c2<T>* in, c2<T>* out, Args a,
                                                                const c2<T>* __restrict__ lo,
                                                                const c2<T>* __restrict__ hi, int dir) {
+    pdl_wait();
+    pdl_trigger();
     using G = Cfg<T, R1, R2>;
     constexpr int C = G::C, TH = G::TH, PR = G::PR, NB = G::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,6 +379,8 @@ template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(SCfg<T, R1, R2>::TH, SCfg<T, R1, R2>::kMinBlocks) k_fft_p2s(const c2<T>* __restrict__ in,
                                                                  c2<T>* __restrict__ out, SArgs a,
                                                                  const c2<T>* __restrict__ tw, int dir) {
+    pdl_wait();
+    pdl_trigger();
     using G = SCfg<T, R1, R2>;
     constexpr int R = G::R, C = G::C, NB = G::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -112,6 +112,8 @@ template <int R1, int R2, bool FUSE = false>
 __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     k_fft_p2t(const __grid_constant__ CUtensorMap tm, float2* __restrict__ out, TArgs a,
               const float2* __restrict__ tw, int dir) {
+    pdl_wait();
+    pdl_trigger();
     static_assert(!FUSE || R1 == R2, "the fused pair needs R1 = R2");
     using G = TCfg<R1, R2>;
     constexpr int R = G::R, C = G::C, TH = G::TH, NB = G::NB, TILE = G::TILE, S = kStages;

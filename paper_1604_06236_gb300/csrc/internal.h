@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "nufft45.h"
@@ -13,6 +14,25 @@ namespace nufft45 {
 
 nufft_status cuda_fail(cudaError_t e, const char* expr, const char* file, int line);
 nufft_status fail(nufft_status st, const char* fmt, ...);
+
+// Launch `kern` on stream s as a programmatic dependent of the previous kernel
+// in s (see pdl_wait in common.cuh: every kernel of the library waits for its
+// predecessor before touching memory).  Errors surface through
+// cudaGetLastError like a <<<>>> launch.
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ------------------------------------------------------------- tracing ----
 // Construct around every kernel launch: counts launches and, when tracing is

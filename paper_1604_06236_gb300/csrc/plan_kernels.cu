@@ -31,6 +31,8 @@ __device__ double phihat(double xi, int w, double beta, const GLRule& gl) {
 // 6: Lambda_k / phihat((k mod P) - K0), the fold of Eq. 7 over k = P r + m
 __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                         int64_t P, double* out_d, float* out_f) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M) return;
     double v;
@@ -53,6 +55,8 @@ __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, in
 // e^{sign j 2 pi K0 t_p} for p = perm[i], i < count (count read from device when given)
 __global__ void k_mod(const uint64_t* __restrict__ T, const int* __restrict__ perm, int64_t cap,
                       const int* __restrict__ count_dev, uint64_t K0, int sign, double2* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
     if (i >= cnt) return;
@@ -64,6 +68,8 @@ __global__ void k_mod(const uint64_t* __restrict__ T, const int* __restrict__ pe
 // B_r the spectrum of the strengths e^{-j 2 pi P r t_p} (grid n)
 __global__ void k_fold(const double2* __restrict__ B, int64_t n, int64_t K0, const double* __restrict__ fac,
                        int64_t P, int eta, double2* __restrict__ Y) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P) return;
     double2 acc = make_double2(0.0, 0.0);
@@ -81,6 +87,8 @@ __global__ void k_fold(const double2* __restrict__ B, int64_t n, int64_t K0, con
 // strengths of the log-kernel type-1: out[r][p] = e^{-j 2 pi P r t_p}, r < eta
 __global__ void k_plan_strengths(const uint64_t* __restrict__ T, int64_t N, uint64_t P, int eta,
                                  double2* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const uint64_t t = T[p];
@@ -91,6 +99,8 @@ __global__ void k_plan_strengths(const uint64_t* __restrict__ T, int64_t N, uint
 // exact turn count P 2^63 + sum T_p mod 2^64.
 __global__ void k_kernel_samples(const double2* __restrict__ v, int64_t P, const unsigned long long* __restrict__ sumT,
                                  double2* __restrict__ K, float2* __restrict__ Kf) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= P) return;
     const uint64_t C = (uint64_t)*sumT + (uint64_t)P * 0x8000000000000000ull;
@@ -107,6 +117,8 @@ __global__ void k_kernel_samples(const double2* __restrict__ v, int64_t P, const
 // d_m = (m + 1) L_{m+1}; rho_neg[m] = rho^{-m}/P.
 __global__ void k_lcoef(const double2* __restrict__ F, int64_t P, double rhoP, const double* __restrict__ rho_neg,
                         double2* __restrict__ d) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P) return;
     double2 L;
@@ -123,6 +135,8 @@ __global__ void k_lcoef(const double2* __restrict__ F, int64_t P, double rhoP, c
 // h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1).
 __global__ void k_weights(const uint64_t* __restrict__ T, const double2* __restrict__ D, int64_t N, double rhoP,
                           double2* __restrict__ w) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const uint64_t t = T[p];
@@ -141,6 +155,8 @@ __global__ void k_slot_weights(const uint64_t* __restrict__ T, const int* __rest
                                const int* __restrict__ count_dev, uint64_t K0, int sign,
                                const double2* __restrict__ w_user, c2<TS>* __restrict__ mod_out,
                                c2<TS>* __restrict__ wmod_out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
     if (i >= cnt) return;
@@ -190,47 +206,47 @@ void gauss_legendre_half(int nq, GLRule& r) {
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s) {
     Launch L(s, K_PLAN_TABLE, M * (out_d ? 8.0 : 4.0));
-    k_table<<<nblk(M), kTB, 0, s>>>(ks.w, ks.beta, gl, n, K0, M, log_rho, mode, P, out_d, out_f);
+    launch_k(k_table, nblk(M), kTB, 0, s, ks.w, ks.beta, gl, n, K0, M, log_rho, mode, P, out_d, out_f);
 }
 
 void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
                 double2* out, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, cap * 28.0);
-    k_mod<<<nblk(cap), kTB, 0, s>>>(T, perm, cap, count_dev, K0, sign, out);
+    launch_k(k_mod, nblk(cap), kTB, 0, s, T, perm, cap, count_dev, K0, sign, out);
 }
 
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, (double)eta * P * 24.0 + P * 16.0);
-    k_fold<<<nblk(P), kTB, 0, s>>>(B, n, K0, fac, P, eta, Y);
+    launch_k(k_fold, nblk(P), kTB, 0, s, B, n, K0, fac, P, eta, Y);
 }
 
 void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, double2* out, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, N * (8.0 + 16.0 * eta));
-    k_plan_strengths<<<nblk(N), kTB, 0, s>>>(T, N, P, eta, out);
+    launch_k(k_plan_strengths, nblk(N), kTB, 0, s, T, N, P, eta, out);
 }
 
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
                            cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, P * (Kf ? 40.0 : 32.0));
-    k_kernel_samples<<<nblk(P), kTB, 0, s>>>(v, P, sumT, K, Kf);
+    launch_k(k_kernel_samples, nblk(P), kTB, 0, s, v, P, sumT, K, Kf);
 }
 
 void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, P * 40.0);
-    k_lcoef<<<nblk(P), kTB, 0, s>>>(F, P, rhoP, rho_neg, d);
+    launch_k(k_lcoef, nblk(P), kTB, 0, s, F, P, rhoP, rho_neg, d);
 }
 
 void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, N * 40.0);
-    k_weights<<<nblk(N), kTB, 0, s>>>(T, D, N, rhoP, w);
+    launch_k(k_weights, nblk(N), kTB, 0, s, T, D, N, rhoP, w);
 }
 
 template <typename TS>
 void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
                          const double2* w_user, c2<TS>* mod_out, c2<TS>* wmod_out, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, cap * (28.0 + 4.0 * sizeof(TS)));
-    k_slot_weights<TS><<<nblk(cap), kTB, 0, s>>>(T, perm, cap, count_dev, K0, sign, w_user, mod_out, wmod_out);
+    launch_k(k_slot_weights<TS>, nblk(cap), kTB, 0, s, T, perm, cap, count_dev, K0, sign, w_user, mod_out, wmod_out);
 }
 template void launch_slot_weights<float>(const uint64_t*, const int*, int64_t, const int*, uint64_t, int,
                                          const double2*, float2*, float2*, cudaStream_t);
@@ -241,6 +257,8 @@ nufft_status plan_kernels_init() { return cis_table_ensure(); }
 
 namespace {
 __global__ void k_debug_cis(const uint64_t* __restrict__ T, int64_t n, double2* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = cis_turns_t(T[i], +1);
 }
@@ -256,7 +274,7 @@ extern "C" nufft_status nufft_debug_cis(int64_t n, const uint64_t* T, void* out,
     nufft_status st = plan_kernels_init();
     if (st != NUFFT_OK || n == 0) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    k_debug_cis<<<nblk(n), kTB, 0, s>>>(T, n, static_cast<double2*>(out));
+    launch_k(k_debug_cis, nblk(n), kTB, 0, s, T, n, static_cast<double2*>(out));
     NUFFT_CUDA_TRY(cudaGetLastError());
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     return NUFFT_OK;

@@ -22,6 +22,8 @@ constexpr int kTB = 256;
 inline unsigned nblk(int64_t n, int tb = kTB) { return (unsigned)((n + tb - 1) / tb); }
 
 __global__ void k_canon(const double* __restrict__ x, int64_t N, uint64_t* __restrict__ T) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     // t = x / (2 pi) mod 1 (IEEE division and floor), T = trunc(t 2^64)
@@ -34,6 +36,8 @@ __global__ void k_canon(const double* __restrict__ x, int64_t N, uint64_t* __res
 // cell = floor(n t) = high word of T*n, fraction = low word / 2^64, exactly
 __global__ void k_cells(const uint64_t* __restrict__ T, int64_t N, uint64_t n, int* __restrict__ cell,
                         double* __restrict__ frac, int* __restrict__ count) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint64_t t = T[i];
@@ -49,6 +53,8 @@ constexpr int kScanTB = 1024;
 constexpr int kScanPer = 2 * kScanTB;
 
 __global__ void k_scan_blocks(const int* __restrict__ in, int64_t L, int* __restrict__ out, int* __restrict__ sums) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s[kScanPer];
     const int64_t base = (int64_t)blockIdx.x * kScanPer;
     for (int e = threadIdx.x; e < kScanPer; e += blockDim.x) s[e] = (base + e < L) ? in[base + e] : 0;
@@ -79,6 +85,8 @@ __global__ void k_scan_blocks(const int* __restrict__ in, int64_t L, int* __rest
 }
 
 __global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict__ total) {
+    pdl_wait();
+    pdl_trigger();
     // one block, sequential over chunks of blockDim with a carry
     __shared__ int s[kScanTB];
     __shared__ int carry;
@@ -104,12 +112,16 @@ __global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict_
 }
 
 __global__ void k_scan_add(int* __restrict__ out, int64_t L, const int* __restrict__ sums) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < L) out[i] += sums[i / kScanPer];
 }
 
 __global__ void k_scatter(const int* __restrict__ cell, int64_t N, const int* __restrict__ start,
                           int* __restrict__ fill, int* __restrict__ perm) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int c = cell[i];
@@ -120,6 +132,8 @@ __global__ void k_scatter(const int* __restrict__ cell, int64_t N, const int* __
 // become neighbours for the duplicate check
 __global__ void k_order_cells(const int* __restrict__ start, int64_t n, const uint64_t* __restrict__ T,
                               int* __restrict__ perm) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int a = start[c], b = start[c + 1];
@@ -141,6 +155,8 @@ __global__ void k_order_cells(const int* __restrict__ start, int64_t n, const ui
 __global__ void k_sorted_fill(const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ frac,
                               const uint64_t* __restrict__ T, int64_t N, int* __restrict__ scell,
                               double* __restrict__ sfrac, float* __restrict__ sfracf, int* __restrict__ dup) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int p = perm[i];
@@ -161,6 +177,8 @@ __global__ void k_ext_fill(const int* __restrict__ start, int64_t n, int h, int6
                            const int* __restrict__ scell, const double* __restrict__ sfrac,
                            int* __restrict__ eperm, int* __restrict__ ecell, double* __restrict__ efrac,
                            float* __restrict__ efracf) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int pre = start[n] - start[n - h];
     const int post = start[h];
@@ -179,6 +197,8 @@ __global__ void k_ext_fill(const int* __restrict__ start, int64_t n, int h, int6
 
 // cstart[e], e = cell + w/2 in [0, n + w]
 __global__ void k_cstart(const int* __restrict__ start, int64_t n, int w, int64_t N, int* __restrict__ cstart) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int h = w / 2;
     if (e > n + w) return;
@@ -191,6 +211,8 @@ __global__ void k_cstart(const int* __restrict__ start, int64_t n, int w, int64_
 }
 
 __global__ void k_sum_turns(const uint64_t* __restrict__ T, int64_t N, unsigned long long* out) {
+    pdl_wait();
+    pdl_trigger();
     // sum mod 2^64 (exactly sum t_p mod 1); unsigned wrap-around is associative
     __shared__ unsigned long long s[kTB];
     unsigned long long acc = 0;
@@ -223,6 +245,8 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
                                                 int64_t src_bs, const c2<T>* __restrict__ wt, c2<T>* __restrict__ grid,
                                                 int64_t batch, T* __restrict__ ktab, const int* __restrict__ pre_at,
                                                 int64_t N) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_cell[kChunk];
     __shared__ T s_frac[kChunk];
     __shared__ c2<T> s_str[BC][kChunk];
@@ -287,6 +311,8 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
                                                 const T* __restrict__ sfrac, const c2<T>* __restrict__ grid,
                                                 const c2<T>* __restrict__ wt, c2<T>* __restrict__ dst, int64_t dst_bs,
                                                 int64_t batch, const T* __restrict__ ktab) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t b0 = (int64_t)blockIdx.y * BC;
@@ -330,6 +356,8 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
 template <typename T>
 __global__ void k_select(const c2<T>* __restrict__ in, int64_t n, c2<T>* __restrict__ out, int64_t out_bs, int64_t P,
                          int64_t K0, const T* __restrict__ fac, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P * batch) return;
     const int64_t b = i / P, k = i - b * P;
@@ -340,6 +368,8 @@ __global__ void k_select(const c2<T>* __restrict__ in, int64_t n, c2<T>* __restr
 template <typename T>
 __global__ void k_place(const c2<T>* __restrict__ in, int64_t in_bs, int64_t P, int64_t K0, const T* __restrict__ fac,
                         c2<T>* __restrict__ out, int64_t n, int64_t batch, int deriv) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * batch) return;
     const int64_t b = i / n, gidx = i - b * n;
@@ -358,6 +388,8 @@ __global__ void k_place(const c2<T>* __restrict__ in, int64_t in_bs, int64_t P, 
 template <typename T>
 __global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* __restrict__ out, int64_t out_bs,
                             int64_t P, const c2<T>* __restrict__ mulc, const T* __restrict__ fac, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P * batch) return;
     const int64_t b = i / P, k = i - b * P;
@@ -370,12 +402,16 @@ __global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* 
 // refinement helpers: widen to float64; r = in - y (in float64, stored in T); out += c
 template <typename T>
 __global__ void k_widen(const c2<T>* __restrict__ in, double2* __restrict__ out, int64_t n) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) { const c2<T> v = in[i]; out[i] = make_double2((double)v.x, (double)v.y); }
 }
 template <typename T>
 __global__ void k_residual(const c2<T>* __restrict__ in, const double2* __restrict__ y, c2<T>* __restrict__ r,
                            int64_t n) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const c2<T> v = in[i];
@@ -385,6 +421,8 @@ __global__ void k_residual(const c2<T>* __restrict__ in, const double2* __restri
 }
 template <typename T>
 __global__ void k_accumulate(c2<T>* __restrict__ out, const c2<T>* __restrict__ c, int64_t n) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = cadd(out[i], c[i]);
 }
@@ -393,6 +431,8 @@ __global__ void k_accumulate(c2<T>* __restrict__ out, const c2<T>* __restrict__ 
 template <typename T>
 __global__ void k_grad_nodes(const c2<T>* __restrict__ X, const c2<T>* __restrict__ Y, int64_t N, int64_t batch,
                              double scale, double* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= N) return;
     double acc = 0.0;
@@ -408,17 +448,17 @@ __global__ void k_grad_nodes(const c2<T>* __restrict__ X, const c2<T>* __restric
 template <typename T>
 void launch_widen(const c2<T>* in, double2* out, int64_t n, cudaStream_t s) {
     Launch L(s, K_POINTWISE, n * (sizeof(c2<T>) + 16.0), sizeof(T) == 8);
-    k_widen<T><<<nblk(n), kTB, 0, s>>>(in, out, n);
+    launch_k(k_widen<T>, nblk(n), kTB, 0, s, in, out, n);
 }
 template <typename T>
 void launch_residual(const c2<T>* in, const double2* y, c2<T>* r, int64_t n, cudaStream_t s) {
     Launch L(s, K_POINTWISE, n * (2.0 * sizeof(c2<T>) + 16.0), sizeof(T) == 8);
-    k_residual<T><<<nblk(n), kTB, 0, s>>>(in, y, r, n);
+    launch_k(k_residual<T>, nblk(n), kTB, 0, s, in, y, r, n);
 }
 template <typename T>
 void launch_accumulate(c2<T>* out, const c2<T>* c, int64_t n, cudaStream_t s) {
     Launch L(s, K_POINTWISE, n * 3.0 * sizeof(c2<T>), sizeof(T) == 8);
-    k_accumulate<T><<<nblk(n), kTB, 0, s>>>(out, c, n);
+    launch_k(k_accumulate<T>, nblk(n), kTB, 0, s, out, c, n);
 }
 #define INST_R(T)                                                                         \
     template void launch_widen<T>(const c2<T>*, double2*, int64_t, cudaStream_t);         \
@@ -432,7 +472,7 @@ template <typename T>
 void launch_grad_nodes(const c2<T>* X, const c2<T>* Y, int64_t N, int64_t batch, double scale, double* out,
                        cudaStream_t s) {
     Launch L(s, K_POINTWISE, 2.0 * batch * N * sizeof(c2<T>) + 8.0 * N, sizeof(T) == 8);
-    k_grad_nodes<T><<<nblk(N), kTB, 0, s>>>(X, Y, N, batch, scale, out);
+    launch_k(k_grad_nodes<T>, nblk(N), kTB, 0, s, X, Y, N, batch, scale, out);
 }
 template void launch_grad_nodes<float>(const float2*, const float2*, int64_t, int64_t, double, double*, cudaStream_t);
 template void launch_grad_nodes<double>(const double2*, const double2*, int64_t, int64_t, double, double*,
@@ -440,14 +480,14 @@ template void launch_grad_nodes<double>(const double2*, const double2*, int64_t,
 
 void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s) {
     Launch L(s, K_GEOMETRY, 16.0 * N);
-    k_canon<<<nblk(N), kTB, 0, s>>>(x, N, T);
+    launch_k(k_canon, nblk(N), kTB, 0, s, x, N, T);
 }
 
 void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     const int blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + kTB - 1) / kTB));
     Launch L(s, K_GEOMETRY, 8.0 * N);
-    k_sum_turns<<<blocks, kTB, 0, s>>>(T, N, out);
+    launch_k(k_sum_turns, blocks, kTB, 0, s, T, N, out);
 }
 
 int64_t geometry_scratch_ints(int64_t N, int64_t n) {
@@ -468,20 +508,20 @@ nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n
     const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
     NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
     NUFFT_CUDA_TRY(cudaMemsetAsync(g.dup_flag, 0, sizeof(int), s));
-    { Launch L(s, K_GEOMETRY, 24.0 * N); k_cells<<<nblk(N), kTB, 0, s>>>(T, N, (uint64_t)n, cell, frac, count); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); k_scan_blocks<<<(unsigned)nb, kScanTB, 0, s>>>(count, n + 1, start, sums); }
-    { Launch L(s, K_GEOMETRY, 8.0 * nb); k_scan_sums<<<1, kScanTB, 0, s>>>(sums, nb, sums + nb); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); k_scan_add<<<nblk(n + 1), kTB, 0, s>>>(start, n + 1, sums); }
+    { Launch L(s, K_GEOMETRY, 24.0 * N); launch_k(k_cells, nblk(N), kTB, 0, s, T, N, (uint64_t)n, cell, frac, count); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_scan_blocks, (unsigned)nb, kScanTB, 0, s, count, n + 1, start, sums); }
+    { Launch L(s, K_GEOMETRY, 8.0 * nb); launch_k(k_scan_sums, 1, kScanTB, 0, s, sums, nb, sums + nb); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_scan_add, nblk(n + 1), kTB, 0, s, start, n + 1, sums); }
     NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
-    { Launch L(s, K_GEOMETRY, 16.0 * N); k_scatter<<<nblk(N), kTB, 0, s>>>(cell, N, start, count, g.srt_perm); }
-    { Launch L(s, K_GEOMETRY, 4.0 * n + 16.0 * N); k_order_cells<<<nblk(n), kTB, 0, s>>>(start, n, T, g.srt_perm); }
+    { Launch L(s, K_GEOMETRY, 16.0 * N); launch_k(k_scatter, nblk(N), kTB, 0, s, cell, N, start, count, g.srt_perm); }
+    { Launch L(s, K_GEOMETRY, 4.0 * n + 16.0 * N); launch_k(k_order_cells, nblk(n), kTB, 0, s, start, n, T, g.srt_perm); }
     { Launch L(s, K_GEOMETRY, 44.0 * N);
-    k_sorted_fill<<<nblk(N), kTB, 0, s>>>(g.srt_perm, cell, frac, T, N, g.srt_cell, g.srt_frac,
+    launch_k(k_sorted_fill, nblk(N), kTB, 0, s, g.srt_perm, cell, frac, T, N, g.srt_cell, g.srt_frac,
                                           want_float ? g.srt_fracf : nullptr, g.dup_flag); }
     { Launch L(s, K_GEOMETRY, 40.0 * N);
-    k_ext_fill<<<nblk(2 * N), kTB, 0, s>>>(start, n, w / 2, N, g.srt_perm, g.srt_cell, g.srt_frac, g.ext_perm,
+    launch_k(k_ext_fill, nblk(2 * N), kTB, 0, s, start, n, w / 2, N, g.srt_perm, g.srt_cell, g.srt_frac, g.ext_perm,
                                            g.ext_cell, g.ext_frac, want_float ? g.ext_fracf : nullptr); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); k_cstart<<<nblk(n + w + 1), kTB, 0, s>>>(start, n, w, N, g.cstart); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_cstart, nblk(n + w + 1), kTB, 0, s, start, n, w, N, g.cstart); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
@@ -499,15 +539,15 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
                               batch * g.n * es, sizeof(T) == 8);
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
-        k_spread<T, 1><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        launch_k(k_spread<T, 1>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
-        k_spread<T, 4><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        launch_k(k_spread<T, 4>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     } else {
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
-        k_spread<T, 8><<<gr, kTB, 0, s>>>(g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
+        launch_k(k_spread<T, 8>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     }
 }
@@ -521,11 +561,11 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
     Launch L(s, K_INTERP, batch * g.n * es + g.N * (8.0 + sizeof(T) + es) + batch * g.N * es, sizeof(T) == 8);
     if (batch == 1) {
         dim3 gr(nblk(g.N), 1);
-        k_interp<T, 1><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
+        launch_k(k_interp<T, 1>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch, ktab);
     } else {
         dim3 gr(nblk(g.N), (unsigned)((batch + 3) / 4));
-        k_interp<T, 4><<<gr, kTB, 0, s>>>(g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
+        launch_k(k_interp<T, 4>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch, ktab);
     }
 }
@@ -534,14 +574,14 @@ template <typename T>
 void launch_select(const c2<T>* in, int64_t n, c2<T>* out, int64_t out_bs, int64_t P, int64_t K0, const T* fac,
                    int64_t batch, cudaStream_t s) {
     Launch L(s, K_SELECT, 2.0 * batch * P * sizeof(c2<T>) + P * sizeof(T), sizeof(T) == 8);
-    k_select<T><<<nblk(P * batch), kTB, 0, s>>>(in, n, out, out_bs, P, K0, fac, batch);
+    launch_k(k_select<T>, nblk(P * batch), kTB, 0, s, in, n, out, out_bs, P, K0, fac, batch);
 }
 
 template <typename T>
 void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T* fac, c2<T>* out, int64_t n,
                   int64_t batch, cudaStream_t s, bool deriv) {
     Launch L(s, K_PLACE, batch * (P + n) * sizeof(c2<T>) + P * sizeof(T), sizeof(T) == 8);
-    k_place<T><<<nblk(n * batch), kTB, 0, s>>>(in, in_bs, P, K0, fac, out, n, batch, deriv ? 1 : 0);
+    launch_k(k_place<T>, nblk(n * batch), kTB, 0, s, in, in_bs, P, K0, fac, out, n, batch, deriv ? 1 : 0);
 }
 
 template <typename T>
@@ -549,7 +589,7 @@ void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs
                       const T* fac, int64_t batch, cudaStream_t s) {
     Launch L(s, K_POINTWISE, 2.0 * batch * P * sizeof(c2<T>) + (mulc ? P * sizeof(c2<T>) : 0) +
                                  (fac ? P * sizeof(T) : 0), sizeof(T) == 8);
-    k_pointwise<T><<<nblk(P * batch), kTB, 0, s>>>(in, in_bs, out, out_bs, P, mulc, fac, batch);
+    launch_k(k_pointwise<T>, nblk(P * batch), kTB, 0, s, in, in_bs, out, out_bs, P, mulc, fac, batch);
 }
 
 #define INST(T)                                                                                                  \
