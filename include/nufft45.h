@@ -98,6 +98,25 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
                         nufft_plan_t* plan);
 
 /*
+ * nufft_plan_ex -- nufft_plan with the method's parameters set explicitly
+ * (Sec. V) instead of derived from `tol`: used to study the error against the
+ * attenuation mu of Eq. 49, mu = e^{-2 pi (eta N - 1) a} / (eta N - 1) with
+ * gamma = e^{2 pi N a}, and to trade accuracy for plan time.  A field <= 0
+ * keeps the value nufft_plan would choose for (tol, prec); `params` may be
+ * NULL.  Out-of-range fields return NUFFT_ERR_ARG.  The accuracy then follows
+ * from the parameters, not from `tol`, which still selects the defaults.
+ */
+typedef struct {
+    double gamma;  /* damping gamma = rho^{-N} = e^{2 pi N a}, in (1, 1e12] */
+    int eta;       /* oversampling of the log-kernel spectrum, R = eta N (Eqs. 41, 42), in [1, 64] */
+    int w_plan;    /* spreading width of the plan's float64 NUFFTs (even, 4..16) */
+    int w_solve;   /* spreading width of the transforms (even, 4..16) */
+} nufft_params_t;
+
+nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                           nufft_stream_t stream, nufft_plan_t* plan);
+
+/*
  * nufft_inv5 -- type-5 NUFFT (Eq. 48): given samples s(t_p) of
  *   s(t) = sum_{m<N} S_m e^{j 2 pi m t}, return S.  Method of Sec. III,
  *   Fig. 1 (lower half): a_p = s(t_p) w_p (Eq. 27), type-1 NUFFT,

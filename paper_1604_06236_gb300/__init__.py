@@ -13,7 +13,7 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "DEFER_CHECK", "build", "library_path", "ProfileEntry", "check"]
+__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "DEFER_CHECK", "Params", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
@@ -59,6 +59,11 @@ class Instance(ctypes.Structure):
                 ("kind", ctypes.c_int)]
 
 
+class Params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("eta", ctypes.c_int), ("w_plan", ctypes.c_int),
+                ("w_solve", ctypes.c_int)]
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -73,6 +78,8 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.nufft_plan.argtypes = [i64, vp, dbl, i32, vp, ctypes.POINTER(vp)]
+        L.nufft_plan_ex.argtypes = [i64, vp, dbl, i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+        L.nufft_plan_ex.restype = i32
         for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
@@ -142,7 +149,7 @@ class Plan:
     prec FP32: complex64 data, float64 node weights; prec FP64: complex128.
     """
 
-    def __init__(self, x, tol=None, prec=FP32, stream=None):
+    def __init__(self, x, tol=None, prec=FP32, stream=None, gamma=None, eta=None, w_plan=None, w_solve=None):
         import torch
         if not isinstance(x, torch.Tensor):
             x = torch.as_tensor(x)
@@ -156,7 +163,14 @@ class Plan:
         self.device = x.device if x.is_cuda else torch.device("cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         self._x_keep = x
-        check(lib().nufft_plan(self.N, _ptr(x), float(tol), int(prec), _stream_handle(stream), ctypes.byref(self._h)))
+        if gamma is None and eta is None and w_plan is None and w_solve is None:
+            check(lib().nufft_plan(self.N, _ptr(x), float(tol), int(prec), _stream_handle(stream),
+                                   ctypes.byref(self._h)))
+        else:
+            # explicit method parameters (Sec. V); None keeps the tol-derived value
+            q = Params(float(gamma or 0.0), int(eta or 0), int(w_plan or 0), int(w_solve or 0))
+            check(lib().nufft_plan_ex(self.N, _ptr(x), float(tol), int(prec), ctypes.byref(q),
+                                      _stream_handle(stream), ctypes.byref(self._h)))
 
     def check(self):
         """Wait for the plan; raise NufftError(NUFFT_ERR_DUP_NODES) if two nodes

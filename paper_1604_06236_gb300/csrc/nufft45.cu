@@ -135,14 +135,36 @@ static nufft_status choose_params(int64_t N, double tol, int prec, Params& p) {
         w_plan = 12;
         w_solve = 8;
     }
+    p.ks_solve = es_shape(w_solve);
+    p.ks_plan = es_shape(w_plan);
+    return NUFFT_OK;
+}
+
+// explicit parameters (fields <= 0 keep the defaults), then the derived quantities
+static nufft_status apply_params(const nufft_params_t* q, Params& p) {
+    if (q) {
+        if (q->gamma > 0) {
+            if (!(q->gamma > 1.0) || !std::isfinite(q->gamma) || q->gamma > 1e12)
+                return fail(NUFFT_ERR_ARG, "gamma %g out of range (1, 1e12]", q->gamma);
+            p.gamma = q->gamma;
+        }
+        if (q->eta > 0) {
+            if (q->eta > 64) return fail(NUFFT_ERR_ARG, "eta %d out of range [1, 64]", q->eta);
+            p.eta = q->eta;
+        }
+        for (int w : {q->w_plan, q->w_solve})
+            if (w > 0 && (w < 4 || w > 16 || (w & 1)))
+                return fail(NUFFT_ERR_ARG, "spreading width %d is not an even number in [4, 16]", w);
+        if (q->w_plan > 0) p.ks_plan = es_shape(q->w_plan);
+        if (q->w_solve > 0) p.ks_solve = es_shape(q->w_solve);
+    }
+    const int64_t N = p.N;
     p.log_rho = -std::log(p.gamma) / (double)N;
     p.a = std::log(p.gamma) / (2.0 * M_PI * (double)N);
     p.rho = std::exp(p.log_rho);
     p.rhoP = 1.0 / p.gamma;
     p.R = (int64_t)p.eta * N;
-    p.ks_solve = es_shape(w_solve);
-    p.ks_plan = es_shape(w_plan);
-    const int wmax = std::max(w_solve, w_plan);
+    const int wmax = std::max(p.ks_solve.w, p.ks_plan.w);
     p.ns = grid_size(std::max<int64_t>(2 * N, 2 * wmax));
     p.K0s = N / 2;
     p.K0R = p.R / 2;
@@ -171,7 +193,7 @@ struct Tables {
 
 using TablesPtr = std::shared_ptr<Tables>;
 static std::mutex g_cache_mu;
-static std::map<std::tuple<int64_t, int, double>, TablesPtr> g_cache;
+static std::map<std::tuple<int64_t, int, double, double, int, int, int>, TablesPtr> g_cache;
 
 static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& out) {
     TablesPtr t = std::make_shared<Tables>();
@@ -222,7 +244,7 @@ static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& ou
 
 static nufft_status get_tables(const Params& prm, cudaStream_t s, TablesPtr& out) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto key = std::make_tuple(prm.N, prm.prec, prm.tol);
+    auto key = std::make_tuple(prm.N, prm.prec, prm.tol, prm.gamma, prm.eta, prm.ks_plan.w, prm.ks_solve.w);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) { out = it->second; return NUFFT_OK; }
     nufft_status st = make_tables(prm, s, out);
@@ -849,6 +871,11 @@ nufft_status grad_nodes_public(nufft_plan_t plan, int kind, const void* p1, cons
 extern "C" {
 
 nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream, nufft_plan_t* plan) {
+    return nufft_plan_ex(N, x, tol, prec, nullptr, stream, plan);
+}
+
+nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                           nufft_stream_t stream, nufft_plan_t* plan) {
     if (!plan) return fail(NUFFT_ERR_ARG, "null plan output pointer");
     *plan = nullptr;
     if (N < 1 || N > ((int64_t)1 << 28)) return fail(NUFFT_ERR_ARG, "N = %lld out of range [1, 2^28]", (long long)N);
@@ -863,6 +890,7 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     Params prm;
     nufft_status st = choose_params(N, tol, prec, prm);
     if (st != NUFFT_OK) return st;
+    if ((st = apply_params(params, prm)) != NUFFT_OK) return st;
     prm.refine = refine;
     if (refine) prm.halo = std::max(prm.ks_solve.w, prm.ks_plan.w);
     int dev = 0;
