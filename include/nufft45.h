@@ -117,6 +117,23 @@ nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, con
                            nufft_stream_t stream, nufft_plan_t* plan);
 
 /*
+ * nufft_plan_tune -- choose (gamma, eta, plan width) for these nodes, `tol`
+ * and precision on this GPU (Sec. V leaves the choice open; on GB300 the
+ * float64 plan's cost grows with eta).  Candidates: for each gamma in a fixed
+ * set (float32 path: 30 .. 3000, plan widths 10 and 12; float64 path: 100 ..
+ * 1e4) the smallest eta with the truncation error 0.4 gamma^-eta below tol/10.
+ * Each candidate is accepted if the round trips c -> type-2 -> inv5 and
+ * c -> type-1 -> inv4 on `batch` test vectors return c within tol/2, and
+ * timed (plan + inv5 + inv4 of `batch` vectors, best of 3); the fastest
+ * accepted set is written to *best (its time to *best_ms when not NULL) and
+ * cached: later nufft_plan calls with the same (N, prec, tol) use it.
+ * prec is NUFFT_FP32 or NUFFT_FP64 (no flags); 1 <= batch <= 1024.
+ * Synchronises `stream`.  NUFFT_ERR_ACCURACY if no candidate met tol.
+ */
+nufft_status nufft_plan_tune(int64_t N, const double* x, double tol, int prec, int64_t batch, nufft_stream_t stream,
+                             nufft_params_t* best, double* best_ms);
+
+/*
  * nufft_inv5 -- type-5 NUFFT (Eq. 48): given samples s(t_p) of
  *   s(t) = sum_{m<N} S_m e^{j 2 pi m t}, return S.  Method of Sec. III,
  *   Fig. 1 (lower half): a_p = s(t_p) w_p (Eq. 27), type-1 NUFFT,
@@ -305,8 +322,9 @@ nufft_status nufft_plan_check(nufft_plan_t plan);
 nufft_status nufft_stream_check(nufft_stream_t stream);
 
 /* Drop the cache of node-independent tables (deconvolution and scaling
- * factors, FFT twiddles) kept per (N, precision, tolerance).  Plans that are
- * alive keep their own reference. */
+ * factors, FFT twiddles) kept per (N, precision, tolerance, parameters) and
+ * the parameter sets nufft_plan_tune chose.  Plans that are alive keep their
+ * own reference. */
 nufft_status nufft_cache_clear(void);
 
 /*

@@ -80,6 +80,8 @@ def lib():
         L.nufft_plan.argtypes = [i64, vp, dbl, i32, vp, ctypes.POINTER(vp)]
         L.nufft_plan_ex.argtypes = [i64, vp, dbl, i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
         L.nufft_plan_ex.restype = i32
+        L.nufft_plan_tune.argtypes = [i64, vp, dbl, i32, i64, vp, ctypes.POINTER(Params), ctypes.POINTER(dbl)]
+        L.nufft_plan_tune.restype = i32
         for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
@@ -130,6 +132,23 @@ def _stream_handle(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def plan_tune(x, tol=None, prec=FP32, batch=8, stream=None):
+    """Choose (gamma, eta, plan width) for these nodes and tol (nufft_plan_tune);
+    returns (params dict, best milliseconds).  Later plans with the same
+    (N, prec, tol) use the result."""
+    import torch
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(x)
+    x = x.to(torch.float64).contiguous()
+    if tol is None:
+        tol = 1e-5 if prec == FP32 else 1e-10
+    q = Params()
+    ms = ctypes.c_double()
+    check(lib().nufft_plan_tune(x.numel(), _ptr(x), float(tol), int(prec), int(batch), _stream_handle(stream),
+                                ctypes.byref(q), ctypes.byref(ms)))
+    return {"gamma": q.gamma, "eta": q.eta, "w_plan": q.w_plan, "w_solve": q.w_solve}, ms.value
 
 
 def stream_check(stream=None):

@@ -194,6 +194,8 @@ struct Tables {
 using TablesPtr = std::shared_ptr<Tables>;
 static std::mutex g_cache_mu;
 static std::map<std::tuple<int64_t, int, double, double, int, int, int>, TablesPtr> g_cache;
+// parameters nufft_plan_tune chose, per (N, precision, tol); nufft_plan uses them
+static std::map<std::tuple<int64_t, int, double>, nufft_params_t> g_tuned;
 
 static nufft_status make_tables(const Params& prm, cudaStream_t s, TablesPtr& out) {
     TablesPtr t = std::make_shared<Tables>();
@@ -890,6 +892,12 @@ nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, con
     Params prm;
     nufft_status st = choose_params(N, tol, prec, prm);
     if (st != NUFFT_OK) return st;
+    nufft_params_t tuned;
+    if (!params) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_tuned.find(std::make_tuple(N, prec, tol));
+        if (it != g_tuned.end()) { tuned = it->second; params = &tuned; }
+    }
     if ((st = apply_params(params, prm)) != NUFFT_OK) return st;
     prm.refine = refine;
     if (refine) prm.halo = std::max(prm.ks_solve.w, prm.ks_plan.w);
@@ -973,6 +981,138 @@ nufft_status nufft_inv4_grad_nodes(nufft_plan_t plan, const void* w, const void*
     return grad_nodes_public(plan, 4, w, a, batch, grad_x, stream);
 }
 
+// ------------------------------------------------------- parameter tuner ---
+namespace {
+
+// deterministic CN(0,1)-like test vectors (a linear congruential generator;
+// their statistics do not matter, only that the round trip exercises every
+// coefficient)
+void test_vector(std::vector<double>& v, uint64_t seed) {
+    uint64_t z = seed * 0x9E3779B97F4A7C15ull + 1;
+    for (auto& e : v) {
+        z = z * 6364136223846793005ull + 1442695040888963407ull;
+        e = ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5) * 2.449489742783178;   // unit variance
+    }
+}
+
+double rel_err(const std::vector<double>& a, const std::vector<double>& b) {
+    double num = 0, den = 0;
+    for (size_t i = 0; i < a.size(); ++i) { num += (a[i] - b[i]) * (a[i] - b[i]); den += b[i] * b[i]; }
+    return std::sqrt(num / den);
+}
+
+}  // namespace
+
+nufft_status nufft_plan_tune(int64_t N, const double* x, double tol, int prec, int64_t batch, nufft_stream_t stream,
+                             nufft_params_t* best, double* best_ms) {
+    if (!best) return fail(NUFFT_ERR_ARG, "null result pointer");
+    if (prec != NUFFT_FP32 && prec != NUFFT_FP64) return fail(NUFFT_ERR_ARG, "precision %d", prec);
+    if (batch < 1 || batch > 1024) return fail(NUFFT_ERR_ARG, "batch %lld out of range [1, 1024]", (long long)batch);
+    if (!(tol > 0.0) || !std::isfinite(tol) || tol > 0.1) return fail(NUFFT_ERR_ARG, "tol %g out of range (0, 0.1]", tol);
+    cudaStream_t s = (cudaStream_t)stream;
+    Params dflt;
+    nufft_status st = choose_params(N, tol, prec, dflt);
+    if (st != NUFFT_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_tuned.erase(std::make_tuple(N, prec, tol));
+    }
+    // candidates: truncation 0.4 gamma^-eta (Sec. V, measured law) at most tol / 10
+    std::vector<nufft_params_t> cands;
+    const double gammas32[] = {30, 100, 300, 1000, 3000};
+    const double gammas64[] = {100, 1000, 10000};
+    const int wps32[] = {10, 12};
+    // (the smallest such eta per gamma: a larger eta only costs plan time)
+    auto min_eta = [&](double g) {
+        int eta = 1;
+        while (eta < 24 && 0.4 * std::pow(g, -eta) > tol / 10) ++eta;
+        return eta;
+    };
+    if (prec == NUFFT_FP32) {
+        for (double g : gammas32)
+            for (int wp : wps32) cands.push_back({g, min_eta(g), wp, 0});
+    } else {
+        for (double g : gammas64) cands.push_back({g, min_eta(g), 0, 0});
+    }
+    const size_t es = prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t n = (size_t)N * (size_t)batch;
+    std::vector<double> c(2 * n), back(2 * n);
+    test_vector(c, 1);
+    std::vector<char> hc(es * n), hb(es * n);
+    auto to_data = [&](const std::vector<double>& v, std::vector<char>& h) {
+        if (prec == NUFFT_FP64) std::memcpy(h.data(), v.data(), es * n);
+        else for (size_t i = 0; i < 2 * n; ++i) reinterpret_cast<float*>(h.data())[i] = (float)v[i];
+    };
+    auto from_data = [&](const std::vector<char>& h, std::vector<double>& v) {
+        if (prec == NUFFT_FP64) std::memcpy(v.data(), h.data(), es * n);
+        else for (size_t i = 0; i < 2 * n; ++i) v[i] = reinterpret_cast<const float*>(h.data())[i];
+    };
+    to_data(c, hc);
+    if (prec == NUFFT_FP32) from_data(hc, c);   // compare against the rounded input
+    Arena buf;
+    if ((st = buf.reserve(3 * es * n + 512, s)) != NUFFT_OK) return st;
+    char* d0 = buf.take<char>(es * n);
+    char* d1 = buf.take<char>(es * n);
+    char* d2 = buf.take<char>(es * n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    bool found = false;
+    double best_t = 1e300;
+    for (const nufft_params_t& q : cands) {
+        nufft_plan_t pl = nullptr;
+        st = nufft_plan_ex(N, x, tol, prec, &q, stream, &pl);
+        if (st == NUFFT_ERR_DUP_NODES) break;
+        if (st != NUFFT_OK) continue;
+        // a posteriori accuracy: c -> type-2 -> inv5 and c -> type-1 -> inv4
+        double err = 0;
+        cudaError_t ce = cudaMemcpyAsync(d0, hc.data(), es * n, cudaMemcpyHostToDevice, s);
+        for (int kind = 5; kind >= 4 && ce == cudaSuccess && st == NUFFT_OK; --kind) {
+            st = kind == 5 ? nufft_fwd2(pl, d0, d1, batch, stream) : nufft_fwd1(pl, d0, d1, batch, stream);
+            if (st == NUFFT_OK) st = kind == 5 ? nufft_inv5(pl, d1, d2, batch, stream) : nufft_inv4(pl, d1, d2, batch, stream);
+            if (st == NUFFT_OK) ce = cudaMemcpyAsync(hb.data(), d2, es * n, cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce == cudaSuccess && st == NUFFT_OK) {
+                from_data(hb, back);
+                err = std::max(err, rel_err(back, c));
+            }
+        }
+        if (ce != cudaSuccess) { nufft_destroy(pl); buf.release(); cudaEventDestroy(e0); cudaEventDestroy(e1);
+                                 return cuda_fail(ce, "tuner", __FILE__, __LINE__); }
+        nufft_destroy(pl);
+        if (st != NUFFT_OK || !(err <= tol / 2)) { st = NUFFT_OK; continue; }
+        // time: plan + inv5 + inv4 on `batch` vectors, best of 3
+        double t = 1e300;
+        for (int r = 0; r < 3 && st == NUFFT_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = nufft_plan_ex(N, x, tol, prec | NUFFT_DEFER_CHECK, &q, stream, &pl);
+            if (st == NUFFT_OK) st = nufft_inv5(pl, d1, d2, batch, stream);
+            if (st == NUFFT_OK) st = nufft_inv4(pl, d1, d2, batch, stream);
+            cudaEventRecord(e1, s);
+            if (pl) nufft_destroy(pl);
+            pl = nullptr;
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = NUFFT_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, (double)ms);
+        }
+        if (st != NUFFT_OK) { st = NUFFT_OK; continue; }
+        if (t < best_t) { best_t = t; *best = q; found = true; }
+    }
+    buf.release();
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NUFFT_OK) return st;
+    if (!found) return fail(NUFFT_ERR_ACCURACY, "no candidate parameter set met tol %g on these nodes", tol);
+    if (best->w_plan <= 0) best->w_plan = dflt.ks_plan.w;
+    if (best->w_solve <= 0) best->w_solve = dflt.ks_solve.w;
+    if (best_ms) *best_ms = best_t;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_tuned[std::make_tuple(N, prec, tol)] = *best;
+    return NUFFT_OK;
+}
+
 nufft_status nufft_destroy(nufft_plan_t plan) {
     if (!plan) return NUFFT_OK;
     // stream-ordered release: work already queued on the plan's stream keeps
@@ -1024,6 +1164,7 @@ nufft_status nufft_stream_check(nufft_stream_t stream) {
 nufft_status nufft_cache_clear(void) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_cache.clear();
+    g_tuned.clear();
     return NUFFT_OK;
 }
 
