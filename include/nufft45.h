@@ -67,7 +67,15 @@ typedef enum {
      * for them to read back the duplicate-node check.  The check still runs
      * on the device; nufft_plan_check reports it.  Device node arrays must
      * then stay valid until the plan's kernels have run (stream order). */
-    NUFFT_DEFER_CHECK = 0x200
+    NUFFT_DEFER_CHECK = 0x200,
+    /* OR-ed into the precision: nufft_inv5/nufft_inv4 apply the middle stage
+     * (Eqs. 37, 30, 31) in its equivalent linear-convolution form
+     * S_m = c_m + rho^P c_{m+P}, c = L * A, with the Lagrange coefficients
+     * L_0..L_P of Eq. 43 (no counterpart in the paper's text; it follows from
+     * Eqs. 10, 30, 31 by expanding K_q = L(rho e^{j 2 pi q/P})).  The solve then
+     * carries no rho^{-m} scaling, whose round-off grows with gamma; it costs
+     * two FFTs of the grid size instead of two of size N. */
+    NUFFT_TOEPLITZ = 0x400
 } nufft_prec;
 
 /*
@@ -87,8 +95,8 @@ typedef enum {
  * tol    target relative L2 error: NUFFT_FP64 accepts [1e-12, 1e-1],
  *        NUFFT_FP32 accepts [1e-6, 1e-1]; tighter values return
  *        NUFFT_ERR_ACCURACY, non-finite or <= 0 values NUFFT_ERR_ARG.
- * prec   NUFFT_FP32 or NUFFT_FP64, optionally | NUFFT_REFINE and/or
- *        | NUFFT_DEFER_CHECK.
+ * prec   NUFFT_FP32 or NUFFT_FP64, optionally | NUFFT_REFINE,
+ *        | NUFFT_DEFER_CHECK and | NUFFT_TOEPLITZ.
  * plan   receives the plan; owned by the caller, release with nufft_destroy.
  * The call synchronises `stream` once to check for coincident nodes: two
  * nodes whose turns t differ by less than 2^-44 modulo 1 make the systems of

@@ -13,12 +13,13 @@ library raises.
 import ctypes
 import os
 
-__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "DEFER_CHECK", "Params", "build", "library_path", "ProfileEntry", "check"]
+__all__ = ["lib", "Plan", "Batch", "NufftError", "FP32", "FP64", "REFINE", "DEFER_CHECK", "TOEPLITZ", "Params", "build", "library_path", "ProfileEntry", "check"]
 
 FP32 = 1
 FP64 = 2
 REFINE = 0x100   # OR into the precision: one refinement step per inverse (Sec. V)
 DEFER_CHECK = 0x200   # OR into the precision: the plan call does not wait for the duplicate-node check
+TOEPLITZ = 0x400   # OR into the precision: middle stage as a linear convolution with L (no rho^-m scaling)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "lib", "libnufft45.so")

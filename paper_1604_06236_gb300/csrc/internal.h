@@ -226,6 +226,15 @@ void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, do
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
                            cudaStream_t s);
 void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s);
+// L_0 .. L_P (Eq. 43) from F = DFT(K), zero-padded to n
+void launch_lagrange_pad(const double2* F, int64_t P, double rhoP, const double* rho_neg, int64_t n, double2* out,
+                         cudaStream_t s);
+template <typename TS>
+void launch_to_solve(const double2* in, int64_t n, double scale, c2<TS>* out, cudaStream_t s);
+// out[b][m] = c[b][m] + rho^P c[b][m + P], m < P (c of batch stride n)
+template <typename T>
+void launch_conv_fold(const c2<T>* c, int64_t n, int64_t P, double rhoP, c2<T>* out, int64_t out_bs, int64_t batch,
+                      cudaStream_t s);
 void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s);
 template <typename TS>
 void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,

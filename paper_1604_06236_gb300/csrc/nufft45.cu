@@ -95,6 +95,7 @@ struct Params {
     int64_t K0s = 0, K0R = 0;
     KernelShape ks_solve{0, 0}, ks_plan{0, 0};
     bool refine = false;   // one refinement step per inverse (Sec. V)
+    bool toeplitz = false; // middle stage as a linear convolution with L (no rho^-m scaling)
     int halo = 0;          // halo width of the transforms' extended node list
 };
 
@@ -277,6 +278,7 @@ struct nufft_plan_s {
     double2* modm64_ext = nullptr;   // float64 e^{-j 2 pi K0 t}, extended slot order
     double2* modp64_srt = nullptr;   // float64 e^{+j 2 pi K0 t}, sorted slot order
     int64_t chunk = 1;
+    void* FL = nullptr;              // DFT of L_0..L_P zero-padded to ns, / ns (solve precision; toeplitz)
     int* dup_host = nullptr;         // pinned copy of the duplicate-node flag
     cudaEvent_t dup_ev = nullptr;    // recorded after that copy
 };
@@ -422,6 +424,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     z.add<char>(es * P);
     z.add<char>(es * 2 * N); z.add<char>(es * 2 * N); z.add<char>(es * N); z.add<char>(es * N);
     z.add<double2>(2 * N); z.add<double2>(N);
+    if (prm.toeplitz) z.add<char>(es * prm.ns);
     nufft_status st = pl->mem.reserve(z.used, s);
     if (st != NUFFT_OK) return st;
     Arena& m = pl->mem;
@@ -443,6 +446,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     pl->wt4_srt = m.take<char>(es * N);
     pl->modm64_ext = m.take<double2>(2 * N);
     pl->modp64_srt = m.take<double2>(N);
+    if (prm.toeplitz) pl->FL = m.take<char>(es * prm.ns);
 
     // temporaries of the plan
     const int eta = prm.eta;
@@ -496,6 +500,15 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     if ((st = fft_exec_dd(tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
     double2* dco = (F == vecP) ? workP : vecP;
     launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
+    if (prm.toeplitz) {
+        // DFT of L_0..L_P zero-padded to the grid size (ns >= 2P), / ns, for
+        // the middle stage as a linear convolution
+        launch_lagrange_pad(F, P, prm.rhoP, tab.sneg64, prm.ns, grid, s);
+        double2* FLd = nullptr;
+        if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, 1, -1, s, &FLd)) != NUFFT_OK) { tmp.release(); return st; }
+        if (f32) launch_to_solve<float>(FLd, prm.ns, 1.0 / (double)prm.ns, (float2*)pl->FL, s);
+        else launch_to_solve<double>(FLd, prm.ns, 1.0 / (double)prm.ns, (double2*)pl->FL, s);
+    }
     // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
     launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
     double2* gsp = nullptr;
@@ -551,6 +564,39 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
     // the IDFT's last pass, x K and the DFT's first pass in one kernel
     const bool conv = scatter && fft_conv_supported<T>(tab.fft_P);
     const int64_t K0 = imod(prm.K0s, ns);
+    if (prm.toeplitz && (op == OP_INV5 || op == OP_INV4)) {
+        // middle stage as S_m = c_m + rho^P c_{m+P}, c = L * A (linear
+        // convolution with the Lagrange coefficients, by length-ns FFTs):
+        // the same operator as Eqs. 37, 30, 31 without their rho^{+-k} scalings
+        c2<T>* X = nullptr;
+        if (op == OP_INV5) {
+            launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            X = (r == gA) ? gW : gA;
+            NUFFT_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(c2<T>) * ns * bc, s));
+            launch_select<T>(r, ns, X, ns, P, prm.K0s, fac1, bc, s);   // A_k, k < P (type-1, Eq. 25)
+        } else {
+            X = gA;
+            NUFFT_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(c2<T>) * ns * bc, s));
+            NUFFT_CUDA_TRY(cudaMemcpy2DAsync(X, sizeof(c2<T>) * ns, in, sizeof(c2<T>) * N, sizeof(c2<T>) * N, bc,
+                                             cudaMemcpyDeviceToDevice, s));
+        }
+        c2<T>* Y = nullptr;
+        if ((st = fft_exec<T>(tab.fft_ns, X, X == gA ? gW : gA, bc, -1, s, &Y)) != NUFFT_OK) return st;
+        launch_pointwise<T>(Y, ns, Y, ns, ns, (const c2<T>*)pl->FL, nullptr, bc, s);
+        c2<T>* c = nullptr;
+        if ((st = fft_exec<T>(tab.fft_ns, Y, Y == gA ? gW : gA, bc, +1, s, &c)) != NUFFT_OK) return st;
+        if (op == OP_INV5) {
+            launch_conv_fold<T>(c, ns, P, prm.rhoP, out, N, bc, s);
+        } else {
+            launch_conv_fold<T>(c, ns, P, prm.rhoP, vA, P, bc, s);
+            launch_place<T>(vA, P, P, prm.K0s, fac1, gA, ns, bc, s);   // type-2 of S (Eq. 39)
+            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
+        }
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        return NUFFT_OK;
+    }
     switch (op) {
         case OP_INV5: {
             launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
@@ -884,10 +930,12 @@ nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, con
     if (!x) return fail(NUFFT_ERR_ARG, "null node pointer");
     const bool refine = (prec & NUFFT_REFINE) != 0;
     const bool defer = (prec & NUFFT_DEFER_CHECK) != 0;
-    prec &= ~(NUFFT_REFINE | NUFFT_DEFER_CHECK);
+    const bool toeplitz = (prec & NUFFT_TOEPLITZ) != 0;
+    prec &= ~(NUFFT_REFINE | NUFFT_DEFER_CHECK | NUFFT_TOEPLITZ);
     if (prec != NUFFT_FP32 && prec != NUFFT_FP64)
         return fail(NUFFT_ERR_ARG,
-                    "precision %d is not NUFFT_FP32/NUFFT_FP64 (optionally | NUFFT_REFINE | NUFFT_DEFER_CHECK)", prec);
+                    "precision %d is not NUFFT_FP32/NUFFT_FP64 (optionally | NUFFT_REFINE | NUFFT_DEFER_CHECK | "
+                    "NUFFT_TOEPLITZ)", prec);
     if (!(tol > 0.0) || !std::isfinite(tol) || tol > 0.1) return fail(NUFFT_ERR_ARG, "tol %g out of range (0, 0.1]", tol);
     Params prm;
     nufft_status st = choose_params(N, tol, prec, prm);
@@ -900,6 +948,7 @@ nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, con
     }
     if ((st = apply_params(params, prm)) != NUFFT_OK) return st;
     prm.refine = refine;
+    prm.toeplitz = toeplitz;
     if (refine) prm.halo = std::max(prm.ks_solve.w, prm.ks_plan.w);
     int dev = 0;
     NUFFT_CUDA_TRY(cudaGetDevice(&dev));

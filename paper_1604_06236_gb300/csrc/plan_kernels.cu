@@ -131,6 +131,33 @@ __global__ void k_lcoef(const double2* __restrict__ F, int64_t P, double rhoP, c
     d[m] = make_double2((double)k * L.x, (double)k * L.y);
 }
 
+// The coefficients L_0 .. L_P of Eq. 43 (L_P = 1) zero-padded to n >= 2P, for
+// the linear-convolution form of the middle stage
+__global__ void k_lagrange_pad(const double2* __restrict__ F, int64_t P, double rhoP, const double* __restrict__ rho_neg,
+                               int64_t n, double2* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double2 L = make_double2(0.0, 0.0);
+    if (m == P) {
+        L.x = 1.0;
+    } else if (m < P) {
+        double2 f = F[m];
+        if (m == 0) f.x -= (double)P * rhoP;   // the delta term of Eq. 43
+        L = make_double2(f.x * rho_neg[m], f.y * rho_neg[m]);
+    }
+    out[m] = L;
+}
+
+template <typename TS>
+__global__ void k_to_solve(const double2* __restrict__ in, int64_t n, double scale, c2<TS>* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = mk<TS>((TS)(in[i].x * scale), (TS)(in[i].y * scale));
+}
+
 // Eqs. 27 / 40: w_p = h(-P t_p + j P a) / (L'(z_p) z_p) with
 // h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1).
 __global__ void k_weights(const uint64_t* __restrict__ T, const double2* __restrict__ D, int64_t N, double rhoP,
@@ -236,6 +263,20 @@ void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_ne
     Launch L(s, K_PLAN_STAGE, P * 40.0);
     launch_k(k_lcoef, nblk(P), kTB, 0, s, F, P, rhoP, rho_neg, d);
 }
+
+void launch_lagrange_pad(const double2* F, int64_t P, double rhoP, const double* rho_neg, int64_t n, double2* out,
+                         cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, P * 24.0 + n * 16.0);
+    launch_k(k_lagrange_pad, nblk(n), kTB, 0, s, F, P, rhoP, rho_neg, n, out);
+}
+
+template <typename TS>
+void launch_to_solve(const double2* in, int64_t n, double scale, c2<TS>* out, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, n * (16.0 + sizeof(c2<TS>)));
+    launch_k(k_to_solve<TS>, nblk(n), kTB, 0, s, in, n, scale, out);
+}
+template void launch_to_solve<float>(const double2*, int64_t, double, float2*, cudaStream_t);
+template void launch_to_solve<double>(const double2*, int64_t, double, double2*, cudaStream_t);
 
 void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s) {
     Launch L(s, K_PLAN_STAGE, N * 40.0);

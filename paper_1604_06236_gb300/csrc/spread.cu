@@ -399,6 +399,20 @@ __global__ void k_pointwise(const c2<T>* __restrict__ in, int64_t in_bs, c2<T>* 
     out[b * out_bs + k] = v;
 }
 
+// middle stage in linear-convolution form: S_m = c_m + rho^P c_{m+P}, m < P,
+// from the length-n (n >= 2P) convolution c of each right-hand side
+template <typename T>
+__global__ void k_conv_fold(const c2<T>* __restrict__ c, int64_t n, int64_t P, T rhoP, c2<T>* __restrict__ out,
+                            int64_t out_bs, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * batch) return;
+    const int64_t b = i / P, m = i - b * P;
+    const c2<T> lo = c[b * n + m], hi = c[b * n + m + P];
+    out[b * out_bs + m] = mk<T>(lo.x + rhoP * hi.x, lo.y + rhoP * hi.y);
+}
+
 // refinement helpers: widen to float64; r = in - y (in float64, stored in T); out += c
 template <typename T>
 __global__ void k_widen(const c2<T>* __restrict__ in, double2* __restrict__ out, int64_t n) {
@@ -585,6 +599,13 @@ void launch_place(const c2<T>* in, int64_t in_bs, int64_t P, int64_t K0, const T
 }
 
 template <typename T>
+void launch_conv_fold(const c2<T>* c, int64_t n, int64_t P, double rhoP, c2<T>* out, int64_t out_bs, int64_t batch,
+                      cudaStream_t s) {
+    Launch L(s, K_POINTWISE, 3.0 * batch * P * sizeof(c2<T>), sizeof(T) == 8);
+    launch_k(k_conv_fold<T>, nblk(P * batch), kTB, 0, s, c, n, P, (T)rhoP, out, out_bs, batch);
+}
+
+template <typename T>
 void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs, int64_t P, const c2<T>* mulc,
                       const T* fac, int64_t batch, cudaStream_t s) {
     Launch L(s, K_POINTWISE, 2.0 * batch * P * sizeof(c2<T>) + (mulc ? P * sizeof(c2<T>) : 0) +
@@ -601,6 +622,8 @@ void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs
                                    cudaStream_t);                                                                \
     template void launch_place<T>(const c2<T>*, int64_t, int64_t, int64_t, const T*, c2<T>*, int64_t, int64_t,  \
                                   cudaStream_t, bool);                                                           \
+    template void launch_conv_fold<T>(const c2<T>*, int64_t, int64_t, double, c2<T>*, int64_t, int64_t,         \
+                                      cudaStream_t);                                                             \
     template void launch_pointwise<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, const c2<T>*, const T*,  \
                                       int64_t, cudaStream_t);
 INST(float)

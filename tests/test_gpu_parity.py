@@ -287,3 +287,36 @@ def test_refinement_on_clustered_nodes(prec):
         e1 = oracle.rel_l2(_np(getattr(refined, op)(_dev(s, prec))), ref)
         assert e1 <= TOL_INV[prec]
         assert e1 <= e0 * 1.01
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("N", [1, 17, 256, 1000, 1009, 4096])
+def test_toeplitz_middle_stage_vs_lu(N, prec):
+    """NUFFT_TOEPLITZ (the middle stage as S_m = c_m + rho^P c_{m+P}, c = L * A)
+    against Gaussian elimination, element by element, at the default
+    parameters."""
+    x = synth.jittered_nodes(N, 0.45, seed=N + 31)
+    s = synth.cn01(N, seed=N + 32)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec | pkg.TOEPLITZ)
+    sr = _rounded(s, prec)
+    assert oracle.rel_l2(_np(plan.inv5(_dev(s, prec))), oracle.inv5(x, sr)) <= TOL_INV[prec]
+    assert oracle.rel_l2(_np(plan.inv4(_dev(s, prec))), oracle.inv4(x, sr)) <= TOL_INV[prec]
+
+
+def test_toeplitz_avoids_rho_amplification():
+    """float32 solves at a strong damping (gamma = 1e4, eta = 2): the scaled
+    middle stage of Eqs. 37/30/31 loses accuracy with gamma, the convolution
+    form keeps the float32 solve near its usual error."""
+    N = 4096
+    x = synth.jittered_nodes(N, 0.45, seed=41)
+    s = synth.cn01(N, seed=42)
+    sr = _rounded(s, FP32)
+    ref5, ref4 = oracle.inv5(x, sr), oracle.inv4(x, sr)
+    errs = {}
+    for name, prec in (("scaled", FP32), ("toeplitz", FP32 | pkg.TOEPLITZ)):
+        plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec, gamma=1e4, eta=2)
+        errs[name] = max(oracle.rel_l2(_np(plan.inv5(_dev(s, FP32))), ref5),
+                         oracle.rel_l2(_np(plan.inv4(_dev(s, FP32))), ref4))
+    print(errs)
+    assert errs["toeplitz"] <= TOL_INV[FP32]
+    assert errs["toeplitz"] < errs["scaled"] / 3
