@@ -197,6 +197,27 @@ def test_lagrange_factorisation_identities(P, gamma):
     np.testing.assert_allclose(w[None, :] * h1, cauchy, rtol=1e-10, atol=1e-12 * np.abs(cauchy).max())
 
 
+@pytest.mark.parametrize("P,gamma", [(16, 10.0), (24, 300.0)])
+def test_middle_stage_convolution_identity(P, gamma):
+    """The middle stage of Eqs. 37, 30, 31, S_m = rho^-m/P DFT(K P IDFT(rho^k A))_m
+    (IDFT with 1/P), equals c_m + rho^P c_{m+P} with c the linear convolution of
+    the coefficients L_0..L_P of prod (z - z_p) with A (reading C-7): K from the
+    oracle, L from numpy's own expansion (np.poly, which rounds badly beyond ~24
+    roots on the circle), the products by numpy."""
+    x = synth.jittered_nodes(P, 0.45, seed=7 * P)
+    t = oracle.canon(x)[1]
+    A = synth.cn01(P, seed=11)
+    rho = oracle.rho_of_gamma(P, gamma)
+    K = oracle.kernel_samples(x, rho)
+    k = np.arange(P)
+    sigma = P * np.fft.ifft(rho ** k * A)
+    S_scaled = rho ** (-k) / P * np.fft.fft(K * sigma)
+    L = np.poly(np.exp(2j * np.pi * t))[::-1]          # L_0 .. L_P, L_P = 1
+    c = np.convolve(L, A)                               # length 2P
+    S_conv = c[:P] + rho ** P * c[P:2 * P]
+    np.testing.assert_allclose(S_scaled, S_conv, rtol=1e-9, atol=1e-10 * np.abs(S_conv).max())
+
+
 @pytest.mark.parametrize("which", ["inv5", "inv4"])
 def test_vjp_against_finite_differences(which):
     """The oracle's gradients of L = ||inv(x, d) - c_t||^2 against central
