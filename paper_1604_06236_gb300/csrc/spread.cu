@@ -10,6 +10,7 @@
 // written once with coalesced stores: no atomics on the grid, deterministic
 // summation order.
 #include "internal.h"
+#include "df.cuh"
 
 #include <algorithm>
 
@@ -305,6 +306,83 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
 }
 
 // ktab (optional): the kernel values k_spread stored for this geometry and kernel
+__constant__ float2 c_exp2_64[64] = NUFFT_EXP2_64_TABLE;
+
+// The float64 spread with the kernel values and the accumulation in
+// double-float arithmetic (float pairs, ~2^-47): on GB300 the float64 pipe
+// issues at 1/64 of the float32 rate, and exp/sqrt per tap made the float64
+// spread bound by it.  Same gather and tables as k_spread; the float64 inputs
+// are converted once per staged node, the outputs once per grid point.
+template <int BC>
+__global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
+                                                   const int* __restrict__ cstart, const int* __restrict__ eperm,
+                                                   const int* __restrict__ ecell, const double* __restrict__ efrac,
+                                                   const double2* __restrict__ src, int64_t src_bs,
+                                                   const double2* __restrict__ wt, double2* __restrict__ grid,
+                                                   int64_t batch, double* __restrict__ ktab,
+                                                   const int* __restrict__ pre_at, int64_t N) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ int s_cell[kChunk];
+    __shared__ dd s_frac[kChunk];
+    __shared__ cdd s_str[BC][kChunk];
+    __shared__ float2 s_exp[64];
+    if (threadIdx.x < 64) s_exp[threadIdx.x] = c_exp2_64[threadIdx.x];
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t g = g0 + threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * BC;
+    const int64_t glast = min(g0 + (int64_t)blockDim.x, n) - 1;
+    const int t0 = cstart[g0], t1 = cstart[glast + w];
+    int lo = 0, hi = 0;
+    if (g < n) { lo = cstart[g]; hi = cstart[g + w]; }
+    cdd acc[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) { acc[b].x = dd(0.f, 0.f); acc[b].y = dd(0.f, 0.f); }
+    for (int ch = t0; ch < t1; ch += kChunk) {
+        const int cnt = min(kChunk, t1 - ch);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int i = ch + e;
+            s_cell[e] = ecell[i];
+            s_frac[e] = dd_from_double(efrac[i]);
+            const double2 wv = wt[i];
+            const int p = src ? eperm[i] : 0;
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                double2 v = wv;
+                if (src) v = (b0 + b < batch) ? cmul(src[(b0 + b) * src_bs + p], wv) : make_double2(0.0, 0.0);
+                cdd c;
+                c.x = dd_from_double(v.x);
+                c.y = dd_from_double(v.y);
+                s_str[b][e] = c;
+            }
+        }
+        __syncthreads();
+        const int a = max(lo, ch), z = min(hi, ch + cnt);
+        const bool keep = ktab != nullptr && blockIdx.y == 0;
+        const int pre = keep ? *pre_at : 0;
+        for (int i = a; i < z; ++i) {
+            const int e = i - ch;
+            const dd d = dd((float)(g - s_cell[e]), 0.f) - s_frac[e];
+            const dd ph = es_kernel_dd(d, 0.5f * (float)w, beta, s_exp);
+            if (keep) {
+                const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
+                ktab[slot * w + (g - s_cell[e]) + w / 2 - 1] = dd_to_double(ph);
+            }
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                acc[b].x += ph * s_str[b][e].x;
+                acc[b].y += ph * s_str[b][e].y;
+            }
+        }
+    }
+    if (g < n) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b0 + b < batch) grid[(b0 + b) * n + g] = make_double2(dd_to_double(acc[b].x), dd_to_double(acc[b].y));
+    }
+}
+
 template <typename T, int BC>
 __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T two_over_w, T beta,
                                                 const int* __restrict__ sperm, const int* __restrict__ scell,
@@ -551,6 +629,23 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
     const double es = sizeof(c2<T>);
     Launch L(s, K_SPREAD, (src ? batch * g.N * es : 0.0) + g.N * (es + 8.0 + sizeof(T)) + 4.0 * (g.n + g.w) +
                               batch * g.n * es, sizeof(T) == 8);
+    if constexpr (sizeof(T) == 8) {
+        const dd beta_dd(ks.beta);
+        const double* efd = g.ext_frac;
+        const double2* sd = reinterpret_cast<const double2*>(src);
+        const double2* wd = reinterpret_cast<const double2*>(wt_ext);
+        double2* gd = reinterpret_cast<double2*>(grid);
+        double* kd = reinterpret_cast<double*>(ktab);
+        if (batch == 1) {
+            launch_k(k_spread_dd<1>, dim3(nblk(g.n), 1), kTB, 0, s, g.n, ks.w, beta_dd, cs, g.ext_perm,
+                     g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2, g.N);
+        } else {
+            launch_k(k_spread_dd<4>, dim3(nblk(g.n), (unsigned)((batch + 3) / 4)), kTB, 0, s, g.n, ks.w,
+                     beta_dd, cs, g.ext_perm, g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2,
+                     g.N);
+        }
+        return;
+    }
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
         launch_k(k_spread<T, 1>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
