@@ -551,14 +551,24 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
     c2<T>* r = nullptr;
     // the middle stage of Eqs. 37, 30, 31 on the vector in vA (already scaled
     // by rho^k); returns the pointer holding DFT(K * P IDFT(.)) before rho^-m/P
+    // float64 data goes through the double-float transforms (float pairs on the
+    // float32 pipes, ~2^-48): GB300 issues float64 at 1/64 of the float32 rate
+    auto fft = [&](bool grid_size, c2<T>* buf, c2<T>* work, int dir, c2<T>** res) -> nufft_status {
+        if constexpr (sizeof(T) == 8) {
+            return fft_exec_dd(grid_size ? tab.fft_ns64 : tab.fft_P64, reinterpret_cast<double2*>(buf),
+                               reinterpret_cast<double2*>(work), bc, dir, s, reinterpret_cast<double2**>(res));
+        } else {
+            return fft_exec<T>(grid_size ? tab.fft_ns : tab.fft_P, buf, work, bc, dir, s, res);
+        }
+    };
     auto middle = [&](c2<T>** res) -> nufft_status {
         c2<T>* r1 = nullptr;
-        nufft_status e = fft_exec<T>(tab.fft_P, vA, vW, bc, +1, s, &r1);
+        nufft_status e = fft(false, vA, vW, +1, &r1);
         if (e != NUFFT_OK) return e;
         launch_pointwise<T>(r1, P, r1, P, P, K, nullptr, bc, s);
-        return fft_exec<T>(tab.fft_P, r1, r1 == vA ? vW : vA, bc, -1, s, res);
+        return fft(false, r1, r1 == vA ? vW : vA, -1, res);
     };
-    const bool fused = fft_hooks_supported<T>(tab.fft_P);
+    const bool fused = sizeof(T) == 4 && fft_hooks_supported<T>(tab.fft_P);
     // selection and placement as scattering stores of the FFT passes
     const bool scatter = fft_scatter_supported<T>(tab.fft_ns) && fft_scatter_supported<T>(tab.fft_P);
     // the IDFT's last pass, x K and the DFT's first pass in one kernel
@@ -571,7 +581,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
         c2<T>* X = nullptr;
         if (op == OP_INV5) {
             launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt5_ext, gA, bc, s);
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, -1, &r)) != NUFFT_OK) return st;
             X = (r == gA) ? gW : gA;
             NUFFT_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(c2<T>) * ns * bc, s));
             launch_select<T>(r, ns, X, ns, P, prm.K0s, fac1, bc, s);   // A_k, k < P (type-1, Eq. 25)
@@ -582,16 +592,16 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                                              cudaMemcpyDeviceToDevice, s));
         }
         c2<T>* Y = nullptr;
-        if ((st = fft_exec<T>(tab.fft_ns, X, X == gA ? gW : gA, bc, -1, s, &Y)) != NUFFT_OK) return st;
+        if ((st = fft(true, X, X == gA ? gW : gA, -1, &Y)) != NUFFT_OK) return st;
         launch_pointwise<T>(Y, ns, Y, ns, ns, (const c2<T>*)pl->FL, nullptr, bc, s);
         c2<T>* c = nullptr;
-        if ((st = fft_exec<T>(tab.fft_ns, Y, Y == gA ? gW : gA, bc, +1, s, &c)) != NUFFT_OK) return st;
+        if ((st = fft(true, Y, Y == gA ? gW : gA, +1, &c)) != NUFFT_OK) return st;
         if (op == OP_INV5) {
             launch_conv_fold<T>(c, ns, P, prm.rhoP, out, N, bc, s);
         } else {
             launch_conv_fold<T>(c, ns, P, prm.rhoP, vA, P, bc, s);
             launch_place<T>(vA, P, P, prm.K0s, fac1, gA, ns, bc, s);   // type-2 of S (Eq. 39)
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
             launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
         }
         NUFFT_CUDA_TRY(cudaGetLastError());
@@ -627,7 +637,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 // the loads of the inverse length-N FFT, Eq. 30 (x K) on its
                 // stores, and Eq. 31 (rho^-m / N) on the stores of the forward
                 // FFT, which writes the result
-                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+                if ((st = fft(true, gA, gW, -1, &r)) != NUFFT_OK) return st;
                 FFTHooks h1;
                 h1.lop = 1; h1.src = r; h1.src_bs = ns; h1.ns = ns; h1.K0 = prm.K0s; h1.fac_in = fac5;
                 h1.sop = 1; h1.mulc = K;
@@ -637,7 +647,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
                 break;
             }
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, -1, &r)) != NUFFT_OK) return st;
             launch_select<T>(r, ns, vA, P, P, prm.K0s, fac5, bc, s);
             if ((st = middle(&r)) != NUFFT_OK) return st;
             launch_pointwise<T>(r, P, out, N, P, nullptr, sneg, bc, s);
@@ -670,7 +680,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                     h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
                     if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
                 }
-                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+                if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
                 break;
             }
@@ -685,27 +695,27 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 FFTHooks h2;
                 if ((st = fft_exec_hooked<T>(tab.fft_P, vA, gW, vW, bc, -1, h2, s)) != NUFFT_OK) return st;
                 launch_place<T>(vW, P, P, prm.K0s, fac4, gA, ns, bc, s);
-                if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+                if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
                 break;
             }
             launch_pointwise<T>(in, N, vA, P, P, nullptr, rpos, bc, s);
             if ((st = middle(&r)) != NUFFT_OK) return st;
             launch_place<T>(r, P, P, prm.K0s, fac4, gA, ns, bc, s);
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
             launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
             break;
         }
         case OP_FWD1: {
             launch_spread<T>(pl->gs, prm.ks_solve, in, N, (const c2<T>*)pl->wt1_ext, gA, bc, s);
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, -1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, -1, &r)) != NUFFT_OK) return st;
             launch_select<T>(r, ns, out, N, P, prm.K0s, fac1, bc, s);
             break;
         }
         case OP_FWD2:
         case OP_FWD2D: {
             launch_place<T>(in, N, P, prm.K0s, fac1, gA, ns, bc, s, op == OP_FWD2D);
-            if ((st = fft_exec<T>(tab.fft_ns, gA, gW, bc, +1, s, &r)) != NUFFT_OK) return st;
+            if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
             launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt2_srt, out, N, bc, s);
             break;
         }
