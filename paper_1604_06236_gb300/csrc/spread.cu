@@ -391,6 +391,11 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
                                                 int64_t batch, const T* __restrict__ ktab) {
     pdl_wait();
     pdl_trigger();
+    __shared__ float2 s_exp[64];   // float64 data: double-float exponential table
+    if constexpr (sizeof(T) == 8) {
+        if (threadIdx.x < 64) s_exp[threadIdx.x] = c_exp2_64[threadIdx.x];
+        __syncthreads();
+    }
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t b0 = (int64_t)blockIdx.y * BC;
@@ -401,6 +406,15 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
     if (ktab) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? ktab[i * w + m] : (T)0;
+    } else if constexpr (sizeof(T) == 8) {
+        // kernel values in double-float on the float32 pipes (see k_spread_dd)
+        const dd fr = dd_from_double((double)f);
+        const dd beta_dd((double)beta);
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+            ker[m] = (m < w) ? (T)dd_to_double(es_kernel_dd(dd((float)(m + 1 - h), 0.f) - fr, 0.5f * (float)w,
+                                                            beta_dd, s_exp))
+                             : (T)0;
     } else {
 #pragma unroll
         for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<T>((T)(m + 1 - h) - f, two_over_w, beta) : (T)0;
