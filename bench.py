@@ -334,8 +334,10 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": d["bytes"] / d["launches"], "launches": d["launches"],
                 "avg_launch_us": d["ms"] / d["launches"] * 1e3,
                 "share_of_step": d["ms"] / traced_ms, "peak_source": peak_src + " (hbm_gbs, copy test)",
-                "timing": "CUDA events around every launch on its stream, in a second pass over the same %d "
-                          "steps (%.3f ms/step with the events)" % (args.steps, traced_ms / args.steps)}
+                "timing": "CUDA events on the launching stream, one pair around each FFT's back-to-back "
+                          "passes and one around every other launch, in a second pass over the same %d steps "
+                          "(%.3f ms/step with the events); per launch = the FFTs' event time / their passes"
+                          % (args.steps, traced_ms / args.steps)}
 
     result = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "mpoints_per_s": value * N / 1e6,

@@ -13,6 +13,7 @@
 #include "df.cuh"
 #include "fft_p2.cuh"
 #include "fft_p2t.cuh"
+#include "fft_ddq.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -905,6 +906,61 @@ nufft_status fft_wait_status(cudaStream_t s) {
     return fail(NUFFT_ERR_TIMEOUT, "%d FFT pass tile wait(s) expired", expired);
 }
 
+// passes of the few-vector double-float kernel: n = 2^L, L >= 11, split into
+// balanced radices 2^5 .. 2^10 (at least two passes, so that every pass has
+// n/R >= 2 columns)
+// batches up to this many points take the few-vector kernel; beyond it the
+// radix-64 streaming passes already fill the GPU with threads
+constexpr int64_t kDdqMaxElems = (int64_t)1 << 21;
+
+static void plan_ddq(int64_t n, std::vector<int>& rl) {
+    rl.clear();
+    int L = 0;
+    while (((int64_t)1 << L) < n) ++L;
+    if (L < 11 || ((int64_t)1 << L) != n) return;
+    const int k = (L + 9) / 10;
+    rl.assign(k, L / k);
+    for (int i = 0; i < L % k; ++i) rl[i] += 1;
+}
+
+static nufft_status exec_ddq(const FFTPlan& p, cdd* buf, cdd* work, int64_t batch, int dir, cudaStream_t s, cdd** result) {
+    int L = 0;
+    while (((int64_t)1 << L) < p.n) ++L;
+    const cdd* tw = static_cast<const cdd*>(p.tw_full);
+    cdd* src = buf;
+    cdd* dst = work;
+    int ns_log = 0;
+    const size_t k = p.q_rlog.size();
+    for (size_t i = 0; i < k; ++i) {
+        const int rl = p.q_rlog[i];
+        ddq::QArgs a;
+        a.n_log = L;
+        a.Ns_log = ns_log;
+        a.cvt_in = (i == 0) ? 1 : 0;
+        a.cvt_out = (i + 1 == k) ? 1 : 0;
+        const int64_t grid = (batch << (L - rl)) / ddq::kCols;
+        const unsigned th = (unsigned)(ddq::kCols * (1 << rl) / 4);
+        {
+            Launch Lk(s, K_FFT, 2.0 * (double)p.n * (double)batch * sizeof(cdd), true);
+            switch (rl) {
+                case 5: launch_k(ddq::k_fft_ddq<5>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                case 6: launch_k(ddq::k_fft_ddq<6>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                case 7: launch_k(ddq::k_fft_ddq<7>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                case 8: launch_k(ddq::k_fft_ddq<8>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                case 9: launch_k(ddq::k_fft_ddq<9>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                case 10: launch_k(ddq::k_fft_ddq<10>, (unsigned)grid, th, 0, s, src, dst, a, tw, dir); break;
+                default: return fail(NUFFT_ERR_ARG, "no few-vector pass for radix 2^%d", rl);
+            }
+        }
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        ns_log += rl;
+        src = dst;
+        dst = (dst == buf) ? work : buf;
+    }
+    *result = src;
+    return NUFFT_OK;
+}
+
 nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
     p.n = n;
     p.prec = prec;
@@ -976,7 +1032,9 @@ nufft_status fft_make(FFTPlan& p, int64_t n, int prec, cudaStream_t s) {
             prec == 3 ? (cdd*)p.tw_full : nullptr);
         NUFFT_CUDA_TRY(cudaGetLastError());
     }
-    return prec == 1 ? make_passes<float>(p) : prec == 2 ? make_passes<double>(p) : make_passes<dd>(p);
+    nufft_status st = prec == 1 ? make_passes<float>(p) : prec == 2 ? make_passes<double>(p) : make_passes<dd>(p);
+    if (st == NUFFT_OK && prec == 3 && p.tw_full) plan_ddq(n, p.q_rlog);
+    return st;
 }
 
 template <typename T>
@@ -1019,6 +1077,15 @@ template nufft_status fft_exec<dd>(const FFTPlan&, cdd*, cdd*, int64_t, int, cud
 // convert the result back in place
 nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
                          double2** result) {
+    if (batch > 0 && !p.q_rlog.empty() && batch * p.n <= kDdqMaxElems) {
+        // few vectors: the shared-memory radix-4 passes, converting on the
+        // first pass's loads and the last pass's stores
+        cdd* r = nullptr;
+        nufft_status st = exec_ddq(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r);
+        if (st != NUFFT_OK) return st;
+        *result = reinterpret_cast<double2*>(r);
+        return NUFFT_OK;
+    }
     if (batch > 0 && p2s_all<dd>(p)) {
         // the first pass converts on its loads, the last on its stores
         cdd* r = nullptr;

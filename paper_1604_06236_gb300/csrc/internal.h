@@ -52,6 +52,27 @@ class Launch {
     double bytes_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+// Traces the launches of one unit (the passes of one FFT) that run back to
+// back on a stream with one pair of events instead of one pair per launch, so
+// that tracing leaves their programmatic overlap intact.  Launches of the
+// group's kind on its stream, made on this thread while the group lives, join
+// it; a launch of another kind ends the current run of the group (a later
+// launch of its kind starts a new one).  Groups nest: an inner group joins the
+// outer one.
+class LaunchGroup {
+  public:
+    LaunchGroup(cudaStream_t s, int kind, bool f64 = false);
+    ~LaunchGroup();
+    bool join(cudaStream_t s, int kind, double bytes);   // called by Launch
+    void close();                                        // ends the current run
+  private:
+    cudaStream_t s_;
+    int kind_;
+    bool outer_ = false;
+    cudaEvent_t a_ = nullptr;
+    long long n_ = 0;
+    double bytes_ = 0;
+};
 
 // ---------------------------------------------------------------- FFT ------
 // One Stockham autosort pass of composite radix R: for every j < n/R the R
@@ -72,6 +93,7 @@ struct FFTPlan {
     int prec = 0;                       // 1 = float, 2 = double, 3 = double-float
     std::vector<FFTPass> passes;
     std::vector<int> p2_rlog;           // power-of-two plan: log2 radix of each pass
+    std::vector<int> q_rlog;            // double-float power-of-two plans: passes of the few-vector kernel
     // two-level table of W_n^e = e^{-j 2 pi e / n}: lo[e & (B-1)] * hi[e >> shift]
     int shift = 0;
     void* tw_lo = nullptr;

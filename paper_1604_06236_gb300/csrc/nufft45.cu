@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 
 namespace nufft45 {
 
@@ -260,6 +261,13 @@ static nufft_status get_tables(const Params& prm, cudaStream_t s, TablesPtr& out
 using namespace nufft45;
 
 // ------------------------------------------------------------------ plan ---
+// one FFT as one traced unit: its passes run back to back on the stream
+template <typename Fn, typename... A>
+nufft_status traced_fft(cudaStream_t s, bool f64, Fn&& fn, A&&... a) {
+    LaunchGroup g(s, K_FFT, f64);
+    return fn(std::forward<A>(a)...);
+}
+
 struct nufft_plan_s {
     Params prm;
     TablesPtr tab;
@@ -487,17 +495,17 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     launch_plan_strengths(pl->T, N, (uint64_t)P, eta, str, s);
     launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s, ktab);
     double2* B = nullptr;
-    if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
     launch_fold(B, prm.ns, prm.K0s, tab.fold, P, eta, vecP, s);
     double2* v = nullptr;
-    if ((st = fft_exec_dd(tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
     // K_q (Eq. 29)
     launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, s);
     if (!f32) NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->Ks, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
     // L_m (Eq. 43) and the coefficients (m+1) L_{m+1} of L' (Eq. 16)
     NUFFT_CUDA_TRY(cudaMemcpyAsync(vecP, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
     double2* F = nullptr;
-    if ((st = fft_exec_dd(tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
     double2* dco = (F == vecP) ? workP : vecP;
     launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
     if (prm.toeplitz) {
@@ -505,14 +513,14 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
         // the middle stage as a linear convolution
         launch_lagrange_pad(F, P, prm.rhoP, tab.sneg64, prm.ns, grid, s);
         double2* FLd = nullptr;
-        if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, 1, -1, s, &FLd)) != NUFFT_OK) { tmp.release(); return st; }
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, -1, s, &FLd)) != NUFFT_OK) { tmp.release(); return st; }
         if (f32) launch_to_solve<float>(FLd, prm.ns, 1.0 / (double)prm.ns, (float2*)pl->FL, s);
         else launch_to_solve<double>(FLd, prm.ns, 1.0 / (double)prm.ns, (double2*)pl->FL, s);
     }
     // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
     launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
     double2* gsp = nullptr;
-    if ((st = fft_exec_dd(tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
     launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s, ktab);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
     launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
@@ -554,6 +562,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
     // float64 data goes through the double-float transforms (float pairs on the
     // float32 pipes, ~2^-48): GB300 issues float64 at 1/64 of the float32 rate
     auto fft = [&](bool grid_size, c2<T>* buf, c2<T>* work, int dir, c2<T>** res) -> nufft_status {
+        LaunchGroup g(s, K_FFT, sizeof(T) == 8);
         if constexpr (sizeof(T) == 8) {
             return fft_exec_dd(grid_size ? tab.fft_ns64 : tab.fft_P64, reinterpret_cast<double2*>(buf),
                                reinterpret_cast<double2*>(work), bc, dir, s, reinterpret_cast<double2**>(res));
@@ -617,19 +626,19 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 // the forward one with Eq. 31's rho^-m / N, which writes the result
                 FFTHooks hs;
                 hs.sop = 3; hs.K0 = K0; hs.P = P; hs.out_bs = P; hs.fac_out = fac5;
-                if ((st = fft_exec_hooked<T>(tab.fft_ns, gA, gW, vA, bc, -1, hs, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_ns, gA, gW, vA, bc, -1, hs, s)) != NUFFT_OK) return st;
                 if (conv) {
                     FFTHooks hc;
                     hc.sop = 2; hc.fac_out = sneg;
-                    if ((st = fft_exec_conv<T>(tab.fft_P, vA, vW, vA, out, bc, +1, K, hc, s)) != NUFFT_OK) return st;
+                    if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_conv<T>, tab.fft_P, vA, vW, vA, out, bc, +1, K, hc, s)) != NUFFT_OK) return st;
                     break;
                 }
                 FFTHooks h1;
                 h1.sop = 1; h1.mulc = K;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
                 FFTHooks h2;
                 h2.sop = 2; h2.fac_out = sneg;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
                 break;
             }
             if (fused) {
@@ -641,10 +650,10 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 FFTHooks h1;
                 h1.lop = 1; h1.src = r; h1.src_bs = ns; h1.ns = ns; h1.K0 = prm.K0s; h1.fac_in = fac5;
                 h1.sop = 1; h1.mulc = K;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
                 FFTHooks h2;
                 h2.sop = 2; h2.fac_out = sneg;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, out, bc, -1, h2, s)) != NUFFT_OK) return st;
                 break;
             }
             if ((st = fft(true, gA, gW, -1, &r)) != NUFFT_OK) return st;
@@ -670,15 +679,15 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                     FFTHooks hc;
                     hc.lop = 2; hc.fac_in = rpos;
                     hc.sop = 4; hc.K0 = K0; hc.ns = ns; hc.out_bs = ns; hc.fac_out = fac4;
-                    if ((st = fft_exec_conv<T>(tab.fft_P, in, vW, vA, gA, bc, +1, K, hc, s)) != NUFFT_OK) return st;
+                    if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_conv<T>, tab.fft_P, in, vW, vA, gA, bc, +1, K, hc, s)) != NUFFT_OK) return st;
                 } else {
                     FFTHooks h1;
                     h1.lop = 2; h1.fac_in = rpos;
                     h1.sop = 1; h1.mulc = K;
-                    if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                    if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
                     FFTHooks h2;
                     h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
-                    if ((st = fft_exec_hooked<T>(tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
+                    if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
                 }
                 if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
@@ -691,9 +700,9 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 FFTHooks h1;
                 h1.lop = 2; h1.fac_in = rpos;
                 h1.sop = 1; h1.mulc = K;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, in, vW, vA, bc, +1, h1, s)) != NUFFT_OK) return st;
                 FFTHooks h2;
-                if ((st = fft_exec_hooked<T>(tab.fft_P, vA, gW, vW, bc, -1, h2, s)) != NUFFT_OK) return st;
+                if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, gW, vW, bc, -1, h2, s)) != NUFFT_OK) return st;
                 launch_place<T>(vW, P, P, prm.K0s, fac4, gA, ns, bc, s);
                 if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
@@ -760,11 +769,11 @@ nufft_status forward64(const nufft_plan_s* pl, bool type2, const double2* x, dou
     nufft_status st;
     if (type2) {
         launch_place<double>(x, N, N, prm.K0s, tab.plan_place, g, prm.ns, bc, s);
-        if ((st = fft_exec_dd(tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
         launch_interp<double>(pl->gs, prm.ks_plan, r, pl->modp64_srt, y, N, bc, s);
     } else {
         launch_spread<double>(pl->gs, prm.ks_plan, x, N, pl->modm64_ext, g, bc, s);
-        if ((st = fft_exec_dd(tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
         launch_select<double>(r, prm.ns, y, N, N, prm.K0s, tab.plan_place, bc, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());

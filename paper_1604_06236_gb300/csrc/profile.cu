@@ -1,6 +1,7 @@
 // Kernel-level tracing: every launch of the library is counted; when
 // enabled, each launch is bracketed by CUDA events on its own stream and
-// attributed to a kernel class with its algorithmic byte count.
+// attributed to a kernel class with its algorithmic byte count.  The passes of
+// one FFT, which run back to back, share one pair of events (LaunchGroup).
 #include "internal.h"
 
 #include <atomic>
@@ -11,12 +12,13 @@
 namespace nufft45 {
 
 namespace {
-struct Rec { int kind; cudaEvent_t a, b; double bytes; };
+struct Rec { int kind; cudaEvent_t a, b; double bytes; long long n; };
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
 std::atomic<long long> g_launches{0};
+thread_local LaunchGroup* t_group = nullptr;
 
 cudaEvent_t get_event() {
     if (!g_free.empty()) { cudaEvent_t e = g_free.back(); g_free.pop_back(); return e; }
@@ -38,6 +40,7 @@ const char* kind_name(int k) {
 Launch::Launch(cudaStream_t s, int kind, double bytes, bool f64) : s_(s), kind_(kind + (f64 ? K_COUNT : 0)), bytes_(bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_on) {
+        if (t_group && t_group->join(s_, kind_, bytes_)) return;
         std::lock_guard<std::mutex> lk(g_mu);
         a_ = get_event();
         b_ = get_event();
@@ -49,8 +52,45 @@ Launch::~Launch() {
     if (a_) {
         cudaEventRecord(b_, s_);
         std::lock_guard<std::mutex> lk(g_mu);
-        g_recs.push_back(Rec{kind_, a_, b_, bytes_});
+        g_recs.push_back(Rec{kind_, a_, b_, bytes_, 1});
     }
+}
+
+LaunchGroup::LaunchGroup(cudaStream_t s, int kind, bool f64) : s_(s), kind_(kind + (f64 ? K_COUNT : 0)) {
+    outer_ = (t_group == nullptr);
+    if (outer_) t_group = this;
+}
+
+LaunchGroup::~LaunchGroup() {
+    if (!outer_) return;
+    close();
+    t_group = nullptr;
+}
+
+bool LaunchGroup::join(cudaStream_t s, int kind, double bytes) {
+    if (s != s_ || kind != kind_) {
+        close();   // the run ends before a launch of another kind
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!a_) {
+        a_ = get_event();
+        cudaEventRecord(a_, s_);
+        n_ = 0;
+        bytes_ = 0;
+    }
+    n_ += 1;
+    bytes_ += bytes;
+    return true;
+}
+
+void LaunchGroup::close() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaEvent_t b = get_event();
+    cudaEventRecord(b, s_);
+    g_recs.push_back(Rec{kind_, a_, b, bytes_, n_});
+    a_ = nullptr;
 }
 
 }  // namespace nufft45
@@ -83,7 +123,7 @@ nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count)
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, r.a, r.b);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime", __FILE__, __LINE__);
-        acc[r.kind].launches += 1;
+        acc[r.kind].launches += r.n;
         acc[r.kind].ms += ms;
         acc[r.kind].bytes += r.bytes;
     }

@@ -40,12 +40,15 @@ def test_fft_matches_numpy(n, prec):
         assert err < tol * max(1.0, np.log2(max(n, 2)) / 10), (n, prec, dir_, err)
 
 
-@pytest.mark.parametrize("n", [8, 256, 4096, 65536, 131072, 1 << 20, 1000, 1009, 40960])
-def test_double_float_fft_matches_numpy(n):
+@pytest.mark.parametrize("n,batch", [(8, 2), (256, 2), (2048, 1), (4096, 2), (65536, 1), (65536, 3), (131072, 3),
+                                     (1 << 20, 1), (1 << 21, 1), (65536, 40), (1000, 2), (1009, 2), (40960, 2)])
+def test_double_float_fft_matches_numpy(n, batch):
     """The double-float FFT (prec 3: pairs of float32) on float64 data reaches
-    float64-class accuracy."""
-    batch = 2 if n <= (1 << 17) else 1
-    x = synth.cn01((batch, n), seed=n + 1)
+    float64-class accuracy: power-of-two lengths from 2^11 on few vectors run
+    the shared-memory radix-4 passes (two or three passes of radix 2^5..2^10),
+    larger batches the radix-64 streaming passes, other lengths the general
+    passes or Bluestein."""
+    x = synth.cn01((batch, n), seed=n + batch)
     for dir_ in (-1, 1):
         ref = np.fft.fft(x, axis=1) if dir_ < 0 else np.fft.ifft(x, axis=1) * n
         got = _run(n, 3, dir_, x)
