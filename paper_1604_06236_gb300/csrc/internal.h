@@ -189,11 +189,12 @@ struct KernelShape { int w; double beta; };
 // per-device tables the plan kernels read (call before the first plan on a device)
 nufft_status plan_kernels_init();
 
-void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s);
-nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n, int w,
-                            bool want_float, int* scratch_int, cudaStream_t s);
+// From the nodes x (radians): the exact turns T, the cell-sorted and extended
+// node lists, the duplicate-node flag (cleared, then set when two nodes
+// coincide) and sumT = sum of T mod 2^64 (the constant phase of Eq. 29)
+nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N, int64_t n, int w,
+                            bool want_float, int* scratch_int, unsigned long long* sumT, cudaStream_t s);
 int64_t geometry_scratch_ints(int64_t N, int64_t n);
-void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s);
 
 // ktab (optional, N * ks.w values): the spread also stores every kernel value
 // it evaluates, by sorted slot and tap, and an interpolation on the same
@@ -237,17 +238,21 @@ void gauss_legendre_half(int nq, GLRule& r);   // nodes in (0,1), weights for in
 // 6: Lambda_k/phihat((k mod P) - K0)
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s);
-// out[i] = e^{sign j 2 pi K0 t_{perm[i]}}, i < (count_dev ? *count_dev : cap)
-void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
-                double2* out, cudaStream_t s);
+// modm_ext[i] = e^{-j 2 pi K0 t_{eperm[i]}}, i < *ext_count; modp_srt[i] =
+// e^{+j 2 pi K0 t_{sperm[i]}}, i < N; str[r][p] = e^{-j 2 pi P r t_p}, r < eta
+void launch_node_phases(const uint64_t* T, const int* eperm, const int* ext_count, const int* sperm, int64_t N,
+                        uint64_t K0, uint64_t P, int eta, double2* modm_ext, double2* modp_srt, double2* str,
+                        cudaStream_t s);
 // Y_m = sum_{r<eta} fac[P r + m] B[r n + (m - K0) mod n]
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s);
-// out[r][p] = e^{-j 2 pi P r t_p}, r < eta
-void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, double2* out, cudaStream_t s);
+// K_q (Eq. 29) into K, and copies into Kf (float32), Kd and Kv where not null
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
-                           cudaStream_t s);
-void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s);
+                           double2* Kd, double2* Kv, cudaStream_t s);
+// d_m = (m + 1) L_{m+1} (Eqs. 43, 16) times fac[m], placed on the grid of size n
+// at the centred index m - K0 (0 elsewhere)
+void launch_lcoef_place(const double2* F, int64_t P, const double* rho_neg, int64_t K0, const double* fac, int64_t n,
+                        double2* grid, cudaStream_t s);
 // L_0 .. L_P (Eq. 43) from F = DFT(K), zero-padded to n
 void launch_lagrange_pad(const double2* F, int64_t P, double rhoP, const double* rho_neg, int64_t n, double2* out,
                          cudaStream_t s);
@@ -257,9 +262,12 @@ void launch_to_solve(const double2* in, int64_t n, double scale, c2<TS>* out, cu
 template <typename T>
 void launch_conv_fold(const c2<T>* c, int64_t n, int64_t P, double rhoP, c2<T>* out, int64_t out_bs, int64_t batch,
                       cudaStream_t s);
-void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s);
+// w_p (Eqs. 27, 40) into w64 (node order) and the solve-precision slot arrays:
+// sorted slots wt2 = e^{+j 2 pi K0 t}, wt4 = w wt2; extended slots
+// wt1 = e^{-j 2 pi K0 t}, wt5 = w wt1
 template <typename TS>
-void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
-                         const double2* w_user, c2<TS>* mod_out, c2<TS>* wmod_out, cudaStream_t s);
+void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
+                    const double2* modp_srt, const double2* modm_ext, double rhoP, double2* w64, c2<TS>* wt2_srt,
+                    c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s);
 
 }  // namespace nufft45

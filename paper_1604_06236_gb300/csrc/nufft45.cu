@@ -479,20 +479,20 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     unsigned long long* sumT = tmp.take<unsigned long long>(1);
     double* ktab = tmp.take<double>((size_t)N * prm.ks_plan.w);
 
-    // nodes: exact turns; sum t_p mod 1 for the constant phase of Eq. 29
-    launch_canon(x_dev, N, pl->T, s);
-    launch_sum_turns(pl->T, N, sumT, s);
-    // cell-sorted geometry on the transforms' grid (halo for the wider width)
-    if ((st = build_geometry(gs, pl->T, N, prm.ns, prm.halo, f32, geo, s)) != NUFFT_OK) { tmp.release(); return st; }
+    // nodes: exact turns, sum t_p mod 1 for the constant phase of Eq. 29, and
+    // the cell-sorted geometry on the transforms' grid (halo for the wider width)
+    if ((st = build_geometry(gs, x_dev, pl->T, N, prm.ns, prm.halo, f32, geo, sumT, s)) != NUFFT_OK) {
+        tmp.release();
+        return st;
+    }
     const int* ext_count = gs.cstart + (prm.ns + prm.halo);
-    launch_mod(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->modm64_ext, s);
-    launch_mod(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->modp64_srt, s);
     // v(q/P) (Eqs. 13, 19, 28): the type-1 of unit strengths at k = P r + m,
     // k < R = eta P, is the type-1 at m < P of the strengths
     // e^{-j 2 pi P r t_p}, r < eta (one spread of eta right-hand sides and a
     // batched FFT on the transforms' grid), folded by Eq. 7 with Eq. 41's
     // coefficients and the deconvolution
-    launch_plan_strengths(pl->T, N, (uint64_t)P, eta, str, s);
+    launch_node_phases(pl->T, gs.ext_perm, ext_count, gs.srt_perm, N, (uint64_t)prm.K0s, (uint64_t)P, eta,
+                       pl->modm64_ext, pl->modp64_srt, str, s);
     launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s, ktab);
     double2* B = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
@@ -500,14 +500,11 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     double2* v = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
     // K_q (Eq. 29)
-    launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, s);
-    if (!f32) NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->Ks, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
-    // L_m (Eq. 43) and the coefficients (m+1) L_{m+1} of L' (Eq. 16)
-    NUFFT_CUDA_TRY(cudaMemcpyAsync(vecP, pl->K64, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
+    // K_q (Eq. 29), with the copy that the DFT of Eq. 43 transforms in place
+    launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, f32 ? nullptr : (double2*)pl->Ks,
+                          vecP, s);
     double2* F = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
-    double2* dco = (F == vecP) ? workP : vecP;
-    launch_lcoef(F, P, prm.rhoP, tab.sneg64, dco, s);
     if (prm.toeplitz) {
         // DFT of L_0..L_P zero-padded to the grid size (ns >= 2P), / ns, for
         // the middle stage as a linear convolution
@@ -517,23 +514,22 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
         if (f32) launch_to_solve<float>(FLd, prm.ns, 1.0 / (double)prm.ns, (float2*)pl->FL, s);
         else launch_to_solve<double>(FLd, prm.ns, 1.0 / (double)prm.ns, (double2*)pl->FL, s);
     }
-    // L'(z_p) by a type-2 NUFFT on the transforms' grid (float64, plan width)
-    launch_place<double>(dco, P, P, prm.K0s, tab.plan_place, grid, prm.ns, 1, s);
+    // L_m (Eq. 43) and the coefficients (m+1) L_{m+1} of L' (Eq. 16) on the
+    // grid, then L'(z_p) by a type-2 NUFFT on the transforms' grid (float64,
+    // plan width)
+    launch_lcoef_place(F, P, tab.sneg64, prm.K0s, tab.plan_place, prm.ns, grid, s);
     double2* gsp = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
     launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s, ktab);
     // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
-    launch_weights(pl->T, pl->D64, N, prm.rhoP, pl->w64, s);
     if (f32) {
-        launch_slot_weights<float>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
-                                   (float2*)pl->wt1_ext, (float2*)pl->wt5_ext, s);
-        launch_slot_weights<float>(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->w64,
-                                   (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, s);
+        launch_weights<float>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, prm.rhoP, pl->w64,
+                              (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext, (float2*)pl->wt5_ext,
+                              s);
     } else {
-        launch_slot_weights<double>(pl->T, gs.ext_perm, 2 * N, ext_count, (uint64_t)prm.K0s, -1, pl->w64,
-                                    (double2*)pl->wt1_ext, (double2*)pl->wt5_ext, s);
-        launch_slot_weights<double>(pl->T, gs.srt_perm, N, nullptr, (uint64_t)prm.K0s, +1, pl->w64,
-                                    (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, s);
+        launch_weights<double>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, prm.rhoP, pl->w64,
+                               (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
+                               (double2*)pl->wt5_ext, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());
     tmp.release();

@@ -52,15 +52,28 @@ __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, in
     if (out_f) out_f[k] = (float)v;
 }
 
-// e^{sign j 2 pi K0 t_p} for p = perm[i], i < count (count read from device when given)
-__global__ void k_mod(const uint64_t* __restrict__ T, const int* __restrict__ perm, int64_t cap,
-                      const int* __restrict__ count_dev, uint64_t K0, int sign, double2* __restrict__ out) {
+// The node-dependent phases of the plan in one launch over three ranges:
+// [0, 2N) e^{-j 2 pi K0 t_p} on the extended slots (p = eperm[i], i below the
+// device-held extended count); [2N, 3N) e^{+j 2 pi K0 t_p} on the sorted slots;
+// [3N, 4N) the strengths of the log-kernel type-1, str[r][p] =
+// e^{-j 2 pi P r t_p}, r < eta (Eqs. 13, 19, 28)
+__global__ void k_node_phases(const uint64_t* __restrict__ T, const int* __restrict__ eperm,
+                              const int* __restrict__ ext_count, const int* __restrict__ sperm, int64_t N, uint64_t K0,
+                              uint64_t P, int eta, double2* __restrict__ modm_ext, double2* __restrict__ modp_srt,
+                              double2* __restrict__ str) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
-    if (i >= cnt) return;
-    out[i] = cis_turns_t(K0 * T[perm[i]], sign);
+    if (i < 2 * N) {
+        if (i < (int64_t)*ext_count) modm_ext[i] = cis_turns_t(K0 * T[eperm[i]], -1);
+    } else if (i < 3 * N) {
+        const int64_t k = i - 2 * N;
+        modp_srt[k] = cis_turns_t(K0 * T[sperm[k]], +1);
+    } else if (i < 4 * N) {
+        const int64_t p = i - 3 * N;
+        const uint64_t t = T[p];
+        for (int r = 0; r < eta; ++r) str[(int64_t)r * N + p] = cis_turns_t(P * (uint64_t)r * t, -1);
+    }
 }
 
 // Eq. 7 with Lambda = g's coefficients (Eq. 41), the deconvolution folded in:
@@ -84,21 +97,13 @@ __global__ void k_fold(const double2* __restrict__ B, int64_t n, int64_t K0, con
     Y[m] = acc;
 }
 
-// strengths of the log-kernel type-1: out[r][p] = e^{-j 2 pi P r t_p}, r < eta
-__global__ void k_plan_strengths(const uint64_t* __restrict__ T, int64_t N, uint64_t P, int eta,
-                                 double2* __restrict__ out) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
-    const uint64_t t = T[p];
-    for (int r = 0; r < eta; ++r) out[(int64_t)r * N + p] = cis_turns_t(P * (uint64_t)r * t, -1);
-}
-
 // Eq. 29: K_q = exp(j P pi + j 2 pi sum_p t_p + v_q).  The constant phase is the
 // exact turn count P 2^63 + sum T_p mod 2^64.
+// K is written in float64 and copied where given: Kf (float32 solves), Kd and
+// Kv (the solve's float64 copy, the input of the DFT of Eq. 43)
 __global__ void k_kernel_samples(const double2* __restrict__ v, int64_t P, const unsigned long long* __restrict__ sumT,
-                                 double2* __restrict__ K, float2* __restrict__ Kf) {
+                                 double2* __restrict__ K, float2* __restrict__ Kf, double2* __restrict__ Kd,
+                                 double2* __restrict__ Kv) {
     pdl_wait();
     pdl_trigger();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -111,24 +116,35 @@ __global__ void k_kernel_samples(const double2* __restrict__ v, int64_t P, const
     const double2 k = make_double2(mag * c, mag * s);
     K[q] = k;
     if (Kf) Kf[q] = make_float2((float)k.x, (float)k.y);
+    if (Kd) Kd[q] = k;
+    if (Kv) Kv[q] = k;
 }
 
-// Eq. 43 and Eq. 16: L_m = (F_m - P rho^P delta_m) rho^{-m} / P, L_P = 1,
-// d_m = (m + 1) L_{m+1}; rho_neg[m] = rho^{-m}/P.
-__global__ void k_lcoef(const double2* __restrict__ F, int64_t P, double rhoP, const double* __restrict__ rho_neg,
-                        double2* __restrict__ d) {
+// Eq. 43 and Eq. 16: L_m = (F_m - P rho^P delta_m) rho^{-m} / P, L_P = 1, and
+// the coefficients d_m = (m + 1) L_{m+1} of L', placed on the grid of size n
+// for the type-2 that evaluates L'(z_p): grid slot g holds the centred index
+// k' = g (g < n - K0) or g - n, m = k' + K0, d_m fac[m] for 0 <= m < P and 0
+// elsewhere; rho_neg[m] = rho^{-m}/P (k = m + 1 >= 1: no delta term)
+__global__ void k_lcoef_place(const double2* __restrict__ F, int64_t P, const double* __restrict__ rho_neg,
+                              int64_t K0, const double* __restrict__ fac, int64_t n, double2* __restrict__ grid) {
     pdl_wait();
     pdl_trigger();
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= P) return;
-    double2 L;
-    const int64_t k = m + 1;
-    if (k == P) L = make_double2(1.0, 0.0);
-    else {
-        const double2 f = F[k];
-        L = make_double2(f.x * rho_neg[k], f.y * rho_neg[k]);   // k >= 1: no delta term
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int64_t kc = g < n - K0 ? g : g - n;
+    const int64_t m = kc + K0;
+    double2 v = make_double2(0.0, 0.0);
+    if (m >= 0 && m < P) {
+        const int64_t k = m + 1;
+        double2 L = make_double2(1.0, 0.0);
+        if (k < P) {
+            const double2 f = F[k];
+            L = make_double2(f.x * rho_neg[k], f.y * rho_neg[k]);
+        }
+        const double sc = (double)k * fac[m];
+        v = make_double2(sc * L.x, sc * L.y);
     }
-    d[m] = make_double2((double)k * L.x, (double)k * L.y);
+    grid[g] = v;
 }
 
 // The coefficients L_0 .. L_P of Eq. 43 (L_P = 1) zero-padded to n >= 2P, for
@@ -159,38 +175,47 @@ __global__ void k_to_solve(const double2* __restrict__ in, int64_t n, double sca
 }
 
 // Eqs. 27 / 40: w_p = h(-P t_p + j P a) / (L'(z_p) z_p) with
-// h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1).
-__global__ void k_weights(const uint64_t* __restrict__ T, const double2* __restrict__ D, int64_t N, double rhoP,
-                          double2* __restrict__ w) {
+// h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1), over the sorted slots
+// (p = sperm[i] visits every node once): w64[p], and the solve-precision
+// slot arrays mod_out[i] = e^{+j 2 pi K0 t_p} (modp_srt) and wmod_out[i] = w_p
+// times it
+template <typename TS>
+__global__ void k_weights_srt(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
+                              const double2* __restrict__ D, const double2* __restrict__ modp_srt, int64_t N,
+                              double rhoP, double2* __restrict__ w64, c2<TS>* __restrict__ mod_out,
+                              c2<TS>* __restrict__ wmod_out) {
     pdl_wait();
     pdl_trigger();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = sperm[i];
     const uint64_t t = T[p];
     const double2 e = cis_turns_t((uint64_t)N * t, -1);
     const double2 z = cis_turns_t(t, +1);
     const double2 h = make_double2(rhoP * e.x - 1.0, rhoP * e.y);
     const double2 den = cmul(h, cmul(D[p], z));
     const double nn = den.x * den.x + den.y * den.y;
-    w[p] = make_double2(den.x / nn, -den.y / nn);
+    const double2 w = make_double2(den.x / nn, -den.y / nn);
+    w64[p] = w;
+    const double2 m = modp_srt[i];
+    mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
+    const double2 wm = cmul(w, m);
+    wmod_out[i] = mk<TS>((TS)wm.x, (TS)wm.y);
 }
 
-// per-slot solve weights: plain modulation e^{sign j 2 pi K0 t} and the node
-// weight times it, in the solve precision
+// the same on the extended slots (below the device-held count), from w64 and
+// the slots' e^{-j 2 pi K0 t_p} (modm_ext)
 template <typename TS>
-__global__ void k_slot_weights(const uint64_t* __restrict__ T, const int* __restrict__ perm, int64_t cap,
-                               const int* __restrict__ count_dev, uint64_t K0, int sign,
-                               const double2* __restrict__ w_user, c2<TS>* __restrict__ mod_out,
-                               c2<TS>* __restrict__ wmod_out) {
+__global__ void k_weights_ext(const int* __restrict__ eperm, int64_t cap, const int* __restrict__ ext_count,
+                              const double2* __restrict__ w64, const double2* __restrict__ modm_ext,
+                              c2<TS>* __restrict__ mod_out, c2<TS>* __restrict__ wmod_out) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t cnt = count_dev ? (int64_t)*count_dev : cap;
-    if (i >= cnt) return;
-    const int p = perm[i];
-    const double2 m = cis_turns_t(K0 * T[p], sign);
+    if (i >= cap || i >= (int64_t)*ext_count) return;
+    const double2 m = modm_ext[i];
     mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
-    const double2 wm = cmul(w_user[p], m);
+    const double2 wm = cmul(w64[eperm[i]], m);
     wmod_out[i] = mk<TS>((TS)wm.x, (TS)wm.y);
 }
 
@@ -236,10 +261,12 @@ void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64
     launch_k(k_table, nblk(M), kTB, 0, s, ks.w, ks.beta, gl, n, K0, M, log_rho, mode, P, out_d, out_f);
 }
 
-void launch_mod(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
-                double2* out, cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, cap * 28.0);
-    launch_k(k_mod, nblk(cap), kTB, 0, s, T, perm, cap, count_dev, K0, sign, out);
+void launch_node_phases(const uint64_t* T, const int* eperm, const int* ext_count, const int* sperm, int64_t N,
+                        uint64_t K0, uint64_t P, int eta, double2* modm_ext, double2* modp_srt, double2* str,
+                        cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, 3.0 * N * 28.0 + N * (8.0 + 16.0 * eta));
+    launch_k(k_node_phases, nblk(4 * N), kTB, 0, s, T, eperm, ext_count, sperm, N, K0, P, eta, modm_ext, modp_srt,
+             str);
 }
 
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
@@ -248,20 +275,16 @@ void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int
     launch_k(k_fold, nblk(P), kTB, 0, s, B, n, K0, fac, P, eta, Y);
 }
 
-void launch_plan_strengths(const uint64_t* T, int64_t N, uint64_t P, int eta, double2* out, cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, N * (8.0 + 16.0 * eta));
-    launch_k(k_plan_strengths, nblk(N), kTB, 0, s, T, N, P, eta, out);
-}
-
 void launch_kernel_samples(const double2* v, int64_t P, const unsigned long long* sumT, double2* K, float2* Kf,
-                           cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, P * (Kf ? 40.0 : 32.0));
-    launch_k(k_kernel_samples, nblk(P), kTB, 0, s, v, P, sumT, K, Kf);
+                           double2* Kd, double2* Kv, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, P * (32.0 + (Kf ? 8.0 : 0.0) + (Kd ? 16.0 : 0.0) + (Kv ? 16.0 : 0.0)));
+    launch_k(k_kernel_samples, nblk(P), kTB, 0, s, v, P, sumT, K, Kf, Kd, Kv);
 }
 
-void launch_lcoef(const double2* F, int64_t P, double rhoP, const double* rho_neg, double2* d, cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, P * 40.0);
-    launch_k(k_lcoef, nblk(P), kTB, 0, s, F, P, rhoP, rho_neg, d);
+void launch_lcoef_place(const double2* F, int64_t P, const double* rho_neg, int64_t K0, const double* fac, int64_t n,
+                        double2* grid, cudaStream_t s) {
+    Launch L(s, K_PLAN_STAGE, P * 32.0 + n * 16.0);
+    launch_k(k_lcoef_place, nblk(n), kTB, 0, s, F, P, rho_neg, K0, fac, n, grid);
 }
 
 void launch_lagrange_pad(const double2* F, int64_t P, double rhoP, const double* rho_neg, int64_t n, double2* out,
@@ -278,21 +301,27 @@ void launch_to_solve(const double2* in, int64_t n, double scale, c2<TS>* out, cu
 template void launch_to_solve<float>(const double2*, int64_t, double, float2*, cudaStream_t);
 template void launch_to_solve<double>(const double2*, int64_t, double, double2*, cudaStream_t);
 
-void launch_weights(const uint64_t* T, const double2* D, int64_t N, double rhoP, double2* w, cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, N * 40.0);
-    launch_k(k_weights, nblk(N), kTB, 0, s, T, D, N, rhoP, w);
-}
-
 template <typename TS>
-void launch_slot_weights(const uint64_t* T, const int* perm, int64_t cap, const int* count_dev, uint64_t K0, int sign,
-                         const double2* w_user, c2<TS>* mod_out, c2<TS>* wmod_out, cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, cap * (28.0 + 4.0 * sizeof(TS)));
-    launch_k(k_slot_weights<TS>, nblk(cap), kTB, 0, s, T, perm, cap, count_dev, K0, sign, w_user, mod_out, wmod_out);
+void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
+                    const double2* modp_srt, const double2* modm_ext, double rhoP, double2* w64, c2<TS>* wt2_srt,
+                    c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s) {
+    const int64_t N = g.N;
+    {
+        Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0 + 16.0 + 4.0 * sizeof(TS)));
+        launch_k(k_weights_srt<TS>, nblk(N), kTB, 0, s, T, g.srt_perm, D, modp_srt, N, rhoP, w64, wt2_srt, wt4_srt);
+    }
+    {
+        Launch L(s, K_PLAN_STAGE, 2.0 * N * (4.0 + 16.0 + 16.0 + 4.0 * sizeof(TS)));
+        launch_k(k_weights_ext<TS>, nblk(2 * N), kTB, 0, s, g.ext_perm, 2 * N, ext_count, (const double2*)w64,
+                 modm_ext, wt1_ext, wt5_ext);
+    }
 }
-template void launch_slot_weights<float>(const uint64_t*, const int*, int64_t, const int*, uint64_t, int,
-                                         const double2*, float2*, float2*, cudaStream_t);
-template void launch_slot_weights<double>(const uint64_t*, const int*, int64_t, const int*, uint64_t, int,
-                                          const double2*, double2*, double2*, cudaStream_t);
+template void launch_weights<float>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
+                                    const double2*, double, double2*, float2*, float2*, float2*, float2*,
+                                    cudaStream_t);
+template void launch_weights<double>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
+                                     const double2*, double, double2*, double2*, double2*, double2*, double2*,
+                                     cudaStream_t);
 
 nufft_status plan_kernels_init() { return cis_table_ensure(); }
 

@@ -22,30 +22,40 @@ constexpr int kTB = 256;
 
 inline unsigned nblk(int64_t n, int tb = kTB) { return (unsigned)((n + tb - 1) / tb); }
 
-__global__ void k_canon(const double* __restrict__ x, int64_t N, uint64_t* __restrict__ T) {
+// t = x / (2 pi) mod 1 (IEEE division and floor) as exact turns T =
+// trunc(t 2^64); cell = floor(n t) = high word of T n and its fraction = low
+// word / 2^64, exactly; per-cell counts; per-block sums of T mod 2^64 (unsigned
+// wrap-around is exact arithmetic mod 1 in turns); block 0 clears the
+// duplicate flag
+__global__ void k_node_prep(const double* __restrict__ x, int64_t N, uint64_t n, uint64_t* __restrict__ T,
+                            int* __restrict__ cell, double* __restrict__ frac, int* __restrict__ count,
+                            unsigned long long* __restrict__ partial, int* __restrict__ dup) {
     pdl_wait();
     pdl_trigger();
+    __shared__ unsigned long long s[kTB];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    // t = x / (2 pi) mod 1 (IEEE division and floor), T = trunc(t 2^64)
-    double u = x[i] / 6.283185307179586476925286766559;
-    u -= floor(u);
-    if (u >= 1.0) u = 0.0;
-    T[i] = __double2ull_rz(u * 18446744073709551616.0);
-}
-
-// cell = floor(n t) = high word of T*n, fraction = low word / 2^64, exactly
-__global__ void k_cells(const uint64_t* __restrict__ T, int64_t N, uint64_t n, int* __restrict__ cell,
-                        double* __restrict__ frac, int* __restrict__ count) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const uint64_t t = T[i];
-    const int c = (int)__umul64hi(t, n);
-    cell[i] = c;
-    frac[i] = (double)(t * n) * 5.42101086242752217003726400434970855712890625e-20;
-    atomicAdd(&count[c], 1);
+    unsigned long long t = 0;
+    if (i < N) {
+        double u = x[i] / 6.283185307179586476925286766559;
+        u -= floor(u);
+        if (u >= 1.0) u = 0.0;
+        t = __double2ull_rz(u * 18446744073709551616.0);
+        T[i] = t;
+        const int c = (int)__umul64hi(t, n);
+        cell[i] = c;
+        frac[i] = (double)(t * n) * 5.42101086242752217003726400434970855712890625e-20;
+        atomicAdd(&count[c], 1);
+    }
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) s[threadIdx.x] += s[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s[0];
+        if (blockIdx.x == 0) *dup = 0;
+    }
 }
 
 // exclusive scan of int counts, three phases (block scan, scan of block sums,
@@ -53,12 +63,20 @@ __global__ void k_cells(const uint64_t* __restrict__ T, int64_t N, uint64_t n, i
 constexpr int kScanTB = 1024;
 constexpr int kScanPer = 2 * kScanTB;
 
-__global__ void k_scan_blocks(const int* __restrict__ in, int64_t L, int* __restrict__ out, int* __restrict__ sums) {
+// (the counts are cleared as they are read: they serve again as fill counters)
+__global__ void k_scan_blocks(int* __restrict__ in, int64_t L, int* __restrict__ out, int* __restrict__ sums) {
     pdl_wait();
     pdl_trigger();
     __shared__ int s[kScanPer];
     const int64_t base = (int64_t)blockIdx.x * kScanPer;
-    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x) s[e] = (base + e < L) ? in[base + e] : 0;
+    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x) {
+        int v = 0;
+        if (base + e < L) {
+            v = in[base + e];
+            in[base + e] = 0;
+        }
+        s[e] = v;
+    }
     __syncthreads();
     // Blelloch up-sweep / down-sweep
     int off = 1;
@@ -85,14 +103,26 @@ __global__ void k_scan_blocks(const int* __restrict__ in, int64_t L, int* __rest
         if (base + e < L) out[base + e] = s[e];
 }
 
-__global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict__ total) {
+// (the same block also adds up the per-block turn sums of k_node_prep)
+__global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict__ total,
+                            const unsigned long long* __restrict__ partial, int64_t np,
+                            unsigned long long* __restrict__ sumT) {
     pdl_wait();
     pdl_trigger();
     // one block, sequential over chunks of blockDim with a carry
     __shared__ int s[kScanTB];
     __shared__ int carry;
+    __shared__ unsigned long long r[kScanTB];
+    unsigned long long acc = 0;
+    for (int64_t i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+    r[threadIdx.x] = acc;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
+    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+        if (threadIdx.x < d) r[threadIdx.x] += r[threadIdx.x + d];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *sumT = r[0];
     for (int64_t base = 0; base < nb; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const int v = i < nb ? sums[i] : 0;
@@ -153,79 +183,58 @@ __global__ void k_order_cells(const int* __restrict__ start, int64_t n, const ui
     }
 }
 
-__global__ void k_sorted_fill(const int* __restrict__ perm, const int* __restrict__ cell, const double* __restrict__ frac,
-                              const uint64_t* __restrict__ T, int64_t N, int* __restrict__ scell,
-                              double* __restrict__ sfrac, float* __restrict__ sfracf, int* __restrict__ dup) {
+// One launch over three ranges: [0, N) the sorted slots (cell, fraction and
+// the coincident-node check: neighbours in sorted, i.e. cyclic turn, order
+// closer than 2^-44 turns, including the pair that wraps from the last to the
+// first); [N, 3N) the extended list [nodes of cells n-h..n-1, shifted by -n]
+// [all nodes] [nodes of cells 0..h-1, shifted by +n], h = w/2; [3N, 3N+n+w+1)
+// the extended list's cell starts cstart[e], e = cell + h in [0, n + w]
+__global__ void k_fill(const int* __restrict__ start, int64_t n, int w, int64_t N, const int* __restrict__ perm,
+                       const int* __restrict__ cell, const double* __restrict__ frac, const uint64_t* __restrict__ T,
+                       int* __restrict__ scell, double* __restrict__ sfrac, float* __restrict__ sfracf,
+                       int* __restrict__ dup, int* __restrict__ eperm, int* __restrict__ ecell,
+                       double* __restrict__ efrac, float* __restrict__ efracf, int* __restrict__ cstart) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int p = perm[i];
-    scell[i] = cell[p];
-    const double f = frac[p];
-    sfrac[i] = f;
-    if (sfracf) sfracf[i] = (float)f;
-    // coincident nodes: neighbours in sorted (= cyclic turn) order closer than
-    // 2^-44 turns, including the pair that wraps from the last to the first
-    if (N > 1) {
-        const uint64_t d = T[perm[i + 1 < N ? i + 1 : 0]] - T[p];
-        if (d < (1ull << 20)) *dup = 1;
-    }
-}
-
-// extended list: [nodes of cells n-h..n-1, shifted by -n] [all nodes] [nodes of cells 0..h-1, shifted by +n]
-__global__ void k_ext_fill(const int* __restrict__ start, int64_t n, int h, int64_t N, const int* __restrict__ sperm,
-                           const int* __restrict__ scell, const double* __restrict__ sfrac,
-                           int* __restrict__ eperm, int* __restrict__ ecell, double* __restrict__ efrac,
-                           float* __restrict__ efracf) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int pre = start[n] - start[n - h];
-    const int post = start[h];
-    if (i >= pre + N + post) return;
-    int64_t slot;
-    int shift;
-    if (i < pre) { slot = start[n - h] + i; shift = -(int)n; }
-    else if (i < pre + N) { slot = i - pre; shift = 0; }
-    else { slot = i - pre - N; shift = (int)n; }
-    eperm[i] = sperm[slot];
-    ecell[i] = scell[slot] + shift;
-    const double f = sfrac[slot];
-    efrac[i] = f;
-    if (efracf) efracf[i] = (float)f;
-}
-
-// cstart[e], e = cell + w/2 in [0, n + w]
-__global__ void k_cstart(const int* __restrict__ start, int64_t n, int w, int64_t N, int* __restrict__ cstart) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int h = w / 2;
-    if (e > n + w) return;
+    if (i < N) {
+        const int p = perm[i];
+        scell[i] = cell[p];
+        const double f = frac[p];
+        sfrac[i] = f;
+        if (sfracf) sfracf[i] = (float)f;
+        if (N > 1) {
+            const uint64_t d = T[perm[i + 1 < N ? i + 1 : 0]] - T[p];
+            if (d < (1ull << 20)) *dup = 1;
+        }
+        return;
+    }
     const int pre = start[n] - start[n - h];
+    if (i < 3 * N) {
+        const int64_t e = i - N;
+        const int post = start[h];
+        if (e >= pre + N + post) return;
+        int64_t slot;
+        int shift;
+        if (e < pre) { slot = start[n - h] + e; shift = -(int)n; }
+        else if (e < pre + N) { slot = e - pre; shift = 0; }
+        else { slot = e - pre - N; shift = (int)n; }
+        const int p = perm[slot];
+        eperm[e] = p;
+        ecell[e] = cell[p] + shift;
+        const double f = frac[p];
+        efrac[e] = f;
+        if (efracf) efracf[e] = (float)f;
+        return;
+    }
+    const int64_t e = i - 3 * N;
+    if (e > n + w) return;
     int v;
     if (e < h) v = start[n - h + e] - start[n - h];
     else if (e < n + h) v = pre + start[e - h];
     else v = pre + (int)N + start[e - h - n];
     cstart[e] = v;
-}
-
-__global__ void k_sum_turns(const uint64_t* __restrict__ T, int64_t N, unsigned long long* out) {
-    pdl_wait();
-    pdl_trigger();
-    // sum mod 2^64 (exactly sum t_p mod 1); unsigned wrap-around is associative
-    __shared__ unsigned long long s[kTB];
-    unsigned long long acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        acc += T[i];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
-        if (threadIdx.x < d) s[threadIdx.x] += s[threadIdx.x + d];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(out, s[0]);
 }
 
 // ---- spreading (gather) -----------------------------------------------------
@@ -584,26 +593,15 @@ template void launch_grad_nodes<float>(const float2*, const float2*, int64_t, in
 template void launch_grad_nodes<double>(const double2*, const double2*, int64_t, int64_t, double, double*,
                                         cudaStream_t);
 
-void launch_canon(const double* x, int64_t N, uint64_t* T, cudaStream_t s) {
-    Launch L(s, K_GEOMETRY, 16.0 * N);
-    launch_k(k_canon, nblk(N), kTB, 0, s, x, N, T);
-}
-
-void launch_sum_turns(const uint64_t* T, int64_t N, unsigned long long* out, cudaStream_t s) {
-    cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
-    const int blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + kTB - 1) / kTB));
-    Launch L(s, K_GEOMETRY, 8.0 * N);
-    launch_k(k_sum_turns, blocks, kTB, 0, s, T, N, out);
-}
-
 int64_t geometry_scratch_ints(int64_t N, int64_t n) {
-    // cell[N] + count[n+1] + start[n+1] + sums + total
+    // cell[N] (+N pad) + frac[N] doubles + count[n+2] + start[n+2] + sums and
+    // total (even count) + per-block turn sums (unsigned 64-bit)
     const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
-    return 2 * N + 2 * (n + 2) + nb + 2 + 2 * N /* frac as doubles */;
+    return 4 * N + 2 * (n + 2) + ((nb + 3) & ~(int64_t)1) + 2 * (int64_t)nblk(N);
 }
 
-nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n, int w, bool want_float,
-                            int* scratch, cudaStream_t s) {
+nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N, int64_t n, int w,
+                            bool want_float, int* scratch, unsigned long long* sumT, cudaStream_t s) {
     if (n < 2 * w) return fail(NUFFT_ERR_ARG, "grid %lld too small for width %d", (long long)n, w);
     g.N = N; g.n = n; g.w = w;
     int* cell = scratch;
@@ -612,22 +610,23 @@ nufft_status build_geometry(Geometry& g, const uint64_t* T, int64_t N, int64_t n
     int* start = count + (n + 2);
     int* sums = start + (n + 2);
     const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
+    // 8-byte aligned: every earlier block has an even number of ints
+    unsigned long long* partial = reinterpret_cast<unsigned long long*>(sums + ((nb + 3) & ~(int64_t)1));
+    const unsigned np = nblk(N);
     NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
-    NUFFT_CUDA_TRY(cudaMemsetAsync(g.dup_flag, 0, sizeof(int), s));
-    { Launch L(s, K_GEOMETRY, 24.0 * N); launch_k(k_cells, nblk(N), kTB, 0, s, T, N, (uint64_t)n, cell, frac, count); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_scan_blocks, (unsigned)nb, kScanTB, 0, s, count, n + 1, start, sums); }
-    { Launch L(s, K_GEOMETRY, 8.0 * nb); launch_k(k_scan_sums, 1, kScanTB, 0, s, sums, nb, sums + nb); }
+    { Launch L(s, K_GEOMETRY, 36.0 * N);
+      launch_k(k_node_prep, np, kTB, 0, s, x, N, (uint64_t)n, T, cell, frac, count, partial, g.dup_flag); }
+    { Launch L(s, K_GEOMETRY, 12.0 * n); launch_k(k_scan_blocks, (unsigned)nb, kScanTB, 0, s, count, n + 1, start, sums); }
+    { Launch L(s, K_GEOMETRY, 8.0 * nb + 8.0 * np);
+      launch_k(k_scan_sums, 1, kScanTB, 0, s, sums, nb, sums + nb, (const unsigned long long*)partial, (int64_t)np,
+               sumT); }
     { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_scan_add, nblk(n + 1), kTB, 0, s, start, n + 1, sums); }
-    NUFFT_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (n + 1), s));
     { Launch L(s, K_GEOMETRY, 16.0 * N); launch_k(k_scatter, nblk(N), kTB, 0, s, cell, N, start, count, g.srt_perm); }
     { Launch L(s, K_GEOMETRY, 4.0 * n + 16.0 * N); launch_k(k_order_cells, nblk(n), kTB, 0, s, start, n, T, g.srt_perm); }
-    { Launch L(s, K_GEOMETRY, 44.0 * N);
-    launch_k(k_sorted_fill, nblk(N), kTB, 0, s, g.srt_perm, cell, frac, T, N, g.srt_cell, g.srt_frac,
-                                          want_float ? g.srt_fracf : nullptr, g.dup_flag); }
-    { Launch L(s, K_GEOMETRY, 40.0 * N);
-    launch_k(k_ext_fill, nblk(2 * N), kTB, 0, s, start, n, w / 2, N, g.srt_perm, g.srt_cell, g.srt_frac, g.ext_perm,
-                                           g.ext_cell, g.ext_frac, want_float ? g.ext_fracf : nullptr); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_cstart, nblk(n + w + 1), kTB, 0, s, start, n, w, N, g.cstart); }
+    { Launch L(s, K_GEOMETRY, 44.0 * N + 40.0 * N + 8.0 * n);
+      launch_k(k_fill, nblk(3 * N + n + w + 1), kTB, 0, s, start, n, w, N, g.srt_perm, cell, frac, T, g.srt_cell,
+               g.srt_frac, want_float ? g.srt_fracf : nullptr, g.dup_flag, g.ext_perm, g.ext_cell, g.ext_frac,
+               want_float ? g.ext_fracf : nullptr, g.cstart); }
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
