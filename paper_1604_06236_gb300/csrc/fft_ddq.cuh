@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kCols * (1 << RL) / 4) k_fft_ddq(const cdd* __
     pdl_trigger();
     constexpr int R = 1 << RL, TPC = R / 4, C = kCols, TH = C * TPC;
     __shared__ __align__(16) cdd sm[C * R];
+    __shared__ __align__(16) cdd tws[R];                 // W_R^i, i < R, for the stages
     const int tid = threadIdx.x;
     const int nR_log = a.n_log - RL;
     const uint32_t nR = 1u << nR_log;
@@ -45,6 +46,9 @@ __global__ void __launch_bounds__(kCols * (1 << RL) / 4) k_fft_ddq(const cdd* __
     cdd* dst = out + (b << a.n_log);
     const int tw_pass = a.n_log - a.Ns_log - RL;
 
+    // the stages' twiddles W_R^i = W_n^{i n/R}, fetched alongside the data
+#pragma unroll
+    for (int i = 0; i < R / TH; ++i) tws[tid + i * TH] = tw[(uint32_t)(tid + i * TH) << (a.n_log - RL)];
     // load the C columns (C consecutive elements per row), inter-pass twiddle
 #pragma unroll
     for (int i = 0; i < R * C / TH; ++i) {
@@ -75,10 +79,11 @@ __global__ void __launch_bounds__(kCols * (1 << RL) / 4) k_fft_ddq(const cdd* __
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = col[t + q * TPC];
         if (tm != 0) {
-            const int sh = a.n_log - (2 * sl + 2);
+            // W_{4s}^{tm q} = W_R^{tm q R/(4s)}
+            const int sh = RL - (2 * sl + 2);
 #pragma unroll
             for (int q = 1; q < 4; ++q) {
-                cdd w = tw[(uint32_t)(tm * q) << sh];
+                cdd w = tws[(tm * q) << sh];
                 if (dir > 0) w.y = -w.y;
                 v[q] = cmul(v[q], w);
             }
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(kCols * (1 << RL) / 4) k_fft_ddq(const cdd* __
             const int u = t + h * TPC;
             cdd x0 = col[u], x1 = col[u + R / 2];
             if (u != 0) {
-                cdd w = tw[(uint32_t)u << (a.n_log - RL)];
+                cdd w = tws[u];
                 if (dir > 0) w.y = -w.y;
                 x1 = cmul(x1, w);
             }
