@@ -181,6 +181,7 @@ struct Geometry {
     float* ext_fracf = nullptr;  //                                        [2N]
     int* cstart = nullptr;     // [n + w + 1]
     int* dup_flag = nullptr;   // set when two nodes coincide mod 1
+    const int* cell_start = nullptr;   // [n + 1] first sorted slot of each cell (plan scratch: valid while the plan is built)
 };
 
 // ------------------------------------------------------------- launchers --
@@ -238,11 +239,11 @@ void gauss_legendre_half(int nq, GLRule& r);   // nodes in (0,1), weights for in
 // 6: Lambda_k/phihat((k mod P) - K0)
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s);
-// modm_ext[i] = e^{-j 2 pi K0 t_{eperm[i]}}, i < *ext_count; modp_srt[i] =
-// e^{+j 2 pi K0 t_{sperm[i]}}, i < N; str[r][p] = e^{-j 2 pi P r t_p}, r < eta
-void launch_node_phases(const uint64_t* T, const int* eperm, const int* ext_count, const int* sperm, int64_t N,
-                        uint64_t K0, uint64_t P, int eta, double2* modm_ext, double2* modp_srt, double2* str,
-                        cudaStream_t s);
+// modp_srt[i] = e^{+j 2 pi K0 t_{sperm[i]}}, i < N, and its conjugate on every
+// extended slot of the same node (modm_ext); str[r][p] = e^{-j 2 pi P r t_p},
+// r < eta
+void launch_node_phases(const uint64_t* T, const Geometry& g, uint64_t K0, uint64_t P, int eta, double2* modm_ext,
+                        double2* modp_srt, double2* str, cudaStream_t s);
 // Y_m = sum_{r<eta} fac[P r + m] B[r n + (m - K0) mod n]
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s);
@@ -265,9 +266,10 @@ void launch_conv_fold(const c2<T>* c, int64_t n, int64_t P, double rhoP, c2<T>* 
 // w_p (Eqs. 27, 40) into w64 (node order) and the solve-precision slot arrays:
 // sorted slots wt2 = e^{+j 2 pi K0 t}, wt4 = w wt2; extended slots
 // wt1 = e^{-j 2 pi K0 t}, wt5 = w wt1
+// (beta: e^{-j 2 pi N t_p} by node when already at hand, else null)
 template <typename TS>
 void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
-                    const double2* modp_srt, const double2* modm_ext, double rhoP, double2* w64, c2<TS>* wt2_srt,
-                    c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s);
+                    const double2* modp_srt, const double2* modm_ext, const double2* beta, double rhoP, double2* w64,
+                    c2<TS>* wt2_srt, c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s);
 
 }  // namespace nufft45

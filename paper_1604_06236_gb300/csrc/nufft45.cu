@@ -491,8 +491,7 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     // e^{-j 2 pi P r t_p}, r < eta (one spread of eta right-hand sides and a
     // batched FFT on the transforms' grid), folded by Eq. 7 with Eq. 41's
     // coefficients and the deconvolution
-    launch_node_phases(pl->T, gs.ext_perm, ext_count, gs.srt_perm, N, (uint64_t)prm.K0s, (uint64_t)P, eta,
-                       pl->modm64_ext, pl->modp64_srt, str, s);
+    launch_node_phases(pl->T, gs, (uint64_t)prm.K0s, (uint64_t)P, eta, pl->modm64_ext, pl->modp64_srt, str, s);
     launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s, ktab);
     double2* B = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
@@ -521,14 +520,16 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     double2* gsp = nullptr;
     if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
     launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s, ktab);
-    // w_p (Eqs. 27, 40) and the per-slot weights of the transforms
+    // w_p (Eqs. 27, 40) and the per-slot weights of the transforms; the
+    // strengths for r = 1 are e^{-j 2 pi P t_p}, the factor of Eq. 17
+    const double2* beta = eta > 1 ? str + N : nullptr;
     if (f32) {
-        launch_weights<float>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, prm.rhoP, pl->w64,
-                              (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext, (float2*)pl->wt5_ext,
-                              s);
+        launch_weights<float>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, beta, prm.rhoP,
+                              pl->w64, (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext,
+                              (float2*)pl->wt5_ext, s);
     } else {
-        launch_weights<double>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, prm.rhoP, pl->w64,
-                               (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
+        launch_weights<double>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, beta, prm.rhoP,
+                               pl->w64, (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
                                (double2*)pl->wt5_ext, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());

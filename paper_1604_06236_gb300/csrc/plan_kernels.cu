@@ -52,27 +52,41 @@ __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, in
     if (out_f) out_f[k] = (float)v;
 }
 
-// The node-dependent phases of the plan in one launch over three ranges:
-// [0, 2N) e^{-j 2 pi K0 t_p} on the extended slots (p = eperm[i], i below the
-// device-held extended count); [2N, 3N) e^{+j 2 pi K0 t_p} on the sorted slots;
-// [3N, 4N) the strengths of the log-kernel type-1, str[r][p] =
-// e^{-j 2 pi P r t_p}, r < eta (Eqs. 13, 19, 28)
-__global__ void k_node_phases(const uint64_t* __restrict__ T, const int* __restrict__ eperm,
-                              const int* __restrict__ ext_count, const int* __restrict__ sperm, int64_t N, uint64_t K0,
-                              uint64_t P, int eta, double2* __restrict__ modm_ext, double2* __restrict__ modp_srt,
+// The node-dependent phases of the plan in one launch over two ranges:
+// [0, N) sorted slot i, node p = sperm[i]: modp_srt[i] = e^{+j 2 pi K0 t_p},
+// and its conjugate e^{-j 2 pi K0 t_p} on each extended slot that holds p (the
+// middle copy at pre + i, the copy shifted by -n if p lies in the last h
+// cells, the copy shifted by +n if it lies in the first h cells); [N, 2N) node
+// p: the strengths of the log-kernel type-1, str[r][p] = beta^r with
+// beta = e^{-j 2 pi P t_p} (Eqs. 13, 19, 28), beta from the exact turn count
+// and its powers by complex products
+__global__ void k_node_phases(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
+                              const int* __restrict__ start, int64_t n, int h, int64_t N, uint64_t K0, uint64_t P,
+                              int eta, double2* __restrict__ modm_ext, double2* __restrict__ modp_srt,
                               double2* __restrict__ str) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 2 * N) {
-        if (i < (int64_t)*ext_count) modm_ext[i] = cis_turns_t(K0 * T[eperm[i]], -1);
-    } else if (i < 3 * N) {
-        const int64_t k = i - 2 * N;
-        modp_srt[k] = cis_turns_t(K0 * T[sperm[k]], +1);
-    } else if (i < 4 * N) {
-        const int64_t p = i - 3 * N;
-        const uint64_t t = T[p];
-        for (int r = 0; r < eta; ++r) str[(int64_t)r * N + p] = cis_turns_t(P * (uint64_t)r * t, -1);
+    if (i < N) {
+        const double2 m = cis_turns_t(K0 * T[sperm[i]], +1);
+        modp_srt[i] = m;
+        const double2 mc = make_double2(m.x, -m.y);
+        const int last = start[n - h], pre = start[n] - last, post = start[h];
+        modm_ext[pre + i] = mc;
+        if (i >= last) modm_ext[i - last] = mc;
+        if (i < post) modm_ext[pre + N + i] = mc;
+    } else if (i < 2 * N) {
+        const int64_t p = i - N;
+        if (eta > 0) str[p] = make_double2(1.0, 0.0);
+        if (eta > 1) {
+            const double2 b = cis_turns_t(P * T[p], -1);
+            double2 v = b;
+            str[N + p] = b;
+            for (int r = 2; r < eta; ++r) {
+                v = cmul(v, b);
+                str[(int64_t)r * N + p] = v;
+            }
+        }
     }
 }
 
@@ -179,23 +193,24 @@ __global__ void k_to_solve(const double2* __restrict__ in, int64_t n, double sca
 // (p = sperm[i] visits every node once): w64[p], and the solve-precision
 // slot arrays mod_out[i] = e^{+j 2 pi K0 t_p} (modp_srt) and wmod_out[i] = w_p
 // times it
+// (beta, when given, holds e^{-j 2 pi N t_p} by node: the plan's strengths for r = 1)
 template <typename TS>
 __global__ void k_weights_srt(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
-                              const double2* __restrict__ D, const double2* __restrict__ modp_srt, int64_t N,
-                              double rhoP, double2* __restrict__ w64, c2<TS>* __restrict__ mod_out,
-                              c2<TS>* __restrict__ wmod_out) {
+                              const double2* __restrict__ D, const double2* __restrict__ modp_srt,
+                              const double2* __restrict__ beta, int64_t N, double rhoP, double2* __restrict__ w64,
+                              c2<TS>* __restrict__ mod_out, c2<TS>* __restrict__ wmod_out) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int p = sperm[i];
     const uint64_t t = T[p];
-    const double2 e = cis_turns_t((uint64_t)N * t, -1);
+    const double2 e = beta ? beta[p] : cis_turns_t((uint64_t)N * t, -1);
     const double2 z = cis_turns_t(t, +1);
     const double2 h = make_double2(rhoP * e.x - 1.0, rhoP * e.y);
     const double2 den = cmul(h, cmul(D[p], z));
-    const double nn = den.x * den.x + den.y * den.y;
-    const double2 w = make_double2(den.x / nn, -den.y / nn);
+    const double inv = 1.0 / (den.x * den.x + den.y * den.y);
+    const double2 w = make_double2(den.x * inv, -den.y * inv);
     w64[p] = w;
     const double2 m = modp_srt[i];
     mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
@@ -261,12 +276,12 @@ void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64
     launch_k(k_table, nblk(M), kTB, 0, s, ks.w, ks.beta, gl, n, K0, M, log_rho, mode, P, out_d, out_f);
 }
 
-void launch_node_phases(const uint64_t* T, const int* eperm, const int* ext_count, const int* sperm, int64_t N,
-                        uint64_t K0, uint64_t P, int eta, double2* modm_ext, double2* modp_srt, double2* str,
-                        cudaStream_t s) {
-    Launch L(s, K_PLAN_STAGE, 3.0 * N * 28.0 + N * (8.0 + 16.0 * eta));
-    launch_k(k_node_phases, nblk(4 * N), kTB, 0, s, T, eperm, ext_count, sperm, N, K0, P, eta, modm_ext, modp_srt,
-             str);
+void launch_node_phases(const uint64_t* T, const Geometry& g, uint64_t K0, uint64_t P, int eta, double2* modm_ext,
+                        double2* modp_srt, double2* str, cudaStream_t s) {
+    const int64_t N = g.N;
+    Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 3.0 * 16.0) + N * (8.0 + 16.0 * eta));
+    launch_k(k_node_phases, nblk(2 * N), kTB, 0, s, T, g.srt_perm, g.cell_start, g.n, g.w / 2, N, K0, P, eta,
+             modm_ext, modp_srt, str);
 }
 
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
@@ -303,12 +318,13 @@ template void launch_to_solve<double>(const double2*, int64_t, double, double2*,
 
 template <typename TS>
 void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
-                    const double2* modp_srt, const double2* modm_ext, double rhoP, double2* w64, c2<TS>* wt2_srt,
-                    c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s) {
+                    const double2* modp_srt, const double2* modm_ext, const double2* beta, double rhoP, double2* w64,
+                    c2<TS>* wt2_srt, c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s) {
     const int64_t N = g.N;
     {
-        Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0 + 16.0 + 4.0 * sizeof(TS)));
-        launch_k(k_weights_srt<TS>, nblk(N), kTB, 0, s, T, g.srt_perm, D, modp_srt, N, rhoP, w64, wt2_srt, wt4_srt);
+        Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0 + 16.0 + 4.0 * sizeof(TS) + (beta ? 16.0 : 0.0)));
+        launch_k(k_weights_srt<TS>, nblk(N), kTB, 0, s, T, g.srt_perm, D, modp_srt, beta, N, rhoP, w64, wt2_srt,
+                 wt4_srt);
     }
     {
         Launch L(s, K_PLAN_STAGE, 2.0 * N * (4.0 + 16.0 + 16.0 + 4.0 * sizeof(TS)));
@@ -317,11 +333,11 @@ void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, 
     }
 }
 template void launch_weights<float>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
-                                    const double2*, double, double2*, float2*, float2*, float2*, float2*,
-                                    cudaStream_t);
+                                    const double2*, const double2*, double, double2*, float2*, float2*, float2*,
+                                    float2*, cudaStream_t);
 template void launch_weights<double>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
-                                     const double2*, double, double2*, double2*, double2*, double2*, double2*,
-                                     cudaStream_t);
+                                     const double2*, const double2*, double, double2*, double2*, double2*, double2*,
+                                     double2*, cudaStream_t);
 
 nufft_status plan_kernels_init() { return cis_table_ensure(); }
 

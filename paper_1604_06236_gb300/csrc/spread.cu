@@ -58,8 +58,11 @@ __global__ void k_node_prep(const double* __restrict__ x, int64_t N, uint64_t n,
     }
 }
 
-// exclusive scan of int counts, three phases (block scan, scan of block sums,
-// add); out has L + 1 entries, out[L] = total
+// exclusive scan of int counts in two launches: k_scan_blocks scans blocks of
+// kScanPer entries (warp shuffles, then the warps' totals) and writes each
+// block's total; k_scan_add adds to every entry the totals of the blocks
+// before its own.  out has L entries (the caller scans n + 1 counts, the
+// last one zero, so out[n] is the total).
 constexpr int kScanTB = 1024;
 constexpr int kScanPer = 2 * kScanTB;
 
@@ -67,86 +70,69 @@ constexpr int kScanPer = 2 * kScanTB;
 __global__ void k_scan_blocks(int* __restrict__ in, int64_t L, int* __restrict__ out, int* __restrict__ sums) {
     pdl_wait();
     pdl_trigger();
-    __shared__ int s[kScanPer];
-    const int64_t base = (int64_t)blockIdx.x * kScanPer;
-    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x) {
-        int v = 0;
-        if (base + e < L) {
-            v = in[base + e];
-            in[base + e] = 0;
+    __shared__ int wsum[kScanTB / 32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanPer + 2 * threadIdx.x;
+    int a = 0, b = 0;
+    if (i0 < L) { a = in[i0]; in[i0] = 0; }
+    if (i0 + 1 < L) { b = in[i0 + 1]; in[i0 + 1] = 0; }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = a + b;   // inclusive scan of the pair sums within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int u = wsum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, u, d);
+            if (lane >= d) u += t;
         }
-        s[e] = v;
+        wsum[lane] = u;   // inclusive over the warps
     }
     __syncthreads();
-    // Blelloch up-sweep / down-sweep
-    int off = 1;
-    for (int d = kScanPer >> 1; d > 0; d >>= 1) {
-        __syncthreads();
-        if (threadIdx.x < d) {
-            int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
-            s[bi] += s[ai];
-        }
-        off <<= 1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) { sums[blockIdx.x] = s[kScanPer - 1]; s[kScanPer - 1] = 0; }
-    for (int d = 1; d < kScanPer; d <<= 1) {
-        off >>= 1;
-        __syncthreads();
-        if (threadIdx.x < d) {
-            int ai = off * (2 * threadIdx.x + 1) - 1, bi = off * (2 * threadIdx.x + 2) - 1;
-            int t = s[ai]; s[ai] = s[bi]; s[bi] += t;
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kScanPer; e += blockDim.x)
-        if (base + e < L) out[base + e] = s[e];
+    const int base = (wid > 0 ? wsum[wid - 1] : 0) + v - (a + b);   // exclusive, this thread's pair
+    if (i0 < L) out[i0] = base;
+    if (i0 + 1 < L) out[i0 + 1] = base + a;
+    if (threadIdx.x == 0) sums[blockIdx.x] = wsum[kScanTB / 32 - 1];
 }
 
-// (the same block also adds up the per-block turn sums of k_node_prep)
-__global__ void k_scan_sums(int* __restrict__ sums, int64_t nb, int* __restrict__ total,
-                            const unsigned long long* __restrict__ partial, int64_t np,
-                            unsigned long long* __restrict__ sumT) {
+// (block 0 also adds up the per-block turn sums of k_node_prep: sumT)
+__global__ void k_scan_add(int* __restrict__ out, int64_t L, const int* __restrict__ sums,
+                           const unsigned long long* __restrict__ partial, int64_t np,
+                           unsigned long long* __restrict__ sumT) {
     pdl_wait();
     pdl_trigger();
-    // one block, sequential over chunks of blockDim with a carry
-    __shared__ int s[kScanTB];
-    __shared__ int carry;
-    __shared__ unsigned long long r[kScanTB];
-    unsigned long long acc = 0;
-    for (int64_t i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
-    r[threadIdx.x] = acc;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int d = blockDim.x / 2; d > 0; d >>= 1) {
-        if (threadIdx.x < d) r[threadIdx.x] += r[threadIdx.x + d];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *sumT = r[0];
-    for (int64_t base = 0; base < nb; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const int v = i < nb ? sums[i] : 0;
-        s[threadIdx.x] = v;
-        __syncthreads();
-        for (int d = 1; d < (int)blockDim.x; d <<= 1) {
-            int t = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
-            __syncthreads();
-            s[threadIdx.x] += t;
-            __syncthreads();
-        }
-        if (i < nb) sums[i] = carry + s[threadIdx.x] - v;   // exclusive
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void k_scan_add(int* __restrict__ out, int64_t L, const int* __restrict__ sums) {
-    pdl_wait();
-    pdl_trigger();
+    __shared__ int carry_w[kTB / 32];
+    __shared__ unsigned long long r[kTB];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < L) out[i] += sums[i / kScanPer];
+    // this block lies inside scan block sb (kScanPer is a multiple of blockDim)
+    const int64_t sb = ((int64_t)blockIdx.x * blockDim.x) / kScanPer;
+    int c = 0;
+    for (int64_t k = threadIdx.x; k < sb; k += blockDim.x) c += sums[k];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+    if ((threadIdx.x & 31) == 0) carry_w[threadIdx.x >> 5] = c;
+    if (blockIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int64_t k = threadIdx.x; k < np; k += blockDim.x) acc += partial[k];
+        r[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    int carry = 0;
+#pragma unroll
+    for (int w = 0; w < kTB / 32; ++w) carry += carry_w[w];
+    if (i < L) out[i] += carry;
+    if (blockIdx.x == 0) {
+        for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+            if (threadIdx.x < d) r[threadIdx.x] += r[threadIdx.x + d];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *sumT = r[0];
+    }
 }
 
 __global__ void k_scatter(const int* __restrict__ cell, int64_t N, const int* __restrict__ start,
@@ -608,6 +594,7 @@ nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N
     double* frac = reinterpret_cast<double*>(scratch + 2 * N);   // 8-byte aligned: 2N ints
     int* count = scratch + 4 * N;
     int* start = count + (n + 2);
+    g.cell_start = start;
     int* sums = start + (n + 2);
     const int64_t nb = (n + 1 + kScanPer - 1) / kScanPer;
     // 8-byte aligned: every earlier block has an even number of ints
@@ -617,10 +604,9 @@ nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N
     { Launch L(s, K_GEOMETRY, 36.0 * N);
       launch_k(k_node_prep, np, kTB, 0, s, x, N, (uint64_t)n, T, cell, frac, count, partial, g.dup_flag); }
     { Launch L(s, K_GEOMETRY, 12.0 * n); launch_k(k_scan_blocks, (unsigned)nb, kScanTB, 0, s, count, n + 1, start, sums); }
-    { Launch L(s, K_GEOMETRY, 8.0 * nb + 8.0 * np);
-      launch_k(k_scan_sums, 1, kScanTB, 0, s, sums, nb, sums + nb, (const unsigned long long*)partial, (int64_t)np,
-               sumT); }
-    { Launch L(s, K_GEOMETRY, 8.0 * n); launch_k(k_scan_add, nblk(n + 1), kTB, 0, s, start, n + 1, sums); }
+    { Launch L(s, K_GEOMETRY, 8.0 * n + 8.0 * np);
+      launch_k(k_scan_add, nblk(n + 1), kTB, 0, s, start, n + 1, (const int*)sums, (const unsigned long long*)partial,
+               (int64_t)np, sumT); }
     { Launch L(s, K_GEOMETRY, 16.0 * N); launch_k(k_scatter, nblk(N), kTB, 0, s, cell, N, start, count, g.srt_perm); }
     { Launch L(s, K_GEOMETRY, 4.0 * n + 16.0 * N); launch_k(k_order_cells, nblk(n), kTB, 0, s, start, n, T, g.srt_perm); }
     { Launch L(s, K_GEOMETRY, 44.0 * N + 40.0 * N + 8.0 * n);
