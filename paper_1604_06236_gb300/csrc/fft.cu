@@ -923,7 +923,8 @@ static void plan_ddq(int64_t n, std::vector<int>& rl) {
     for (int i = 0; i < L % k; ++i) rl[i] += 1;
 }
 
-static nufft_status exec_ddq(const FFTPlan& p, cdd* buf, cdd* work, int64_t batch, int dir, cudaStream_t s, cdd** result) {
+static nufft_status exec_ddq(const FFTPlan& p, cdd* buf, cdd* work, int64_t batch, int dir, cudaStream_t s, cdd** result,
+                             int cvt_in, int cvt_out) {
     int L = 0;
     while (((int64_t)1 << L) < p.n) ++L;
     const cdd* tw = static_cast<const cdd*>(p.tw_full);
@@ -936,8 +937,8 @@ static nufft_status exec_ddq(const FFTPlan& p, cdd* buf, cdd* work, int64_t batc
         ddq::QArgs a;
         a.n_log = L;
         a.Ns_log = ns_log;
-        a.cvt_in = (i == 0) ? 1 : 0;
-        a.cvt_out = (i + 1 == k) ? 1 : 0;
+        a.cvt_in = (i == 0) ? cvt_in : 0;
+        a.cvt_out = (i + 1 == k) ? cvt_out : 0;
         const int64_t grid = (batch << (L - rl)) / ddq::kCols;
         const unsigned th = (unsigned)(ddq::kCols * (1 << rl) / 4);
         {
@@ -1076,12 +1077,14 @@ template nufft_status fft_exec<dd>(const FFTPlan&, cdd*, cdd*, int64_t, int, cud
 // float64 data through a double-float plan: convert in place, transform,
 // convert the result back in place
 nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
-                         double2** result) {
+                         double2** result, int io) {
+    const int cvt_in = (io & kDdIn) ? 0 : 1, cvt_out = (io & kDdOut) ? 0 : 1;
     if (batch > 0 && !p.q_rlog.empty() && batch * p.n <= kDdqMaxElems) {
         // few vectors: the shared-memory radix-4 passes, converting on the
         // first pass's loads and the last pass's stores
         cdd* r = nullptr;
-        nufft_status st = exec_ddq(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r);
+        nufft_status st = exec_ddq(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r,
+                                   cvt_in, cvt_out);
         if (st != NUFFT_OK) return st;
         *result = reinterpret_cast<double2*>(r);
         return NUFFT_OK;
@@ -1090,21 +1093,21 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
         // the first pass converts on its loads, the last on its stores
         cdd* r = nullptr;
         nufft_status st = exec_p2<dd>(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r,
-                                      1, 1);
+                                      cvt_in, cvt_out);
         if (st != NUFFT_OK) return st;
         *result = reinterpret_cast<double2*>(r);
         return NUFFT_OK;
     }
     const int64_t cnt = p.n * batch;
     const unsigned nb = (unsigned)((cnt + 255) / 256);
-    {
+    if (cvt_in) {
         Launch L(s, K_FFT, 32.0 * cnt, true);
         launch_k(k_to_dd, nb, 256, 0, s, buf, cnt);
     }
     cdd* r = nullptr;
     nufft_status st = fft_exec<dd>(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r);
     if (st != NUFFT_OK) return st;
-    {
+    if (cvt_out) {
         Launch L(s, K_FFT, 32.0 * cnt, true);
         launch_k(k_from_dd, nb, 256, 0, s, reinterpret_cast<double2*>(r), cnt);
     }

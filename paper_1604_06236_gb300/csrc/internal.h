@@ -124,9 +124,12 @@ template <typename T>
 nufft_status fft_exec(const FFTPlan& p, c2<T>* buf, c2<T>* work, int64_t batch, int dir,
                       cudaStream_t s, c2<T>** result);
 // float64 vectors through a double-float plan (prec 3): ~2^-48 relative
-// accuracy with the arithmetic on the float32 pipes
+// accuracy with the arithmetic on the float32 pipes.  io bit 1: the input is
+// already complex double-float (no conversion); bit 2: leave the result in
+// complex double-float.
+constexpr int kDdIn = 1, kDdOut = 2;
 nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t batch, int dir, cudaStream_t s,
-                         double2** result);
+                         double2** result, int io = 0);
 
 // Element-wise work fused into the first pass's loads (lop) and the last
 // pass's stores (sop) of a multi-pass power-of-two FFT; idx is the element's
@@ -206,6 +209,16 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
 template <typename T>
 void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt,
                    c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s, const T* ktab = nullptr);
+// The plan's pair in double-float ("complex double-float": 16 bytes per
+// value, real hi, real lo, imaginary hi, imaginary lo): the spread takes
+// weighted strengths per extended slot (sx[b sx_bs + slot], batch <= 4 per
+// launch row), writes the grid in that format and stores its kernel values as
+// double-float pairs in ktab (N * ks.w); the interpolation reads both and
+// writes dst[perm[i]] = (sum over taps) * wt[i] in float64.
+void launch_spread_plan_dd(const Geometry& g, KernelShape ks, const void* sx, int64_t sx_bs, void* grid,
+                           int64_t batch, cudaStream_t s, void* ktab);
+void launch_interp_plan_dd(const Geometry& g, KernelShape ks, const void* grid, const void* ktab, const double2* wt,
+                           double2* dst, cudaStream_t s);
 
 // out[b][k] = in[b][(k - K0) mod n] * fac[k], k < P
 template <typename T>
@@ -240,10 +253,11 @@ void gauss_legendre_half(int nq, GLRule& r);   // nodes in (0,1), weights for in
 void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64_t M, double log_rho, int mode,
                   int64_t P, double* out_d, float* out_f, cudaStream_t s);
 // modp_srt[i] = e^{+j 2 pi K0 t_{sperm[i]}}, i < N, and its conjugate on every
-// extended slot of the same node (modm_ext); str[r][p] = e^{-j 2 pi P r t_p},
-// r < eta
+// extended slot of the same node (modm_ext); beta[p] = e^{-j 2 pi P t_p}; the
+// plan spread's strengths per extended slot in complex double-float,
+// sx[r * 2N + e] = beta^r e^{-j 2 pi K0 t_p}, r < eta
 void launch_node_phases(const uint64_t* T, const Geometry& g, uint64_t K0, uint64_t P, int eta, double2* modm_ext,
-                        double2* modp_srt, double2* str, cudaStream_t s);
+                        double2* modp_srt, double2* beta, void* sx, cudaStream_t s);
 // Y_m = sum_{r<eta} fac[P r + m] B[r n + (m - K0) mod n]
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,
                  cudaStream_t s);

@@ -461,7 +461,8 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     Sizer zt;
     const int64_t geo_ints = geometry_scratch_ints(N, prm.ns);
     zt.add<int>(geo_ints);
-    zt.add<double2>((size_t)eta * N);                                    // strengths
+    zt.add<double2>((size_t)N);                                          // e^{-j 2 pi P t_p}
+    zt.add<double2>((size_t)eta * 2 * N);                                // strengths per extended slot (dd)
     zt.add<double2>((size_t)eta * prm.ns);                               // grids
     zt.add<double2>((size_t)eta * fft_work_elems(tab.fft_ns64));
     zt.add<double2>(P); zt.add<double2>(fft_work_elems(tab.fft_P64));
@@ -471,7 +472,8 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     Arena tmp;
     if ((st = tmp.reserve(zt.used, s)) != NUFFT_OK) return st;
     int* geo = tmp.take<int>(geo_ints);
-    double2* str = tmp.take<double2>((size_t)eta * N);
+    double2* beta64 = tmp.take<double2>((size_t)N);
+    double2* sx = tmp.take<double2>((size_t)eta * 2 * N);
     double2* grid = tmp.take<double2>((size_t)eta * prm.ns);
     double2* gwork = tmp.take<double2>((size_t)eta * fft_work_elems(tab.fft_ns64));
     double2* vecP = tmp.take<double2>(P);
@@ -491,25 +493,29 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     // e^{-j 2 pi P r t_p}, r < eta (one spread of eta right-hand sides and a
     // batched FFT on the transforms' grid), folded by Eq. 7 with Eq. 41's
     // coefficients and the deconvolution
-    launch_node_phases(pl->T, gs, (uint64_t)prm.K0s, (uint64_t)P, eta, pl->modm64_ext, pl->modp64_srt, str, s);
-    launch_spread<double>(gs, prm.ks_plan, str, N, pl->modm64_ext, grid, eta, s, ktab);
+    // (the spread, its grid and the FFT's input stay in double-float)
+    launch_node_phases(pl->T, gs, (uint64_t)prm.K0s, (uint64_t)P, eta, pl->modm64_ext, pl->modp64_srt, beta64, sx, s);
+    launch_spread_plan_dd(gs, prm.ks_plan, sx, 2 * N, grid, eta, s, ktab);
     double2* B = nullptr;
-    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, eta, -1, s, &B)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, eta, -1, s, &B, kDdIn)) != NUFFT_OK) {
+        tmp.release();
+        return st;
+    }
     launch_fold(B, prm.ns, prm.K0s, tab.fold, P, eta, vecP, s);
     double2* v = nullptr;
-    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, +1, s, &v)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, +1, s, &v, 0)) != NUFFT_OK) { tmp.release(); return st; }
     // K_q (Eq. 29)
     // K_q (Eq. 29), with the copy that the DFT of Eq. 43 transforms in place
     launch_kernel_samples(v, P, sumT, pl->K64, f32 ? (float2*)pl->Ks : nullptr, f32 ? nullptr : (double2*)pl->Ks,
                           vecP, s);
     double2* F = nullptr;
-    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, -1, s, &F)) != NUFFT_OK) { tmp.release(); return st; }
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_P64, vecP, workP, 1, -1, s, &F, 0)) != NUFFT_OK) { tmp.release(); return st; }
     if (prm.toeplitz) {
         // DFT of L_0..L_P zero-padded to the grid size (ns >= 2P), / ns, for
         // the middle stage as a linear convolution
         launch_lagrange_pad(F, P, prm.rhoP, tab.sneg64, prm.ns, grid, s);
         double2* FLd = nullptr;
-        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, -1, s, &FLd)) != NUFFT_OK) { tmp.release(); return st; }
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, -1, s, &FLd, 0)) != NUFFT_OK) { tmp.release(); return st; }
         if (f32) launch_to_solve<float>(FLd, prm.ns, 1.0 / (double)prm.ns, (float2*)pl->FL, s);
         else launch_to_solve<double>(FLd, prm.ns, 1.0 / (double)prm.ns, (double2*)pl->FL, s);
     }
@@ -517,12 +523,16 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     // grid, then L'(z_p) by a type-2 NUFFT on the transforms' grid (float64,
     // plan width)
     launch_lcoef_place(F, P, tab.sneg64, prm.K0s, tab.plan_place, prm.ns, grid, s);
+    // (the FFT leaves its result in double-float for the interpolation)
     double2* gsp = nullptr;
-    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, +1, s, &gsp)) != NUFFT_OK) { tmp.release(); return st; }
-    launch_interp<double>(gs, prm.ks_plan, gsp, pl->modp64_srt, pl->D64, N, 1, s, ktab);
-    // w_p (Eqs. 27, 40) and the per-slot weights of the transforms; the
-    // strengths for r = 1 are e^{-j 2 pi P t_p}, the factor of Eq. 17
-    const double2* beta = eta > 1 ? str + N : nullptr;
+    if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, grid, gwork, 1, +1, s, &gsp, kDdOut)) != NUFFT_OK) {
+        tmp.release();
+        return st;
+    }
+    launch_interp_plan_dd(gs, prm.ks_plan, gsp, ktab, pl->modp64_srt, pl->D64, s);
+    // w_p (Eqs. 27, 40) and the per-slot weights of the transforms, with
+    // e^{-j 2 pi P t_p} (the factor of Eq. 17) from the node phases
+    const double2* beta = beta64;
     if (f32) {
         launch_weights<float>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, beta, prm.rhoP,
                               pl->w64, (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext,
@@ -766,11 +776,11 @@ nufft_status forward64(const nufft_plan_s* pl, bool type2, const double2* x, dou
     nufft_status st;
     if (type2) {
         launch_place<double>(x, N, N, prm.K0s, tab.plan_place, g, prm.ns, bc, s);
-        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, +1, s, &r)) != NUFFT_OK) return st;
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, +1, s, &r, 0)) != NUFFT_OK) return st;
         launch_interp<double>(pl->gs, prm.ks_plan, r, pl->modp64_srt, y, N, bc, s);
     } else {
         launch_spread<double>(pl->gs, prm.ks_plan, x, N, pl->modm64_ext, g, bc, s);
-        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, -1, s, &r)) != NUFFT_OK) return st;
+        if ((st = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, g, gw, bc, -1, s, &r, 0)) != NUFFT_OK) return st;
         launch_select<double>(r, prm.ns, y, N, N, prm.K0s, tab.plan_place, bc, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());

@@ -3,6 +3,7 @@
 // node weights (Secs. III-C to III-E).
 #include "internal.h"
 #include "cis64.cuh"
+#include "df.cuh"
 
 #include <cmath>
 
@@ -52,41 +53,43 @@ __global__ void k_table(int w, double beta, GLRule gl, int64_t n, int64_t K0, in
     if (out_f) out_f[k] = (float)v;
 }
 
-// The node-dependent phases of the plan in one launch over two ranges:
-// [0, N) sorted slot i, node p = sperm[i]: modp_srt[i] = e^{+j 2 pi K0 t_p},
-// and its conjugate e^{-j 2 pi K0 t_p} on each extended slot that holds p (the
-// middle copy at pre + i, the copy shifted by -n if p lies in the last h
-// cells, the copy shifted by +n if it lies in the first h cells); [N, 2N) node
-// p: the strengths of the log-kernel type-1, str[r][p] = beta^r with
-// beta = e^{-j 2 pi P t_p} (Eqs. 13, 19, 28), beta from the exact turn count
-// and its powers by complex products
+// The node-dependent phases of the plan, one thread per sorted slot i, node
+// p = sperm[i]: modp_srt[i] = m = e^{+j 2 pi K0 t_p}; beta[p] =
+// e^{-j 2 pi P t_p}; and on each extended slot e that holds p (the middle copy
+// at pre + i, the copy shifted by -n if p lies in the last h cells, the copy
+// shifted by +n if it lies in the first h cells) conj(m) and the strengths of
+// the log-kernel type-1 weighted by it, sx[r][e] = beta^r conj(m), r < eta
+// (Eqs. 13, 19, 28), formed in double-float from the two exact-turn phases
 __global__ void k_node_phases(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
                               const int* __restrict__ start, int64_t n, int h, int64_t N, uint64_t K0, uint64_t P,
                               int eta, double2* __restrict__ modm_ext, double2* __restrict__ modp_srt,
-                              double2* __restrict__ str) {
+                              double2* __restrict__ beta, cdd* __restrict__ sx) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) {
-        const double2 m = cis_turns_t(K0 * T[sperm[i]], +1);
-        modp_srt[i] = m;
-        const double2 mc = make_double2(m.x, -m.y);
-        const int last = start[n - h], pre = start[n] - last, post = start[h];
-        modm_ext[pre + i] = mc;
-        if (i >= last) modm_ext[i - last] = mc;
-        if (i < post) modm_ext[pre + N + i] = mc;
-    } else if (i < 2 * N) {
-        const int64_t p = i - N;
-        if (eta > 0) str[p] = make_double2(1.0, 0.0);
-        if (eta > 1) {
-            const double2 b = cis_turns_t(P * T[p], -1);
-            double2 v = b;
-            str[N + p] = b;
-            for (int r = 2; r < eta; ++r) {
-                v = cmul(v, b);
-                str[(int64_t)r * N + p] = v;
-            }
-        }
+    if (i >= N) return;
+    const int p = sperm[i];
+    const uint64_t t = T[p];
+    const double2 m = cis_turns_t(K0 * t, +1);
+    const double2 b = cis_turns_t(P * t, -1);
+    modp_srt[i] = m;
+    beta[p] = b;
+    const double2 mc = make_double2(m.x, -m.y);
+    const int last = start[n - h], pre = start[n] - last, post = start[h];
+    int64_t e[3];
+    int ne = 0;
+    e[ne++] = pre + i;
+    if (i >= last) e[ne++] = i - last;
+    if (i < post) e[ne++] = pre + N + i;
+    cdd v, bd;
+    v.x = dd_from_double(mc.x);
+    v.y = dd_from_double(mc.y);
+    bd.x = dd_from_double(b.x);
+    bd.y = dd_from_double(b.y);
+    for (int k = 0; k < ne; ++k) modm_ext[e[k]] = mc;
+    for (int r = 0; r < eta; ++r) {
+        for (int k = 0; k < ne; ++k) sx[(int64_t)r * 2 * N + e[k]] = v;
+        v = cmul(v, bd);
     }
 }
 
@@ -277,11 +280,11 @@ void launch_table(KernelShape ks, const GLRule& gl, int64_t n, int64_t K0, int64
 }
 
 void launch_node_phases(const uint64_t* T, const Geometry& g, uint64_t K0, uint64_t P, int eta, double2* modm_ext,
-                        double2* modp_srt, double2* str, cudaStream_t s) {
+                        double2* modp_srt, double2* beta, void* sx, cudaStream_t s) {
     const int64_t N = g.N;
-    Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 3.0 * 16.0) + N * (8.0 + 16.0 * eta));
-    launch_k(k_node_phases, nblk(2 * N), kTB, 0, s, T, g.srt_perm, g.cell_start, g.n, g.w / 2, N, K0, P, eta,
-             modm_ext, modp_srt, str);
+    Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0) + 2.0 * N * (16.0 + 16.0 * eta));
+    launch_k(k_node_phases, nblk(N), kTB, 0, s, T, g.srt_perm, g.cell_start, g.n, g.w / 2, N, K0, P, eta, modm_ext,
+             modp_srt, beta, static_cast<cdd*>(sx));
 }
 
 void launch_fold(const double2* B, int64_t n, int64_t K0, const double* fac, int64_t P, int eta, double2* Y,

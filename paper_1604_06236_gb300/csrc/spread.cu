@@ -308,14 +308,19 @@ __constant__ float2 c_exp2_64[64] = NUFFT_EXP2_64_TABLE;
 // issues at 1/64 of the float32 rate, and exp/sqrt per tap made the float64
 // spread bound by it.  Same gather and tables as k_spread; the float64 inputs
 // are converted once per staged node, the outputs once per grid point.
-template <int BC>
+// DDIO (the plan's log-kernel type-1): the strengths come per extended slot,
+// already weighted and in double-float (sx[b sx_bs + slot], complex
+// double-float), the grid is written in double-float and so are the stored
+// kernel values, so no value crosses the float64 pipe.
+template <int BC, bool DDIO>
 __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
                                                    const int* __restrict__ cstart, const int* __restrict__ eperm,
                                                    const int* __restrict__ ecell, const double* __restrict__ efrac,
                                                    const double2* __restrict__ src, int64_t src_bs,
                                                    const double2* __restrict__ wt, double2* __restrict__ grid,
                                                    int64_t batch, double* __restrict__ ktab,
-                                                   const int* __restrict__ pre_at, int64_t N) {
+                                                   const int* __restrict__ pre_at, int64_t N,
+                                                   const cdd* __restrict__ sx, int64_t sx_bs) {
     pdl_wait();
     pdl_trigger();
     __shared__ int s_cell[kChunk];
@@ -340,16 +345,27 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
             const int i = ch + e;
             s_cell[e] = ecell[i];
             s_frac[e] = dd_from_double(efrac[i]);
-            const double2 wv = wt[i];
-            const int p = src ? eperm[i] : 0;
+            if constexpr (DDIO) {
 #pragma unroll
-            for (int b = 0; b < BC; ++b) {
-                double2 v = wv;
-                if (src) v = (b0 + b < batch) ? cmul(src[(b0 + b) * src_bs + p], wv) : make_double2(0.0, 0.0);
-                cdd c;
-                c.x = dd_from_double(v.x);
-                c.y = dd_from_double(v.y);
-                s_str[b][e] = c;
+                for (int b = 0; b < BC; ++b) {
+                    cdd c;
+                    c.x = dd(0.f, 0.f);
+                    c.y = dd(0.f, 0.f);
+                    if (b0 + b < batch) c = sx[(b0 + b) * sx_bs + i];
+                    s_str[b][e] = c;
+                }
+            } else {
+                const double2 wv = wt[i];
+                const int p = src ? eperm[i] : 0;
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    double2 v = wv;
+                    if (src) v = (b0 + b < batch) ? cmul(src[(b0 + b) * src_bs + p], wv) : make_double2(0.0, 0.0);
+                    cdd c;
+                    c.x = dd_from_double(v.x);
+                    c.y = dd_from_double(v.y);
+                    s_str[b][e] = c;
+                }
             }
         }
         __syncthreads();
@@ -362,7 +378,9 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
             const dd ph = es_kernel_dd(d, 0.5f * (float)w, beta, s_exp);
             if (keep) {
                 const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
-                ktab[slot * w + (g - s_cell[e]) + w / 2 - 1] = dd_to_double(ph);
+                const int64_t k = slot * w + (g - s_cell[e]) + w / 2 - 1;
+                if constexpr (DDIO) reinterpret_cast<dd*>(ktab)[k] = ph;
+                else ktab[k] = dd_to_double(ph);
             }
 #pragma unroll
             for (int b = 0; b < BC; ++b) {
@@ -373,9 +391,43 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
     }
     if (g < n) {
 #pragma unroll
-        for (int b = 0; b < BC; ++b)
-            if (b0 + b < batch) grid[(b0 + b) * n + g] = make_double2(dd_to_double(acc[b].x), dd_to_double(acc[b].y));
+        for (int b = 0; b < BC; ++b) {
+            if (b0 + b < batch) {
+                if constexpr (DDIO) reinterpret_cast<cdd*>(grid)[(b0 + b) * n + g] = acc[b];
+                else grid[(b0 + b) * n + g] = make_double2(dd_to_double(acc[b].x), dd_to_double(acc[b].y));
+            }
+        }
     }
+}
+
+// The plan's type-2 for L'(z_p) in double-float: the grid (complex
+// double-float) and the kernel values the plan's spread stored (double-float,
+// by sorted slot and tap) are combined on the float32 pipes; the sum is
+// converted once per node and multiplied by wt (float64, by sorted slot) into
+// dst[perm[i]].
+__global__ void __launch_bounds__(kTB) k_interp_plan_dd(int64_t N, int64_t n, int w, const int* __restrict__ sperm,
+                                                        const int* __restrict__ scell, const cdd* __restrict__ grid,
+                                                        const dd* __restrict__ ktab, const double2* __restrict__ wt,
+                                                        double2* __restrict__ dst) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int h = w / 2;
+    int64_t gi = scell[i] + 1 - h;
+    if (gi < 0) gi += n;
+    cdd acc;
+    acc.x = dd(0.f, 0.f);
+    acc.y = dd(0.f, 0.f);
+    for (int m = 0; m < w; ++m) {
+        const dd k = ktab[i * w + m];
+        const cdd v = grid[gi];
+        acc.x += k * v.x;
+        acc.y += k * v.y;
+        if (++gi == n) gi = 0;
+    }
+    const double2 a = make_double2(dd_to_double(acc.x), dd_to_double(acc.y));
+    dst[sperm[i]] = cmul(a, wt[i]);
 }
 
 template <typename T, int BC>
@@ -636,12 +688,13 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
         double2* gd = reinterpret_cast<double2*>(grid);
         double* kd = reinterpret_cast<double*>(ktab);
         if (batch == 1) {
-            launch_k(k_spread_dd<1>, dim3(nblk(g.n), 1), kTB, 0, s, g.n, ks.w, beta_dd, cs, g.ext_perm,
-                     g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2, g.N);
+            launch_k(k_spread_dd<1, false>, dim3(nblk(g.n), 1), kTB, 0, s, g.n, ks.w, beta_dd, cs, g.ext_perm,
+                     g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2, g.N, (const cdd*)nullptr,
+                     (int64_t)0);
         } else {
-            launch_k(k_spread_dd<4>, dim3(nblk(g.n), (unsigned)((batch + 3) / 4)), kTB, 0, s, g.n, ks.w,
+            launch_k(k_spread_dd<4, false>, dim3(nblk(g.n), (unsigned)((batch + 3) / 4)), kTB, 0, s, g.n, ks.w,
                      beta_dd, cs, g.ext_perm, g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2,
-                     g.N);
+                     g.N, (const cdd*)nullptr, (int64_t)0);
         }
         return;
     }
@@ -676,6 +729,25 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
         launch_k(k_interp<T, 4>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch, ktab);
     }
+}
+
+void launch_spread_plan_dd(const Geometry& g, KernelShape ks, const void* sx, int64_t sx_bs, void* grid,
+                           int64_t batch, cudaStream_t s, void* ktab) {
+    const int* cs = g.cstart + (g.w - ks.w) / 2;
+    Launch L(s, K_SPREAD, batch * 2.0 * g.N * 16.0 + g.N * (8.0 + 8.0) + 4.0 * (g.n + g.w) + batch * g.n * 16.0 +
+                              g.N * ks.w * 8.0, true);
+    const dd beta_dd(ks.beta);
+    launch_k(k_spread_dd<4, true>, dim3(nblk(g.n), (unsigned)((batch + 3) / 4)), kTB, 0, s, g.n, ks.w, beta_dd, cs,
+             g.ext_perm, g.ext_cell, (const double*)g.ext_frac, (const double2*)nullptr, (int64_t)0,
+             (const double2*)nullptr, static_cast<double2*>(grid), batch, static_cast<double*>(ktab),
+             g.cstart + g.w / 2, g.N, static_cast<const cdd*>(sx), sx_bs);
+}
+
+void launch_interp_plan_dd(const Geometry& g, KernelShape ks, const void* grid, const void* ktab, const double2* wt,
+                           double2* dst, cudaStream_t s) {
+    Launch L(s, K_INTERP, g.N * ks.w * (16.0 + 8.0) + g.N * (8.0 + 16.0 + 16.0), true);
+    launch_k(k_interp_plan_dd, nblk(g.N), kTB, 0, s, g.N, g.n, ks.w, g.srt_perm, g.srt_cell,
+             static_cast<const cdd*>(grid), static_cast<const dd*>(ktab), wt, dst);
 }
 
 template <typename T>
