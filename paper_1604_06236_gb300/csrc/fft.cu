@@ -502,7 +502,7 @@ nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta,
     cuuint64_t dims[4] = {nR, (cuuint64_t)R2, (cuuint64_t)R1, (cuuint64_t)batch};
     cuuint64_t strides[3] = {nR * sizeof(float2), (cuuint64_t)R2 * nR * sizeof(float2),
                              (1ull << ta.n_log) * sizeof(float2)};
-    cuuint32_t box[4] = {(cuuint32_t)G::C, (cuuint32_t)R2, (cuuint32_t)R1, 1};
+    cuuint32_t box[4] = {(cuuint32_t)G::C, (cuuint32_t)R2, (cuuint32_t)(ta.lop == 3 ? R1 / 4 : R1), 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (tma_encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<float2*>(in), dims, strides, box, es,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -537,7 +537,8 @@ nufft_status try_p2t(const FFTPlan& p, const c2<T>* in, c2<T>* out, const p2::Ar
         return NUFFT_OK;
     } else {
         if (!p.tw_full || p.p2_rlog.size() < 2 || (a.R_log != 8 && a.R_log != 9)) return NUFFT_OK;
-        if (a.lop != 0 && a.lop != 2) return NUFFT_OK;
+        if (a.lop != 0 && a.lop != 2 && a.lop != 3) return NUFFT_OK;
+        if (a.lop == 3 && a.Ns_log != 0) return NUFFT_OK;
         if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15)) return NUFFT_OK;
         const int clog = p2_C_log<float>(a.R_log);
         if (clog > a.n_log - a.R_log) return NUFFT_OK;                       // a tile stays inside one vector
@@ -741,13 +742,16 @@ nufft_status exec_p2_hooked(const FFTPlan& p, const c2<T>* in, c2<T>* work, c2<T
         if (a.sop == 4) { a.sel_off = h.K0; a.sel_len = h.ns; }
         {
             // algorithmic bytes: one read and one write of the vectors (the
-            // selecting store writes P of the n outputs)
+            // selecting store writes P of the n outputs, the half-support
+            // load reads n/2 of the n inputs)
             const double wr = (a.sop == 3) ? (double)h.P : (double)p.n;
-            Launch Lk(s, K_FFT, ((double)p.n + wr) * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
+            const double rd = (a.lop == 3) ? 0.5 * (double)p.n : (double)p.n;
+            Launch Lk(s, K_FFT, (rd + wr) * (double)batch * sizeof(c2<T>), sizeof(T) == 8);
             bool done = false;
             nufft_status st = try_p2t<T>(p, src, dst, a, batch, dir, s, &done);
             if (st == NUFFT_OK && !done) {
-                if (a.sop >= 3) return fail(NUFFT_ERR_ARG, "scattering FFT stores need the TMA-fed pass");
+                if (a.sop >= 3 || a.lop == 3)
+                    return fail(NUFFT_ERR_ARG, "scattering FFT stores and half-support loads need the TMA-fed pass");
                 st = launch_p2<T>(rl, src, dst, a, lo, hi, dir, s);
             }
             if (st != NUFFT_OK) return st;

@@ -69,9 +69,11 @@ __global__ void __launch_bounds__(kCols * (1 << RL) / 4) k_fft_ddq(const cdd* __
     // radix-4 Stockham stages inside each column: with the stage's block
     // length s, thread t reads col[t + q R/4], q < 4, twiddles by
     // W_{4s}^{(t mod s) q}, and writes col[(t - t mod s) 4 + t mod s + m s]
+    // (a rolled loop: each SM runs these stages once or twice per launch, so a
+    // fully unrolled body would be fetched cold from the instruction cache)
     const int c = tid / TPC, t = tid % TPC;
     cdd* col = sm + c * R;
-#pragma unroll
+#pragma unroll 1
     for (int sl = 0; 2 * sl + 2 <= RL; ++sl) {
         const int s = 1 << (2 * sl);
         const int tm = t & (s - 1);

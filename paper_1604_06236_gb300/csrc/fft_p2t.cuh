@@ -53,7 +53,11 @@ struct TArgs {
     int n_log, R_log, Ns_log, C_log;
     int ntiles;
     const float2* fmul;   // FUSE: the pointwise factor between the two transforms (length n)
-    // lop 2: x = in[idx] * fac_in[idx]; sop 1: y *= mulc[idx]; sop 2: y *= fac_out[idx];
+    // lop 2: x = in[idx] * fac_in[idx]; lop 3 (first pass): the input is zero
+    // outside rows k1 < R1/4 and k1 >= 3 R1/4 (a spectrum centred on the
+    // grid's index 0 that fills half of it): only those rows are loaded, as two
+    // boxes of R1/4 rows, and the others enter the DFT as zeros;
+    // sop 1: y *= mulc[idx]; sop 2: y *= fac_out[idx];
     // sop 3: k = (idx + off) mod n, if k < len: out[b out_bs + k] = y fac_out[k];
     // sop 4: out[b out_bs + ((idx - off) mod len)] = y fac_out[idx]
     int lop, sop;
@@ -95,12 +99,20 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, ui
 }
 
 template <int R1, int R2>
-__device__ __forceinline__ void issue(const CUtensorMap* tm, float2* st, uint64_t* bar, int tile, int nR_log) {
+__device__ __forceinline__ void issue(const CUtensorMap* tm, float2* st, uint64_t* bar, int tile, int nR_log,
+                                      bool half) {
     using G = TCfg<R1, R2>;
     const int g0 = tile * G::C;
     const int b = g0 >> nR_log, j0 = g0 & ((1 << nR_log) - 1);
-    mbar_expect_tx(bar, G::TILE_BYTES);
-    tma_load_4d(st, tm, bar, j0, 0, 0, b);
+    if (half) {
+        // rows k1 < R1/4 and k1 >= 3 R1/4 (the tensor map's box is R1/4 rows high)
+        mbar_expect_tx(bar, G::TILE_BYTES / 2);
+        tma_load_4d(st, tm, bar, j0, 0, 0, b);
+        tma_load_4d(st + (3 * R1 / 4) * R2 * G::C, tm, bar, j0, 0, 3 * R1 / 4, b);
+    } else {
+        mbar_expect_tx(bar, G::TILE_BYTES);
+        tma_load_4d(st, tm, bar, j0, 0, 0, b);
+    }
 }
 
 // staged (Ns = 1) store layout: output m of column c at c R + (m ^ swz(c));
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int s = 0; s < S; ++s) {
             const int t = tile + s * step;
-            if (t < ntiles) issue<R1, R2>(&tm, stage + s * TILE, &bars[s], t, nR_log);
+            if (t < ntiles) issue<R1, R2>(&tm, stage + s * TILE, &bars[s], t, nR_log, a.lop == 3);
         }
     }
     __syncthreads();
@@ -175,8 +187,12 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         }
         // step A: DFT over k1 of column ca, then the inner twiddle W_R^{m1 k2}
         float2 v[R1];
+        const bool half = a.lop == 3;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) v[k1] = st[(k1 * R2 + k2) * C + ca];
+        for (int k1 = 0; k1 < R1; ++k1) {
+            const bool mid = k1 >= R1 / 4 && k1 < 3 * R1 / 4;
+            v[k1] = (half && mid) ? make_float2(0.f, 0.f) : st[(k1 * R2 + k2) * C + ca];
+        }
         if (a.lop == 2) {
             const float* fac = a.fac_in + j0 + ca;
 #pragma unroll
@@ -298,7 +314,7 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         __syncthreads();
         if (tid == 0) {
             const int t = tile + S * step;
-            if (t < ntiles) issue<R1, R2>(&tm, st, &bars[s], t, nR_log);
+            if (t < ntiles) issue<R1, R2>(&tm, st, &bars[s], t, nR_log, a.lop == 3);
         }
     }
     // after an expired wait, let the copies still in flight land before the CTA ends

@@ -136,6 +136,9 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
 // position in its length-n vector:
 //   lop 1: x[idx] = src[b * src_bs + ((idx - K0) mod ns)] * fac_in[idx]
 //   lop 2: x[idx] = in[idx] * fac_in[idx]
+//   lop 3: the input is known to be zero outside idx < n/4 and idx >= 3n/4
+//          (a centred spectrum filling half of the grid): only that half is
+//          read, so the rest of `in` need not be cleared
 //   sop 1: y[idx] *= mulc[idx];   sop 2: y[idx] *= fac_out[idx]
 // and two scattering stores, where `out` has batch stride out_bs:
 //   sop 3 (select): k = (idx + K0) mod n; if k < P: out[b out_bs + k] = y[idx] fac_out[k]

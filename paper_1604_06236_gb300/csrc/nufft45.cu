@@ -674,14 +674,22 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                 // Eq. 37's rho^k on the loads and Eq. 30's x K on the stores of
                 // the inverse FFT; the forward FFT's last pass places its
                 // outputs on the grid with Eq. 31 and the deconvolution folded
-                // into fac4 (the other ns - N grid points are zeroed); grid
-                // FFT; type-2; x w (Eq. 40)
-                const int64_t g0 = imod(P - K0, ns), gap = ns - P;
-                const int64_t first = std::min(gap, ns - g0);
-                if (first > 0)
-                    NUFFT_CUDA_TRY(cudaMemset2DAsync(gA + g0, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * first, bc, s));
-                if (gap > first)
-                    NUFFT_CUDA_TRY(cudaMemset2DAsync(gA, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * (gap - first), bc, s));
+                // into fac4; grid FFT; type-2; x w (Eq. 40).  With ns = 2P and
+                // K0 = P/2 the placed outputs fill exactly grid indices
+                // g < ns/4 and g >= 3ns/4, and the grid FFT's first pass reads
+                // only those (the other half is zero and is never written);
+                // otherwise the other ns - N grid points are zeroed
+                const bool half = ns == 2 * P && K0 == P / 2;
+                if (!half) {
+                    const int64_t g0 = imod(P - K0, ns), gap = ns - P;
+                    const int64_t first = std::min(gap, ns - g0);
+                    if (first > 0)
+                        NUFFT_CUDA_TRY(
+                            cudaMemset2DAsync(gA + g0, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * first, bc, s));
+                    if (gap > first)
+                        NUFFT_CUDA_TRY(
+                            cudaMemset2DAsync(gA, sizeof(c2<T>) * ns, 0, sizeof(c2<T>) * (gap - first), bc, s));
+                }
                 if (conv) {
                     FFTHooks hc;
                     hc.lop = 2; hc.fac_in = rpos;
@@ -696,7 +704,14 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
                     h2.sop = 4; h2.K0 = K0; h2.ns = ns; h2.out_bs = ns; h2.fac_out = fac4;
                     if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_P, vA, vW, gA, bc, -1, h2, s)) != NUFFT_OK) return st;
                 }
-                if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
+                if (half) {
+                    FFTHooks hg;
+                    hg.lop = 3;
+                    if ((st = traced_fft(s, sizeof(T) == 8, fft_exec_hooked<T>, tab.fft_ns, gA, gW, gA, bc, +1, hg, s)) != NUFFT_OK) return st;
+                    r = gA;
+                } else if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) {
+                    return st;
+                }
                 launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
                 break;
             }
