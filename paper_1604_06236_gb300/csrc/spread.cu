@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
         const int pre = keep ? *pre_at : 0;
         for (int i = a; i < z; ++i) {
             const int e = i - ch;
-            const T d = (T)(g - s_cell[e]) - s_frac[e];
+            const T d = (T)(int)(g - s_cell[e]) - s_frac[e];   // small offset: a 32-bit integer conversion
             const T ph = es_kernel<T>(d, two_over_w, beta);
             if (keep) {
                 const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
         const int pre = keep ? *pre_at : 0;
         for (int i = a; i < z; ++i) {
             const int e = i - ch;
-            const dd d = dd((float)(g - s_cell[e]), 0.f) - s_frac[e];
+            const dd d = dd((float)(int)(g - s_cell[e]), 0.f) - s_frac[e];
             const dd ph = es_kernel_dd(d, 0.5f * (float)w, beta, s_exp);
             if (keep) {
                 const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
