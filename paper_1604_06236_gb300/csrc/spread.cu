@@ -706,9 +706,14 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
         dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
         launch_k(k_spread<T, 4>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
-    } else {
+    } else if (batch <= 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
         launch_k(k_spread<T, 8>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
+                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
+    } else {
+        // 16 right-hand sides per block row: each kernel value serves twice as many
+        dim3 gr(nblk(g.n), (unsigned)((batch + 15) / 16));
+        launch_k(k_spread<T, 16>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
     }
 }
@@ -724,9 +729,14 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
         dim3 gr(nblk(g.N), 1);
         launch_k(k_interp<T, 1>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch, ktab);
-    } else {
+    } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.N), (unsigned)((batch + 3) / 4));
         launch_k(k_interp<T, 4>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
+                                          dst_bs, batch, ktab);
+    } else {
+        // 8 right-hand sides per block row: each kernel value serves twice as many
+        dim3 gr(nblk(g.N), (unsigned)((batch + 7) / 8));
+        launch_k(k_interp<T, 8>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch, ktab);
     }
 }
