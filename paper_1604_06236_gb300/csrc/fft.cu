@@ -913,9 +913,11 @@ nufft_status fft_wait_status(cudaStream_t s) {
 // passes of the few-vector double-float kernel: n = 2^L, L >= 11, split into
 // balanced radices 2^5 .. 2^10 (at least two passes, so that every pass has
 // n/R >= 2 columns)
-// batches up to this many points take the few-vector kernel; beyond it the
-// radix-64 streaming passes already fill the GPU with threads
-constexpr int64_t kDdqMaxElems = (int64_t)1 << 21;
+// batches up to this many points take the shared-memory radix-4 kernel (for
+// few vectors its threads are what the pass needs; for the all-float64 path's
+// batches its radix-1024 passes save a pass over the radix-64 streaming
+// ones); beyond it the streaming passes
+constexpr int64_t kDdqMaxElems = (int64_t)1 << 26;
 
 static void plan_ddq(int64_t n, std::vector<int>& rl) {
     rl.clear();
@@ -1084,8 +1086,8 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
                          double2** result, int io) {
     const int cvt_in = (io & kDdIn) ? 0 : 1, cvt_out = (io & kDdOut) ? 0 : 1;
     if (batch > 0 && !p.q_rlog.empty() && batch * p.n <= kDdqMaxElems) {
-        // few vectors: the shared-memory radix-4 passes, converting on the
-        // first pass's loads and the last pass's stores
+        // the shared-memory radix-4 passes, converting on the first pass's
+        // loads and the last pass's stores
         cdd* r = nullptr;
         nufft_status st = exec_ddq(p, reinterpret_cast<cdd*>(buf), reinterpret_cast<cdd*>(work), batch, dir, s, &r,
                                    cvt_in, cvt_out);

@@ -6,7 +6,8 @@
 // transformed there by radix-4 Stockham stages (one radix-2 stage when R is an
 // odd power of two), four elements per thread per stage.  With R up to 1024 a
 // 64K-point transform takes two passes instead of three radix-64 passes, and
-// twice as many threads share the work of each pass.
+// twice as many threads share the work of each pass.  Batches of many vectors
+// (the all-float64 path) gain from the saved pass as well.
 //
 // Pass layout (the same as the other power-of-two passes): for j < n/R the R
 // inputs x[j + k n/R] are twiddled by W_{Ns R}^{(j mod Ns) k}, transformed, and
