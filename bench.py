@@ -427,6 +427,21 @@ def run_gpu(args):
                            "value": 2 * B * args.steps / (ms_t / 1e3), "unit": "transforms/s",
                            "note": "not the headline: nufft_plan's default parameters are timed above"}
         L.nufft_cache_clear()
+
+        # ---- per-point roofline (what the method must move per point and
+        # right-hand side, solve-only: read s, w_p, K_q, the node geometry,
+        # write S: 40 B) and the arithmetic pipes' measured rates (the plan's
+        # float64 stages are bound by the float64 pipe, not by HBM)
+        bpp = 40.0
+        alg = {"bytes_per_point": bpp,
+               "plan_and_solve": {"GBps": bpp * N * value / 1e9, "frac": bpp * N * value / 1e9 / peak},
+               "solve_only": {"GBps": bpp * N * result["solve_only"]["value"] / 1e9,
+                              "frac": bpp * N * result["solve_only"]["value"] / 1e9 / peak},
+               "peak_GBps": peak}
+        result["alg_roofline"] = alg
+        result["pipes"] = {"fp32_fma_tflops": pkg.measure_fma(pkg.FP32), "fp64_fma_tflops": pkg.measure_fma(pkg.FP64),
+                           "how": "nufft_measure_fma: 8 independent FMA chains per thread, 8 CTAs of 256 per SM, "
+                                  "CUDA events around one launch after a warm-up launch"}
     time.sleep(0.3)
     clocks.stop()
     result["clocks"] = clocks.summary(t_wall0, t_wall1)

@@ -358,6 +358,17 @@ nufft_status nufft_profile_enable(int on);
 nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count);
 int64_t nufft_launch_count(void);
 
+/*
+ * Measurement utility (no counterpart in the paper): the device's sustained
+ * fused multiply-add rate in float32 (prec = NUFFT_FP32) or float64
+ * (NUFFT_FP64), from a kernel of independent FMA chains filling every SM,
+ * timed with CUDA events on `stream` after a warm-up launch.  Writes
+ * TFLOP/s (2 flops per FMA) to *tflops; synchronises the stream.  It is the
+ * denominator for kernels bound by arithmetic rather than memory (the plan's
+ * float64 stages).  NUFFT_ERR_ARG for a null pointer or another precision.
+ */
+nufft_status nufft_measure_fma(int prec, double* tflops, nufft_stream_t stream);
+
 const char* nufft_status_string(nufft_status st);
 const char* nufft_last_error_message(void);
 

@@ -111,6 +111,8 @@ def lib():
         L.nufft_profile_read.restype = i32
         L.nufft_launch_count.argtypes = []
         L.nufft_launch_count.restype = i64
+        L.nufft_measure_fma.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.nufft_measure_fma.restype = i32
         L.nufft_status_string.argtypes = [i32]
         L.nufft_status_string.restype = ctypes.c_char_p
         L.nufft_last_error_message.argtypes = []
@@ -150,6 +152,14 @@ def plan_tune(x, tol=None, prec=FP32, batch=8, stream=None):
     check(lib().nufft_plan_tune(x.numel(), _ptr(x), float(tol), int(prec), int(batch), _stream_handle(stream),
                                 ctypes.byref(q), ctypes.byref(ms)))
     return {"gamma": q.gamma, "eta": q.eta, "w_plan": q.w_plan, "w_solve": q.w_solve}, ms.value
+
+
+def measure_fma(prec=FP32, stream=None):
+    """Sustained fused multiply-add rate of the device in TFLOP/s, float32
+    (FP32) or float64 (FP64) (nufft_measure_fma; a measurement utility)."""
+    r = ctypes.c_double()
+    check(lib().nufft_measure_fma(prec, ctypes.byref(r), _stream_handle(stream)))
+    return r.value
 
 
 def stream_check(stream=None):

@@ -93,6 +93,60 @@ void LaunchGroup::close() {
     a_ = nullptr;
 }
 
+// independent FMA chains: kChains accumulators per thread, so the pipe,
+// not the dependency latency, sets the rate; the result is stored so the
+// chains stay live
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, T b, T c, T* __restrict__ out) {
+    T acc[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) acc[k] = fma(acc[k], b, c);
+        }
+    }
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) sum += acc[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+template <typename T>
+nufft_status measure_fma(double* tflops, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 8 * sms, threads = 256;
+    // enough work for a launch of a few milliseconds at either rate
+    const int iters = sizeof(T) == 4 ? 4096 : 64;
+    T* out = nullptr;
+    NUFFT_CUDA_TRY(cudaMallocAsync(&out, sizeof(T) * blocks * threads, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // b just below 1 and c tiny keep the chains finite
+    k_fma_rate<T><<<blocks, threads, 0, s>>>(iters, (T)0.999999, (T)1e-7, out);
+    cudaEventRecord(e0, s);
+    k_fma_rate<T><<<blocks, threads, 0, s>>>(iters, (T)0.999999, (T)1e-7, out);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fma rate", __FILE__, __LINE__);
+    g_launches.fetch_add(2, std::memory_order_relaxed);
+    const double fmas = (double)blocks * threads * iters * 8.0 * kChains;
+    *tflops = ms > 0.f ? 2.0 * fmas / ((double)ms * 1e-3) / 1e12 : 0.0;
+    return NUFFT_OK;
+}
+
 }  // namespace nufft45
 
 using namespace nufft45;
@@ -110,6 +164,14 @@ nufft_status nufft_profile_enable(int on) {
 }
 
 int64_t nufft_launch_count(void) { return (int64_t)g_launches.load(); }
+
+nufft_status nufft_measure_fma(int prec, double* tflops, nufft_stream_t stream) {
+    if (!tflops) return fail(NUFFT_ERR_ARG, "null result pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == NUFFT_FP32) return measure_fma<float>(tflops, s);
+    if (prec == NUFFT_FP64) return measure_fma<double>(tflops, s);
+    return fail(NUFFT_ERR_ARG, "precision %d is neither NUFFT_FP32 nor NUFFT_FP64", prec);
+}
 
 nufft_status nufft_profile_read(nufft_profile_entry_t* out, int cap, int* count) {
     if (!out || !count || cap < 0) return fail(NUFFT_ERR_ARG, "null argument");
