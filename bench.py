@@ -477,8 +477,10 @@ def run_batched(args):
         b.run(stream=s)
         s.synchronize()
         g = torch.cuda.CUDAGraph()
+        c0 = L.nufft_launch_count()
         with torch.cuda.graph(g, stream=s):
             b.run(stream=s)
+        per_replay = L.nufft_launch_count() - c0   # kernels the captured run launches
         for _ in range(args.warmup):
             g.replay()
         s.synchronize()
@@ -505,8 +507,8 @@ def run_batched(args):
                                "one persistent launch replayed from a CUDA graph" % (args.instances, n_pts),
                    "autotuned": {"ctas": ctas, "threads": threads, "max_fft_radix": radix, "tune_ms": tune_ms},
                    "l2": "512 MiB buffer written between timed steps (outside the events)"},
-        "gpu_launches": 0, "instances_flagged": int((st != 0).sum()),
-        "note": "graph replays launch kernels outside the library's launch counter",
+        "gpu_launches": int(per_replay) * args.steps, "instances_flagged": int((st != 0).sum()),
+        "note": "the launches the library counted while the graph was captured, times the replays",
     }
     print(json.dumps(result), flush=True)
     return 0

@@ -11,9 +11,13 @@
 // Stages are separated by block barriers; arrays live in a per-CTA scratch
 // slab.  Every FFT inside is a power of two: grids are rounded up to one, and
 // lengths N that are not use Bluestein's chirp-z on a power-of-two length, so
-// one table of W_{2^L} twiddles serves all instances.
+// one table of W_{2^L} twiddles serves all instances.  The plan's
+// float64-class arithmetic (its FFTs, spreading and interpolation) runs in
+// double-float (pairs of float32, ~2^-48) on the float32 pipes; float64 is
+// kept for the per-node phases, exponentials and the weights.
 #include "internal.h"
 #include "cis64.cuh"
+#include "df.cuh"
 #include "fft_p2.cuh"
 
 #include <algorithm>
@@ -51,7 +55,7 @@ struct Args {
     int* status;
     char* scratch;
     size_t scratch_per_cta;
-    const double2* tw64;     // W_{2^kMaxLog}^e
+    const cdd* twdd;         // W_{2^kMaxLog}^e in double-float
     const float2* tw32;
     const double* dec_plan;  // 1/phihat (plan width) per grid, centred index
     const float* dec_solve;  // 1/phihat (transforms' width)
@@ -66,9 +70,15 @@ template <typename X> __device__ __forceinline__ X* carve(char*& p, size_t count
     return r;
 }
 
-template <typename T> struct TwSel;
-template <> struct TwSel<double> { static __device__ const double2* get(const Args& a) { return a.tw64; } };
-template <> struct TwSel<float> { static __device__ const float2* get(const Args& a) { return a.tw32; } };
+// 2^(j/64) in double-float for the double-float kernel values
+__constant__ float2 c_exp2_64b[64] = NUFFT_EXP2_64_TABLE;
+
+__device__ __forceinline__ cdd to_cdd(double2 v) {
+    cdd r;
+    r.x = dd_from_double(v.x);
+    r.y = dd_from_double(v.y);
+    return r;
+}
 
 // block-wide power-of-two Stockham FFT of length 2^logn over global scratch,
 // radix 8/4/2 stages; dir -1 forward, +1 inverse, unnormalised.  Returns the
@@ -91,7 +101,7 @@ __device__ c2<T>* cta_fft(c2<T>* buf, c2<T>* work, int logn, int dir, const c2<T
                 c2<T> x = src[j + k * nr];
                 if (jm && k) {
                     // W_{Ns r}^{jm k} = W_{2^kMaxLog}^{jm k 2^(kMaxLog - log(Ns r))}
-                    c2<T> w = __ldg(&tw[(jm * k) << (kMaxLog - ns_log - rl)]);
+                    c2<T> w = ldg(&tw[(jm * k) << (kMaxLog - ns_log - rl)]);
                     if (dir > 0) w.y = -w.y;
                     x = cmul(x, w);
                 }
@@ -183,8 +193,10 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
     __shared__ int s_item;
     __shared__ int s_part[1024];
     __shared__ unsigned long long s_sum[32];
+    __shared__ float2 s_exp[64];
     char* const base = a.scratch + (size_t)blockIdx.x * a.scratch_per_cta;
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid < 64) s_exp[tid] = c_exp2_64b[tid];
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
@@ -210,17 +222,17 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         int* start = carve<int>(p, ns + 1);
         double2* modm = carve<double2>(p, N);
         double2* modp = carve<double2>(p, N);
-        double2* str = carve<double2>(p, (size_t)kEta * N);
-        double2* G = carve<double2>(p, (size_t)kEta * ns);
-        double2* GW = carve<double2>(p, (size_t)ns);
-        double2* v64 = carve<double2>(p, M);
-        double2* w64v = carve<double2>(p, M);
+        cdd* str = carve<cdd>(p, (size_t)kEta * N);    // log-kernel strengths (double-float)
+        cdd* G = carve<cdd>(p, (size_t)kEta * ns);
+        cdd* GW = carve<cdd>(p, (size_t)ns);
+        cdd* v64 = carve<cdd>(p, M);
+        cdd* w64v = carve<cdd>(p, M);
         double2* K64 = carve<double2>(p, N);
         double2* D64 = carve<double2>(p, N);
-        double2* chirp_d = carve<double2>(p, N);
-        double2* H_d = carve<double2>(p, M);
-        double2* A_d = carve<double2>(p, M);
-        double2* W_d = carve<double2>(p, M);
+        cdd* chirp_d = carve<cdd>(p, N);
+        cdd* H_d = carve<cdd>(p, M);
+        cdd* A_d = carve<cdd>(p, M);
+        cdd* W_d = carve<cdd>(p, M);
         float2* chirp_f = carve<float2>(p, N);
         float2* H_f = carve<float2>(p, M);
         float2* A_f = carve<float2>(p, M);
@@ -231,7 +243,9 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         float2* gw32 = carve<float2>(p, ns);
         float2* vec32 = carve<float2>(p, M);
         float2* vw32 = carve<float2>(p, M);
-        Blue<double> bd{chirp_d, H_d, A_d, W_d};
+        dd* fracd = carve<dd>(p, N);
+        float* fracf = carve<float>(p, N);
+        Blue<dd> bd{chirp_d, H_d, A_d, W_d};
         Blue<float> bf{chirp_f, H_f, A_f, W_f};
 
         // ---- nodes: exact turns, their sum mod 2^64, cells on the grid
@@ -254,12 +268,22 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             const uint64_t t = T[i];
             const int c = (int)__umul64hi(t, (uint64_t)ns);
             cell[i] = c;
-            frac[i] = (double)(t * (uint64_t)ns) * 5.42101086242752217003726400434970855712890625e-20;
+            const double fr = (double)(t * (uint64_t)ns) * 5.42101086242752217003726400434970855712890625e-20;
+            frac[i] = fr;
+            fracd[i] = dd_from_double(fr);
+            fracf[i] = (float)fr;
             atomicAdd(&cnt[c], 1);
-            modm[i] = cis_turns_t((uint64_t)K0 * t, -1);
-            modp[i] = cis_turns_t((uint64_t)K0 * t, +1);
-            for (int r = 0; r < kEta; ++r)
-                str[(int64_t)r * N + i] = cmul(cis_turns_t((uint64_t)N * (uint64_t)r * t, -1), modm[i]);
+            const double2 mm = cis_turns_t((uint64_t)K0 * t, -1);
+            modm[i] = mm;
+            modp[i] = make_double2(mm.x, -mm.y);
+            // strengths e^{-j 2 pi N r t} e^{-j 2 pi K0 t} as powers of
+            // beta = e^{-j 2 pi N t}, in double-float
+            cdd sv = to_cdd(mm);
+            const cdd bt = to_cdd(cis_turns_t((uint64_t)N * t, -1));
+            for (int r = 0; r < kEta; ++r) {
+                str[(int64_t)r * N + i] = sv;
+                sv = cmul(sv, bt);
+            }
         }
         __syncthreads();
         cta_scan(cnt, ns, start, s_part);
@@ -286,120 +310,137 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             if (N > 1 && T[perm[i + 1 < N ? i + 1 : 0]] - T[perm[i]] < (1ull << 20)) a.status[d.slot] = NUFFT_ERR_DUP_NODES;
         }
 
-        // ---- Bluestein chirps and filter spectra (float64, float32 copies)
+        // ---- Bluestein chirps and filter spectra (double-float, float32 copies)
         if (!d.pow2) {
             for (int64_t i = tid; i < M; i += nt) {
                 int64_t k = -1;
                 if (i < N) k = i; else if (i > M - N) k = M - i;
-                double2 c = make_double2(0.0, 0.0);
-                if (k >= 0) c = chirp64(k, N);
+                cdd c = mk<dd>(0, 0);
+                if (k >= 0) {
+                    const double2 cv = chirp64(k, N);
+                    c = to_cdd(cv);
+                    if (i < N) chirp_f[i] = make_float2((float)cv.x, (float)cv.y);
+                }
                 A_d[i] = c;
-                if (i < N) { chirp_d[i] = c; chirp_f[i] = make_float2((float)c.x, (float)c.y); }
+                if (i < N) chirp_d[i] = c;
             }
             __syncthreads();
-            double2* h = cta_fft<double>(A_d, W_d, d.log_m, -1, a.tw64, a.max_rl);
-            const double invM = 1.0 / (double)M;
+            cdd* h = cta_fft<dd>(A_d, W_d, d.log_m, -1, a.twdd, a.max_rl);
+            const float invM = 1.0f / (float)M;   // a power of two: exact
             for (int64_t i = tid; i < M; i += nt) {
-                const double2 v = make_double2(h[i].x * invM, h[i].y * invM);
+                cdd v;
+                v.x = dd_mul_f(h[i].x, invM);
+                v.y = dd_mul_f(h[i].y, invM);
                 H_d[i] = v;
-                H_f[i] = make_float2((float)v.x, (float)v.y);
+                H_f[i] = make_float2(v.x.hi, v.y.hi);
             }
             __syncthreads();
         }
 
-        // ---- log-kernel spectrum: eta type-1s of length N on the grid (float64)
-        const double tow_p = 2.0 / kWPlan;
+        // ---- log-kernel spectrum: eta type-1s of length N on the grid
+        // (double-float kernel values and sums)
+        const float hp = 0.5f * (float)kWPlan;
+        const dd beta_p(a.beta_plan);
         for (int g = tid; g < ns; g += nt) {
-            double2 acc[kEta];
-            for (int r = 0; r < kEta; ++r) acc[r] = make_double2(0.0, 0.0);
+            cdd acc[kEta];
+#pragma unroll
+            for (int r = 0; r < kEta; ++r) acc[r] = mk<dd>(0, 0);
             for (int j = 0; j < kWPlan; ++j) {
                 const int cu = g - kWPlan / 2 + j;                  // unwrapped cell
                 const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
                 for (int i = start[cw]; i < start[cw + 1]; ++i) {
                     const int q = perm[i];
-                    const double ph = es_kernel<double>((double)(g - cu) - frac[q], tow_p, a.beta_plan);
+                    const dd ph = es_kernel_dd(dd((float)(g - cu), 0.f) - fracd[q], hp, beta_p, s_exp);
+#pragma unroll
                     for (int r = 0; r < kEta; ++r) {
-                        const double2 sv = str[(int64_t)r * N + q];
-                        acc[r].x = fma(ph, sv.x, acc[r].x);
-                        acc[r].y = fma(ph, sv.y, acc[r].y);
+                        const cdd sv = str[(int64_t)r * N + q];
+                        acc[r].x += ph * sv.x;
+                        acc[r].y += ph * sv.y;
                     }
                 }
             }
+#pragma unroll
             for (int r = 0; r < kEta; ++r) G[(int64_t)r * ns + g] = acc[r];
         }
         __syncthreads();
         for (int r = 0; r < kEta; ++r) {
-            double2* res = cta_fft<double>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.tw64, a.max_rl);
+            cdd* res = cta_fft<dd>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.twdd, a.max_rl);
             if (res != G + (int64_t)r * ns)
                 for (int g = tid; g < ns; g += nt) G[(int64_t)r * ns + g] = res[g];
             __syncthreads();
         }
-        // fold (Eq. 7) with Lambda_k = -rho^k / k (Eq. 41) and the deconvolution
+        // fold (Eq. 7) with Lambda_k = -rho^k / k (Eq. 41) and the deconvolution;
+        // rho^{N r + m} = gamma^{-r} rho^m
         for (int64_t m = tid; m < N; m += nt) {
             const int64_t kc = m - K0;
             const int64_t src = kc < 0 ? kc + ns : kc;
             const double dec = dec_p[kc + ns / 2];
-            double2 acc = make_double2(0.0, 0.0);
-            for (int r = 0; r < kEta; ++r) {
+            const double rm = exp((double)m * log_rho);
+            cdd acc = mk<dd>(0, 0);
+            double gr = 1.0;
+            for (int r = 0; r < kEta; ++r, gr *= rhoN) {
                 const int64_t k = N * r + m;
                 if (k == 0) continue;
-                const double lam = -exp((double)k * log_rho) / (double)k * dec;
-                const double2 b = G[(int64_t)r * ns + src];
-                acc.x = fma(lam, b.x, acc.x);
-                acc.y = fma(lam, b.y, acc.y);
+                const dd lam = dd_from_double(-gr * rm / (double)k * dec);
+                const cdd b = G[(int64_t)r * ns + src];
+                acc.x += lam * b.x;
+                acc.y += lam * b.y;
             }
             v64[m] = acc;
         }
         __syncthreads();
-        cta_dft<double>(v64, w64v, d, +1, bd, a.tw64, a.max_rl);
+        cta_dft<dd>(v64, w64v, d, +1, bd, a.twdd, a.max_rl);
         // K_q (Eq. 29), then F = DFT(K) for Eq. 43
         const uint64_t Cph = (uint64_t)sumT + (uint64_t)N * 0x8000000000000000ull;
         for (int64_t q = tid; q < N; q += nt) {
-            const double2 vq = v64[q];
+            const cdd vq = v64[q];
             double s, c;
-            sincospi(vq.y / 3.141592653589793238462643383279502884 + 2.0 * turns_of(Cph), &s, &c);
-            const double mag = exp(vq.x);
+            sincospi(dd_to_double(vq.y) / 3.141592653589793238462643383279502884 + 2.0 * turns_of(Cph), &s, &c);
+            const double mag = exp(dd_to_double(vq.x));
             const double2 k = make_double2(mag * c, mag * s);
             K64[q] = k;
             K32[q] = make_float2((float)k.x, (float)k.y);
-            v64[q] = k;
+            v64[q] = to_cdd(k);
         }
         __syncthreads();
-        cta_dft<double>(v64, w64v, d, -1, bd, a.tw64, a.max_rl);
+        cta_dft<dd>(v64, w64v, d, -1, bd, a.twdd, a.max_rl);
         // d_m = (m+1) L_{m+1}, L_k = F_k rho^-k / N (k >= 1), L_N = 1; placed on
         // the grid with the plan's deconvolution (type-2, Eq. 16)
         for (int g = tid; g < ns; g += nt) {
             const int64_t kc = g < ns - K0 ? g : g - ns;
             const int64_t m = kc + K0;
-            double2 v = make_double2(0.0, 0.0);
+            cdd v = mk<dd>(0, 0);
             if (m >= 0 && m < N) {
                 const int64_t k = m + 1;
-                double2 L = make_double2(1.0, 0.0);
+                double f = (double)k * dec_p[kc + ns / 2];
                 if (k < N) {
-                    const double sc = exp(-(double)k * log_rho) / (double)N;
-                    L = make_double2(v64[k].x * sc, v64[k].y * sc);
+                    f *= exp(-(double)k * log_rho) / (double)N;
+                    const dd fd = dd_from_double(f);
+                    v.x = fd * v64[k].x;
+                    v.y = fd * v64[k].y;
+                } else {
+                    v.x = dd_from_double(f);
                 }
-                const double f = (double)k * dec_p[kc + ns / 2];
-                v = make_double2(L.x * f, L.y * f);
             }
             G[g] = v;
         }
         __syncthreads();
         {
-            double2* gsp = cta_fft<double>(G, GW, d.log_ns, +1, a.tw64, a.max_rl);
-            // L'(z_p) by interpolation; then w_p (Eqs. 27, 40)
+            cdd* gsp = cta_fft<dd>(G, GW, d.log_ns, +1, a.twdd, a.max_rl);
+            // L'(z_p) by interpolation (double-float); then w_p (Eqs. 27, 40)
             for (int64_t i = tid; i < N; i += nt) {
                 const int c = cell[i];
-                const double f = frac[i];
-                double2 acc = make_double2(0.0, 0.0);
+                const dd fdd = fracd[i];
+                cdd acc = mk<dd>(0, 0);
                 for (int m = 0; m < kWPlan; ++m) {
                     int gi = c + 1 - kWPlan / 2 + m;
                     gi = gi < 0 ? gi + ns : (gi >= ns ? gi - ns : gi);
-                    const double ph = es_kernel<double>((double)(m + 1 - kWPlan / 2) - f, tow_p, a.beta_plan);
-                    acc.x = fma(ph, gsp[gi].x, acc.x);
-                    acc.y = fma(ph, gsp[gi].y, acc.y);
+                    const dd ph = es_kernel_dd(dd((float)(m + 1 - kWPlan / 2), 0.f) - fdd, hp, beta_p, s_exp);
+                    const cdd gv = gsp[gi];
+                    acc.x += ph * gv.x;
+                    acc.y += ph * gv.y;
                 }
-                const double2 Dp = cmul(acc, modp[i]);
+                const double2 Dp = cmul(make_double2(dd_to_double(acc.x), dd_to_double(acc.y)), modp[i]);
                 D64[i] = Dp;
                 const uint64_t t = T[i];
                 const double2 e = cis_turns_t((uint64_t)N * t, -1);
@@ -426,7 +467,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                     const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
                     for (int i = start[cw]; i < start[cw + 1]; ++i) {
                         const int q = perm[i];
-                        const float ph = es_kernel<float>((float)(g - cu) - (float)frac[q], tow_s, beta_s);
+                        const float ph = es_kernel<float>((float)(g - cu) - fracf[q], tow_s, beta_s);
                         const float2 sv = cmul(d.in[q], wm32[q]);
                         acc.x = fmaf(ph, sv.x, acc.x);
                         acc.y = fmaf(ph, sv.y, acc.y);
@@ -468,7 +509,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             float2* gsp = cta_fft<float>(g32, gw32, d.log_ns, +1, a.tw32, a.max_rl);
             for (int64_t i = tid; i < N; i += nt) {
                 const int c = cell[i];
-                const float f = (float)frac[i];
+                const float f = fracf[i];
                 float2 acc = make_float2(0.f, 0.f);
                 for (int m = 0; m < kWSolve; ++m) {
                     int gi = c + 1 - kWSolve / 2 + m;
@@ -484,12 +525,12 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
     }
 }
 
-__global__ void k_twiddle_table(int logn, double2* t64, float2* t32) {
+__global__ void k_twiddle_table(int logn, cdd* tdd, float2* t32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (1 << logn)) return;
     double s, c;
     sincospi(-2.0 * (double)i / (double)(1 << logn), &s, &c);
-    t64[i] = make_double2(c, s);
+    tdd[i] = to_cdd(make_double2(c, s));
     t32[i] = make_float2((float)c, (float)s);
 }
 
@@ -501,6 +542,7 @@ size_t scratch_bytes(int64_t N, int log_ns, int log_m) {
     s += 2 * al(16 * N) + al(16 * kEta * N) + al(16 * kEta * ns) + al(16 * ns);
     s += 2 * al(16 * M) + 2 * al(16 * N) + al(16 * N) + 3 * al(16 * M);
     s += al(8 * N) + 3 * al(8 * M) + 2 * al(8 * N) + 2 * al(8 * ns) + 2 * al(8 * M);
+    s += al(8 * N) + al(4 * N);   // node fractions in double-float and float32
     return s;
 }
 
@@ -522,7 +564,7 @@ struct nufft_batch_s {
     int* status = nullptr;
     char* scratch = nullptr;
     size_t scratch_per_cta = 0;
-    double2* tw64 = nullptr;
+    cdd* twdd = nullptr;
     float2* tw32 = nullptr;
     double* dec_plan = nullptr;
     float* dec_solve = nullptr;
@@ -611,7 +653,7 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     if ((e = cudaMalloc(&b->counter, sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->status, sizeof(int) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->scratch, b->scratch_per_cta * b->scratch_cap)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
-    if ((e = cudaMalloc(&b->tw64, sizeof(double2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->twdd, sizeof(cdd) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->tw32, sizeof(float2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->dec_plan, sizeof(double) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->dec_solve, sizeof(float) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
@@ -619,7 +661,7 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
         return cleanup(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
     {
         Launch L(s, K_PLAN_TABLE, 24.0 * (1 << kMaxLog));
-        k_twiddle_table<<<(1 << kMaxLog) / 256, 256, 0, s>>>(kMaxLog, b->tw64, b->tw32);
+        k_twiddle_table<<<(1 << kMaxLog) / 256, 256, 0, s>>>(kMaxLog, b->twdd, b->tw32);
     }
     // deconvolution tables per grid, indexed by the centred index k' + ns/2
     GLRule glp, gls;
@@ -650,7 +692,7 @@ nufft_status nufft_batch_run(nufft_batch_t b, nufft_stream_t stream) {
     a.status = b->status;
     a.scratch = b->scratch;
     a.scratch_per_cta = b->scratch_per_cta;
-    a.tw64 = b->tw64;
+    a.twdd = b->twdd;
     a.tw32 = b->tw32;
     a.dec_plan = b->dec_plan;
     a.dec_solve = b->dec_solve;
@@ -729,7 +771,7 @@ nufft_status nufft_batch_destroy(nufft_batch_t b) {
     cudaFree(b->counter);
     cudaFree(b->status);
     cudaFree(b->scratch);
-    cudaFree(b->tw64);
+    cudaFree(b->twdd);
     cudaFree(b->tw32);
     cudaFree(b->dec_plan);
     cudaFree(b->dec_solve);
