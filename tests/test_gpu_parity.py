@@ -267,6 +267,10 @@ def test_n65536_known_truth(prec):
     Sb = _np(plan.inv5(_dev(fb, prec)))
     for b, sc in enumerate([1, 1j, -1, 0.5]):
         assert oracle.rel_l2(Sb[b], sc * c) <= TOL_INV[prec]
+    Ab = np.stack([A, -1j * A, 2 * A])
+    ab = _np(plan.inv4(_dev(Ab, prec)))
+    for b, sc in enumerate([1, -1j, 2]):
+        assert oracle.rel_l2(ab[b], sc * c) <= TOL_INV[prec]
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
