@@ -273,6 +273,28 @@ def test_n65536_known_truth(prec):
         assert oracle.rel_l2(ab[b], sc * c) <= TOL_INV[prec]
 
 
+def test_n131072_known_truth_float32():
+    """N = 131072: the scattering-store path without the fused pair (radix
+    512 x 256 length-N passes) and the type-4 grid FFT that reads only the
+    placed half of its 2^18-point grid; full-vector comparison with known
+    truth from exact-phase direct sums."""
+    N = 131072
+    g = synth.rng(5)
+    x = synth.jittered_nodes(N, 0.45, generator=g)
+    c = synth.cn01(N, generator=g)
+    f = oracle.type2(x, c)
+    A = oracle.type1(x, c)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=FP32)
+    fb = np.stack([f, -1j * f])
+    Ab = np.stack([A, 2 * A])
+    Sb = _np(plan.inv5(_dev(fb, FP32)))
+    ab = _np(plan.inv4(_dev(Ab, FP32)))
+    for b, sc in enumerate([1, -1j]):
+        assert oracle.rel_l2(Sb[b], sc * c) <= TOL_INV[FP32]
+    for b, sc in enumerate([1, 2]):
+        assert oracle.rel_l2(ab[b], sc * c) <= TOL_INV[FP32]
+
+
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_refinement_on_clustered_nodes(prec):
     """Sec. V refinement on an ill-conditioned node set (1% of the nodes within
