@@ -80,6 +80,34 @@ __device__ __forceinline__ cdd to_cdd(double2 v) {
     return r;
 }
 
+// one radix-R stage of a block-wide Stockham FFT (R a compile-time constant so
+// the R values of a butterfly stay in registers)
+template <typename T, int R>
+__device__ __forceinline__ void cta_fft_stage(const c2<T>* src, c2<T>* dst, int n, int ns_log, int dir,
+                                              const c2<T>* __restrict__ tw) {
+    constexpr int rl = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int nr = n >> rl;
+    for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        c2<T> v[R];
+        const int jm = j & ((1 << ns_log) - 1);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            c2<T> x = src[j + k * nr];
+            if (jm && k) {
+                // W_{Ns R}^{jm k} = W_{2^kMaxLog}^{jm k 2^(kMaxLog - log(Ns R))}
+                c2<T> w = ldg(&tw[(jm * k) << (kMaxLog - ns_log - rl)]);
+                if (dir > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[k] = x;
+        }
+        p2::dft_reg<R, T>(v, dir);
+        c2<T>* d = dst + ((j >> ns_log) << (ns_log + rl)) + jm;
+#pragma unroll
+        for (int m = 0; m < R; ++m) d[m << ns_log] = v[m];
+    }
+}
+
 // block-wide power-of-two Stockham FFT of length 2^logn over global scratch,
 // radix 8/4/2 stages; dir -1 forward, +1 inverse, unnormalised.  Returns the
 // buffer that holds the result.
@@ -92,27 +120,9 @@ __device__ c2<T>* cta_fft(c2<T>* buf, c2<T>* work, int logn, int dir, const c2<T
     while (ns_log < logn) {
         const int rem = logn - ns_log;
         const int rl = rem >= max_rl ? max_rl : rem;
-        const int r = 1 << rl;
-        const int nr = n >> rl;
-        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
-            c2<T> v[8];
-            const int jm = j & ((1 << ns_log) - 1);
-            for (int k = 0; k < r; ++k) {
-                c2<T> x = src[j + k * nr];
-                if (jm && k) {
-                    // W_{Ns r}^{jm k} = W_{2^kMaxLog}^{jm k 2^(kMaxLog - log(Ns r))}
-                    c2<T> w = ldg(&tw[(jm * k) << (kMaxLog - ns_log - rl)]);
-                    if (dir > 0) w.y = -w.y;
-                    x = cmul(x, w);
-                }
-                v[k] = x;
-            }
-            if (r == 8) p2::dft_reg<8, T>(v, dir);
-            else if (r == 4) p2::dft_reg<4, T>(v, dir);
-            else p2::dft_reg<2, T>(v, dir);
-            c2<T>* d = dst + ((j >> ns_log) << (ns_log + rl)) + jm;
-            for (int m = 0; m < r; ++m) d[m << ns_log] = v[m];
-        }
+        if (rl == 3) cta_fft_stage<T, 8>(src, dst, n, ns_log, dir, tw);
+        else if (rl == 2) cta_fft_stage<T, 4>(src, dst, n, ns_log, dir, tw);
+        else cta_fft_stage<T, 2>(src, dst, n, ns_log, dir, tw);
         __syncthreads();
         c2<T>* t = src; src = dst; dst = t;
         ns_log += rl;
