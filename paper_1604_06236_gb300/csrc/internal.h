@@ -222,6 +222,10 @@ void launch_spread_plan_dd(const Geometry& g, KernelShape ks, const void* sx, in
                            int64_t batch, cudaStream_t s, void* ktab);
 void launch_interp_plan_dd(const Geometry& g, KernelShape ks, const void* grid, const void* ktab, const double2* wt,
                            double2* dst, cudaStream_t s);
+// float64 type-2 interpolation from a complex double-float grid (batch stride
+// n): taps summed in double-float, dst[b dst_bs + perm[i]] = sum * wt_srt[i]
+void launch_interp_dd(const Geometry& g, KernelShape ks, const void* grid, const double2* wt_srt, double2* dst,
+                      int64_t dst_bs, int64_t batch, cudaStream_t s);
 
 // out[b][k] = in[b][(k - K0) mod n] * fac[k], k < P
 template <typename T>

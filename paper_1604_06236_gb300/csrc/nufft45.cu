@@ -584,6 +584,25 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
         launch_pointwise<T>(r1, P, r1, P, P, K, nullptr, bc, s);
         return fft(false, r1, r1 == vA ? vW : vA, -1, res);
     };
+    // grid (already placed) -> type-2 at the nodes times wt_srt: the float64
+    // path keeps the FFT's result in double-float and interpolates in it
+    auto grid_to_nodes = [&](const void* wt_srt) -> nufft_status {
+        if constexpr (sizeof(T) == 8) {
+            double2* rd = nullptr;
+            nufft_status e = traced_fft(s, true, fft_exec_dd, tab.fft_ns64, reinterpret_cast<double2*>(gA),
+                                        reinterpret_cast<double2*>(gW), bc, +1, s, &rd, kDdOut);
+            if (e != NUFFT_OK) return e;
+            launch_interp_dd(pl->gs, prm.ks_solve, rd, (const double2*)wt_srt, reinterpret_cast<double2*>(out), N,
+                             bc, s);
+            return NUFFT_OK;
+        } else {
+            c2<T>* rr = nullptr;
+            nufft_status e = fft(true, gA, gW, +1, &rr);
+            if (e != NUFFT_OK) return e;
+            launch_interp<T>(pl->gs, prm.ks_solve, rr, (const c2<T>*)wt_srt, out, N, bc, s);
+            return NUFFT_OK;
+        }
+    };
     const bool fused = sizeof(T) == 4 && fft_hooks_supported<T>(tab.fft_P);
     // selection and placement as scattering stores of the FFT passes
     const bool scatter = fft_scatter_supported<T>(tab.fft_ns) && fft_scatter_supported<T>(tab.fft_P);
@@ -733,8 +752,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
             launch_pointwise<T>(in, N, vA, P, P, nullptr, rpos, bc, s);
             if ((st = middle(&r)) != NUFFT_OK) return st;
             launch_place<T>(r, P, P, prm.K0s, fac4, gA, ns, bc, s);
-            if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
-            launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt4_srt, out, N, bc, s);
+            if ((st = grid_to_nodes(pl->wt4_srt)) != NUFFT_OK) return st;
             break;
         }
         case OP_FWD1: {
@@ -746,8 +764,7 @@ nufft_status run_chunk(const nufft_plan_s* pl, Op op, const c2<T>* in, c2<T>* ou
         case OP_FWD2:
         case OP_FWD2D: {
             launch_place<T>(in, N, P, prm.K0s, fac1, gA, ns, bc, s, op == OP_FWD2D);
-            if ((st = fft(true, gA, gW, +1, &r)) != NUFFT_OK) return st;
-            launch_interp<T>(pl->gs, prm.ks_solve, r, (const c2<T>*)pl->wt2_srt, out, N, bc, s);
+            if ((st = grid_to_nodes(pl->wt2_srt)) != NUFFT_OK) return st;
             break;
         }
     }

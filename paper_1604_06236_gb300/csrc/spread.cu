@@ -400,6 +400,58 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
     }
 }
 
+// The all-float64 path's type-2 interpolation in double-float: the grid comes
+// in complex double-float (the FFT leaves it so), the kernel values are formed
+// in double-float per node (as in k_interp's float64 case) and the taps are
+// summed in double-float on the float32 pipes; one conversion per output, then
+// the float64 weight (wt, by sorted slot) and the store at dst[b dst_bs + perm[i]].
+template <int BC>
+__global__ void __launch_bounds__(kTB) k_interp_dd(int64_t N, int64_t n, int w, dd beta,
+                                                   const int* __restrict__ sperm, const int* __restrict__ scell,
+                                                   const double* __restrict__ sfrac, const cdd* __restrict__ grid,
+                                                   const double2* __restrict__ wt, double2* __restrict__ dst,
+                                                   int64_t dst_bs, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float2 s_exp[64];
+    if (threadIdx.x < 64) s_exp[threadIdx.x] = c_exp2_64[threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t b0 = (int64_t)blockIdx.y * BC;
+    const int h = w / 2;
+    const dd fr = dd_from_double(sfrac[i]);
+    dd ker[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+        ker[m] = (m < w) ? es_kernel_dd(dd((float)(m + 1 - h), 0.f) - fr, 0.5f * (float)w, beta, s_exp) : dd(0.f, 0.f);
+    cdd acc[BC];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) { acc[b].x = dd(0.f, 0.f); acc[b].y = dd(0.f, 0.f); }
+    int64_t gi = scell[i] + 1 - h;
+    if (gi < 0) gi += n;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (m < w) {
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                if (b0 + b < batch) {
+                    const cdd v = grid[(b0 + b) * n + gi];
+                    acc[b].x += ker[m] * v.x;
+                    acc[b].y += ker[m] * v.y;
+                }
+            }
+            if (++gi == n) gi = 0;
+        }
+    }
+    const int p = sperm[i];
+    const double2 wv = wt[i];
+#pragma unroll
+    for (int b = 0; b < BC; ++b)
+        if (b0 + b < batch)
+            dst[(b0 + b) * dst_bs + p] = cmul(make_double2(dd_to_double(acc[b].x), dd_to_double(acc[b].y)), wv);
+}
+
 // The plan's type-2 for L'(z_p) in double-float: the grid (complex
 // double-float) and the kernel values the plan's spread stored (double-float,
 // by sorted slot and tap) are combined on the float32 pipes; the sum is
@@ -751,6 +803,20 @@ void launch_spread_plan_dd(const Geometry& g, KernelShape ks, const void* sx, in
              g.ext_perm, g.ext_cell, (const double*)g.ext_frac, (const double2*)nullptr, (int64_t)0,
              (const double2*)nullptr, static_cast<double2*>(grid), batch, static_cast<double*>(ktab),
              g.cstart + g.w / 2, g.N, static_cast<const cdd*>(sx), sx_bs);
+}
+
+void launch_interp_dd(const Geometry& g, KernelShape ks, const void* grid, const double2* wt_srt, double2* dst,
+                      int64_t dst_bs, int64_t batch, cudaStream_t s) {
+    Launch L(s, K_INTERP, batch * g.n * 16.0 + g.N * (8.0 + 8.0 + 16.0) + batch * g.N * 16.0, true);
+    const dd beta_dd(ks.beta);
+    const cdd* gd = static_cast<const cdd*>(grid);
+    if (batch <= 2) {
+        launch_k(k_interp_dd<2>, dim3(nblk(g.N), (unsigned)((batch + 1) / 2)), kTB, 0, s, g.N, g.n, ks.w, beta_dd,
+                 g.srt_perm, g.srt_cell, (const double*)g.srt_frac, gd, wt_srt, dst, dst_bs, batch);
+    } else {
+        launch_k(k_interp_dd<8>, dim3(nblk(g.N), (unsigned)((batch + 7) / 8)), kTB, 0, s, g.N, g.n, ks.w, beta_dd,
+                 g.srt_perm, g.srt_cell, (const double*)g.srt_frac, gd, wt_srt, dst, dst_bs, batch);
+    }
 }
 
 void launch_interp_plan_dd(const Geometry& g, KernelShape ks, const void* grid, const void* ktab, const double2* wt,
