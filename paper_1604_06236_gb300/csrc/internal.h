@@ -203,15 +203,12 @@ nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N
                             bool want_float, int* scratch_int, unsigned long long* sumT, cudaStream_t s);
 int64_t geometry_scratch_ints(int64_t N, int64_t n);
 
-// ktab (optional, N * ks.w values): the spread also stores every kernel value
-// it evaluates, by sorted slot and tap, and an interpolation on the same
-// geometry and kernel reads them instead of evaluating the kernel again
 template <typename T>
 void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs,
-                   const c2<T>* wt_ext, c2<T>* grid, int64_t batch, cudaStream_t s, T* ktab = nullptr);
+                   const c2<T>* wt_ext, c2<T>* grid, int64_t batch, cudaStream_t s);
 template <typename T>
 void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt,
-                   c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s, const T* ktab = nullptr);
+                   c2<T>* dst, int64_t dst_bs, int64_t batch, cudaStream_t s);
 // The plan's pair in double-float ("complex double-float": 16 bytes per
 // value, real hi, real lo, imaginary hi, imaginary lo): the spread takes
 // weighted strengths per extended slot (sx[b sx_bs + slot], batch <= 4 per

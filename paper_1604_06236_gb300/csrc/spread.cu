@@ -230,17 +230,14 @@ template <> struct FracPtr<double> { static const double* ext(const Geometry& g)
 
 constexpr int kChunk = 256;
 
-// ktab (optional): every kernel value the gather evaluates is also stored at
-// ktab[s w + m], s the node's sorted slot and m its tap (grid point
-// cell + 1 - w/2 + m), for the interpolation on the same geometry and kernel;
-// pre_at points at the count of prepended halo slots, N is the node count.
+// output-stationary gather: grid point g sums the extended nodes of the
+// cells within w/2 of it, BC right-hand sides per block row
 template <typename T, int BC>
 __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, T beta, const int* __restrict__ cstart,
                                                 const int* __restrict__ eperm, const int* __restrict__ ecell,
                                                 const T* __restrict__ efrac, const c2<T>* __restrict__ src,
                                                 int64_t src_bs, const c2<T>* __restrict__ wt, c2<T>* __restrict__ grid,
-                                                int64_t batch, T* __restrict__ ktab, const int* __restrict__ pre_at,
-                                                int64_t N) {
+                                                int64_t batch) {
     pdl_wait();
     pdl_trigger();
     __shared__ int s_cell[kChunk];
@@ -276,16 +273,10 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
         }
         __syncthreads();
         const int a = max(lo, ch), z = min(hi, ch + cnt);
-        const bool keep = ktab != nullptr && blockIdx.y == 0;
-        const int pre = keep ? *pre_at : 0;
         for (int i = a; i < z; ++i) {
             const int e = i - ch;
             const T d = (T)(int)(g - s_cell[e]) - s_frac[e];   // small offset: a 32-bit integer conversion
             const T ph = es_kernel<T>(d, two_over_w, beta);
-            if (keep) {
-                const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
-                ktab[slot * w + (g - s_cell[e]) + w / 2 - 1] = ph;
-            }
 #pragma unroll
             for (int b = 0; b < BC; ++b) {
                 acc[b].x = fma(ph, s_str[b][e].x, acc[b].x);
@@ -300,7 +291,6 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
     }
 }
 
-// ktab (optional): the kernel values k_spread stored for this geometry and kernel
 __constant__ float2 c_exp2_64[64] = NUFFT_EXP2_64_TABLE;
 
 // The float64 spread with the kernel values and the accumulation in
@@ -310,8 +300,11 @@ __constant__ float2 c_exp2_64[64] = NUFFT_EXP2_64_TABLE;
 // are converted once per staged node, the outputs once per grid point.
 // DDIO (the plan's log-kernel type-1): the strengths come per extended slot,
 // already weighted and in double-float (sx[b sx_bs + slot], complex
-// double-float), the grid is written in double-float and so are the stored
-// kernel values, so no value crosses the float64 pipe.
+// double-float), the grid is written in double-float, and every kernel value
+// is also stored, in double-float, at ktab[s w + m] (s the node's sorted slot,
+// m its tap: grid point cell + 1 - w/2 + m; pre_at points at the count of
+// prepended halo slots) for the plan's interpolation on the same geometry and
+// kernel, so no value crosses the float64 pipe.
 template <int BC, bool DDIO>
 __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
                                                    const int* __restrict__ cstart, const int* __restrict__ eperm,
@@ -370,7 +363,7 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
         }
         __syncthreads();
         const int a = max(lo, ch), z = min(hi, ch + cnt);
-        const bool keep = ktab != nullptr && blockIdx.y == 0;
+        const bool keep = DDIO && blockIdx.y == 0;
         const int pre = keep ? *pre_at : 0;
         for (int i = a; i < z; ++i) {
             const int e = i - ch;
@@ -378,9 +371,7 @@ __global__ void __launch_bounds__(kTB) k_spread_dd(int64_t n, int w, dd beta,
             const dd ph = es_kernel_dd(d, 0.5f * (float)w, beta, s_exp);
             if (keep) {
                 const int64_t slot = i < pre ? N - pre + i : (i < pre + N ? i - pre : i - pre - N);
-                const int64_t k = slot * w + (g - s_cell[e]) + w / 2 - 1;
-                if constexpr (DDIO) reinterpret_cast<dd*>(ktab)[k] = ph;
-                else ktab[k] = dd_to_double(ph);
+                reinterpret_cast<dd*>(ktab)[slot * w + (g - s_cell[e]) + w / 2 - 1] = ph;
             }
 #pragma unroll
             for (int b = 0; b < BC; ++b) {
@@ -487,7 +478,7 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
                                                 const int* __restrict__ sperm, const int* __restrict__ scell,
                                                 const T* __restrict__ sfrac, const c2<T>* __restrict__ grid,
                                                 const c2<T>* __restrict__ wt, c2<T>* __restrict__ dst, int64_t dst_bs,
-                                                int64_t batch, const T* __restrict__ ktab) {
+                                                int64_t batch) {
     pdl_wait();
     pdl_trigger();
     __shared__ float2 s_exp[64];   // float64 data: double-float exponential table
@@ -502,10 +493,7 @@ __global__ void __launch_bounds__(kTB) k_interp(int64_t N, int64_t n, int w, T t
     const T f = sfrac[i];
     const int h = w / 2;
     T ker[16];
-    if (ktab) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? ktab[i * w + m] : (T)0;
-    } else if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
         // kernel values in double-float on the float32 pipes (see k_spread_dd)
         const dd fr = dd_from_double((double)f);
         const dd beta_dd((double)beta);
@@ -723,7 +711,7 @@ nufft_status build_geometry(Geometry& g, const double* x, uint64_t* T, int64_t N
 
 template <typename T>
 void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t src_bs, const c2<T>* wt_ext,
-                   c2<T>* grid, int64_t batch, cudaStream_t s, T* ktab) {
+                   c2<T>* grid, int64_t batch, cudaStream_t s) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* ef = FracPtr<T>::ext(g);
     // the extended list may carry a wider halo (g.w >= ks.w): cell starts are
@@ -738,14 +726,13 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
         const double2* sd = reinterpret_cast<const double2*>(src);
         const double2* wd = reinterpret_cast<const double2*>(wt_ext);
         double2* gd = reinterpret_cast<double2*>(grid);
-        double* kd = reinterpret_cast<double*>(ktab);
         if (batch == 1) {
             launch_k(k_spread_dd<1, false>, dim3(nblk(g.n), 1), kTB, 0, s, g.n, ks.w, beta_dd, cs, g.ext_perm,
-                     g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2, g.N, (const cdd*)nullptr,
+                     g.ext_cell, efd, sd, src_bs, wd, gd, batch, (double*)nullptr, g.cstart + g.w / 2, g.N, (const cdd*)nullptr,
                      (int64_t)0);
         } else {
             launch_k(k_spread_dd<4, false>, dim3(nblk(g.n), (unsigned)((batch + 3) / 4)), kTB, 0, s, g.n, ks.w,
-                     beta_dd, cs, g.ext_perm, g.ext_cell, efd, sd, src_bs, wd, gd, batch, kd, g.cstart + g.w / 2,
+                     beta_dd, cs, g.ext_perm, g.ext_cell, efd, sd, src_bs, wd, gd, batch, (double*)nullptr, g.cstart + g.w / 2,
                      g.N, (const cdd*)nullptr, (int64_t)0);
         }
         return;
@@ -753,26 +740,26 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
     if (batch == 1) {
         dim3 gr(nblk(g.n), 1);
         launch_k(k_spread<T, 1>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
+                                          wt_ext, grid, batch);
     } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 3) / 4));
         launch_k(k_spread<T, 4>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
+                                          wt_ext, grid, batch);
     } else if (batch <= 8) {
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
         launch_k(k_spread<T, 8>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
+                                          wt_ext, grid, batch);
     } else {
         // 16 right-hand sides per block row: each kernel value serves twice as many
         dim3 gr(nblk(g.n), (unsigned)((batch + 15) / 16));
         launch_k(k_spread<T, 16>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
-                                          wt_ext, grid, batch, ktab, g.cstart + g.w / 2, g.N);
+                                          wt_ext, grid, batch);
     }
 }
 
 template <typename T>
 void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c2<T>* wt_srt, c2<T>* dst,
-                   int64_t dst_bs, int64_t batch, cudaStream_t s, const T* ktab) {
+                   int64_t dst_bs, int64_t batch, cudaStream_t s) {
     const T tow = (T)(2.0 / ks.w), beta = (T)ks.beta;
     const T* sf = FracPtr<T>::srt(g);
     const double es = sizeof(c2<T>);
@@ -780,16 +767,16 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
     if (batch == 1) {
         dim3 gr(nblk(g.N), 1);
         launch_k(k_interp<T, 1>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch, ktab);
+                                          dst_bs, batch);
     } else if (batch <= 4 || sizeof(T) == 8) {
         dim3 gr(nblk(g.N), (unsigned)((batch + 3) / 4));
         launch_k(k_interp<T, 4>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch, ktab);
+                                          dst_bs, batch);
     } else {
         // 8 right-hand sides per block row: each kernel value serves twice as many
         dim3 gr(nblk(g.N), (unsigned)((batch + 7) / 8));
         launch_k(k_interp<T, 8>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch, ktab);
+                                          dst_bs, batch);
     }
 }
 
@@ -857,9 +844,9 @@ void launch_pointwise(const c2<T>* in, int64_t in_bs, c2<T>* out, int64_t out_bs
 
 #define INST(T)                                                                                                  \
     template void launch_spread<T>(const Geometry&, KernelShape, const c2<T>*, int64_t, const c2<T>*, c2<T>*,   \
-                                   int64_t, cudaStream_t, T*);                                                   \
+                                   int64_t, cudaStream_t);                                                       \
     template void launch_interp<T>(const Geometry&, KernelShape, const c2<T>*, const c2<T>*, c2<T>*, int64_t,   \
-                                   int64_t, cudaStream_t, const T*);                                             \
+                                   int64_t, cudaStream_t);                                                       \
     template void launch_select<T>(const c2<T>*, int64_t, c2<T>*, int64_t, int64_t, int64_t, const T*, int64_t, \
                                    cudaStream_t);                                                                \
     template void launch_place<T>(const c2<T>*, int64_t, int64_t, int64_t, const T*, c2<T>*, int64_t, int64_t,  \
