@@ -284,10 +284,12 @@ void launch_conv_fold(const c2<T>* c, int64_t n, int64_t P, double rhoP, c2<T>* 
 // w_p (Eqs. 27, 40) into w64 (node order) and the solve-precision slot arrays:
 // sorted slots wt2 = e^{+j 2 pi K0 t}, wt4 = w wt2; extended slots
 // wt1 = e^{-j 2 pi K0 t}, wt5 = w wt1
-// (beta: e^{-j 2 pi N t_p} by node when already at hand, else null)
+// (beta: e^{-j 2 pi N t_p} by node when already at hand, else null; one
+// launch: the extended slots are reached from the sorted ones through the
+// geometry's cell starts)
 template <typename TS>
-void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
-                    const double2* modp_srt, const double2* modm_ext, const double2* beta, double rhoP, double2* w64,
-                    c2<TS>* wt2_srt, c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s);
+void launch_weights(const uint64_t* T, const Geometry& g, const double2* D, const double2* modp_srt,
+                    const double2* beta, double rhoP, double2* w64, c2<TS>* wt2_srt, c2<TS>* wt4_srt,
+                    c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s);
 
 }  // namespace nufft45

@@ -487,7 +487,6 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
         tmp.release();
         return st;
     }
-    const int* ext_count = gs.cstart + (prm.ns + prm.halo);
     // v(q/P) (Eqs. 13, 19, 28): the type-1 of unit strengths at k = P r + m,
     // k < R = eta P, is the type-1 at m < P of the strengths
     // e^{-j 2 pi P r t_p}, r < eta (one spread of eta right-hand sides and a
@@ -534,12 +533,11 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     // e^{-j 2 pi P t_p} (the factor of Eq. 17) from the node phases
     const double2* beta = beta64;
     if (f32) {
-        launch_weights<float>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, beta, prm.rhoP,
-                              pl->w64, (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext,
-                              (float2*)pl->wt5_ext, s);
+        launch_weights<float>(pl->T, gs, pl->D64, pl->modp64_srt, beta, prm.rhoP, pl->w64, (float2*)pl->wt2_srt,
+                              (float2*)pl->wt4_srt, (float2*)pl->wt1_ext, (float2*)pl->wt5_ext, s);
     } else {
-        launch_weights<double>(pl->T, gs, ext_count, pl->D64, pl->modp64_srt, pl->modm64_ext, beta, prm.rhoP,
-                               pl->w64, (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
+        launch_weights<double>(pl->T, gs, pl->D64, pl->modp64_srt, beta, prm.rhoP, pl->w64,
+                               (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
                                (double2*)pl->wt5_ext, s);
     }
     NUFFT_CUDA_TRY(cudaGetLastError());

@@ -192,16 +192,19 @@ __global__ void k_to_solve(const double2* __restrict__ in, int64_t n, double sca
 }
 
 // Eqs. 27 / 40: w_p = h(-P t_p + j P a) / (L'(z_p) z_p) with
-// h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1), over the sorted slots
-// (p = sperm[i] visits every node once): w64[p], and the solve-precision
-// slot arrays mod_out[i] = e^{+j 2 pi K0 t_p} (modp_srt) and wmod_out[i] = w_p
-// times it
+// h(-P t + j P a) = 1/(rho^P e^{-j 2 pi P t} - 1), one thread per sorted slot
+// i (p = sperm[i] visits every node once): w64[p]; the solve-precision slot
+// arrays of the sorted list, srt_mod[i] = m = e^{+j 2 pi K0 t_p} (modp_srt) and
+// srt_wmod[i] = w_p m; and those of each extended slot e holding p (the middle
+// copy at pre + i, the copy of the last h cells, the copy of the first h cells),
+// ext_mod[e] = conj(m) and ext_wmod[e] = w_p conj(m).
 // (beta, when given, holds e^{-j 2 pi N t_p} by node: the plan's strengths for r = 1)
 template <typename TS>
-__global__ void k_weights_srt(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
-                              const double2* __restrict__ D, const double2* __restrict__ modp_srt,
-                              const double2* __restrict__ beta, int64_t N, double rhoP, double2* __restrict__ w64,
-                              c2<TS>* __restrict__ mod_out, c2<TS>* __restrict__ wmod_out) {
+__global__ void k_weights(const uint64_t* __restrict__ T, const int* __restrict__ sperm,
+                          const int* __restrict__ start, int64_t n, int h, const double2* __restrict__ D,
+                          const double2* __restrict__ modp_srt, const double2* __restrict__ beta, int64_t N,
+                          double rhoP, double2* __restrict__ w64, c2<TS>* __restrict__ srt_mod,
+                          c2<TS>* __restrict__ srt_wmod, c2<TS>* __restrict__ ext_mod, c2<TS>* __restrict__ ext_wmod) {
     pdl_wait();
     pdl_trigger();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,31 +213,29 @@ __global__ void k_weights_srt(const uint64_t* __restrict__ T, const int* __restr
     const uint64_t t = T[p];
     const double2 e = beta ? beta[p] : cis_turns_t((uint64_t)N * t, -1);
     const double2 z = cis_turns_t(t, +1);
-    const double2 h = make_double2(rhoP * e.x - 1.0, rhoP * e.y);
-    const double2 den = cmul(h, cmul(D[p], z));
+    const double2 hh = make_double2(rhoP * e.x - 1.0, rhoP * e.y);
+    const double2 den = cmul(hh, cmul(D[p], z));
     const double inv = 1.0 / (den.x * den.x + den.y * den.y);
     const double2 w = make_double2(den.x * inv, -den.y * inv);
     w64[p] = w;
     const double2 m = modp_srt[i];
-    mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
     const double2 wm = cmul(w, m);
-    wmod_out[i] = mk<TS>((TS)wm.x, (TS)wm.y);
-}
-
-// the same on the extended slots (below the device-held count), from w64 and
-// the slots' e^{-j 2 pi K0 t_p} (modm_ext)
-template <typename TS>
-__global__ void k_weights_ext(const int* __restrict__ eperm, int64_t cap, const int* __restrict__ ext_count,
-                              const double2* __restrict__ w64, const double2* __restrict__ modm_ext,
-                              c2<TS>* __restrict__ mod_out, c2<TS>* __restrict__ wmod_out) {
-    pdl_wait();
-    pdl_trigger();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cap || i >= (int64_t)*ext_count) return;
-    const double2 m = modm_ext[i];
-    mod_out[i] = mk<TS>((TS)m.x, (TS)m.y);
-    const double2 wm = cmul(w64[eperm[i]], m);
-    wmod_out[i] = mk<TS>((TS)wm.x, (TS)wm.y);
+    srt_mod[i] = mk<TS>((TS)m.x, (TS)m.y);
+    srt_wmod[i] = mk<TS>((TS)wm.x, (TS)wm.y);
+    // conj(m) and w conj(m) = conj(conj(w) m) on the extended copies
+    const double2 wcm = cmul(w, make_double2(m.x, -m.y));
+    const c2<TS> em = mk<TS>((TS)m.x, (TS)-m.y), ewm = mk<TS>((TS)wcm.x, (TS)wcm.y);
+    const int last = start[n - h], pre = start[n] - last, post = start[h];
+    ext_mod[pre + i] = em;
+    ext_wmod[pre + i] = ewm;
+    if (i >= last) {
+        ext_mod[i - last] = em;
+        ext_wmod[i - last] = ewm;
+    }
+    if (i < post) {
+        ext_mod[pre + N + i] = em;
+        ext_wmod[pre + N + i] = ewm;
+    }
 }
 
 }  // namespace
@@ -320,27 +321,20 @@ template void launch_to_solve<float>(const double2*, int64_t, double, float2*, c
 template void launch_to_solve<double>(const double2*, int64_t, double, double2*, cudaStream_t);
 
 template <typename TS>
-void launch_weights(const uint64_t* T, const Geometry& g, const int* ext_count, const double2* D,
-                    const double2* modp_srt, const double2* modm_ext, const double2* beta, double rhoP, double2* w64,
-                    c2<TS>* wt2_srt, c2<TS>* wt4_srt, c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s) {
+void launch_weights(const uint64_t* T, const Geometry& g, const double2* D, const double2* modp_srt,
+                    const double2* beta, double rhoP, double2* w64, c2<TS>* wt2_srt, c2<TS>* wt4_srt,
+                    c2<TS>* wt1_ext, c2<TS>* wt5_ext, cudaStream_t s) {
     const int64_t N = g.N;
-    {
-        Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0 + 16.0 + 4.0 * sizeof(TS) + (beta ? 16.0 : 0.0)));
-        launch_k(k_weights_srt<TS>, nblk(N), kTB, 0, s, T, g.srt_perm, D, modp_srt, beta, N, rhoP, w64, wt2_srt,
-                 wt4_srt);
-    }
-    {
-        Launch L(s, K_PLAN_STAGE, 2.0 * N * (4.0 + 16.0 + 16.0 + 4.0 * sizeof(TS)));
-        launch_k(k_weights_ext<TS>, nblk(2 * N), kTB, 0, s, g.ext_perm, 2 * N, ext_count, (const double2*)w64,
-                 modm_ext, wt1_ext, wt5_ext);
-    }
+    Launch L(s, K_PLAN_STAGE, N * (4.0 + 8.0 + 16.0 + 16.0 + 16.0 + (beta ? 16.0 : 0.0) + 12.0 * sizeof(TS)));
+    launch_k(k_weights<TS>, nblk(N), kTB, 0, s, T, g.srt_perm, g.cell_start, g.n, g.w / 2, D, modp_srt, beta, N,
+             rhoP, w64, wt2_srt, wt4_srt, wt1_ext, wt5_ext);
 }
-template void launch_weights<float>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
-                                    const double2*, const double2*, double, double2*, float2*, float2*, float2*,
-                                    float2*, cudaStream_t);
-template void launch_weights<double>(const uint64_t*, const Geometry&, const int*, const double2*, const double2*,
-                                     const double2*, const double2*, double, double2*, double2*, double2*, double2*,
-                                     double2*, cudaStream_t);
+template void launch_weights<float>(const uint64_t*, const Geometry&, const double2*, const double2*,
+                                    const double2*, double, double2*, float2*, float2*, float2*, float2*,
+                                    cudaStream_t);
+template void launch_weights<double>(const uint64_t*, const Geometry&, const double2*, const double2*,
+                                     const double2*, double, double2*, double2*, double2*, double2*, double2*,
+                                     cudaStream_t);
 
 nufft_status plan_kernels_init() { return cis_table_ensure(); }
 
