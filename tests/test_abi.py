@@ -67,3 +67,7 @@ def test_argument_errors_without_device(L):
     assert L.nufft_inv5(None, xp, xp, 1, None) == 1
     assert L.nufft_destroy(None) == 0
     assert L.nufft_plan_info(None, None) == 1
+    # the measurement utility checks its arguments before touching a device
+    r = ctypes.c_double()
+    assert L.nufft_measure_fma(3, ctypes.byref(r), None) == 1
+    assert L.nufft_measure_fma(1, None, None) == 1
