@@ -899,6 +899,19 @@ FFTPlan::~FFTPlan() {
 
 int64_t fft_work_elems(const FFTPlan& p) { return p.bluestein ? 2 * p.m : p.n; }
 
+namespace {
+// a wait on a barrier phase that nothing completes: the bounded wait of the
+// pass kernels gives up and counts the expiry (test hook)
+__global__ void k_debug_wait_expiry() {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        p2t::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!p2t::mbar_wait(&bar, 0)) atomicAdd(&g_wait_expired, 1);
+    }
+}
+}  // namespace
+
 nufft_status fft_wait_status(cudaStream_t s) {
     int expired = 0;
     NUFFT_CUDA_TRY(cudaMemcpyFromSymbolAsync(&expired, g_wait_expired, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
@@ -910,7 +923,7 @@ nufft_status fft_wait_status(cudaStream_t s) {
     return fail(NUFFT_ERR_TIMEOUT, "%d FFT pass tile wait(s) expired", expired);
 }
 
-// passes of the few-vector double-float kernel: n = 2^L, L >= 11, split into
+// passes of the shared-memory double-float kernel: n = 2^L, L >= 11, split into
 // balanced radices 2^5 .. 2^10 (at least two passes, so that every pass has
 // n/R >= 2 columns)
 // batches up to this many points take the shared-memory radix-4 kernel (for
@@ -1124,3 +1137,13 @@ nufft_status fft_exec_dd(const FFTPlan& p, double2* buf, double2* work, int64_t 
 template nufft_status fft_exec<double>(const FFTPlan&, double2*, double2*, int64_t, int, cudaStream_t, double2**);
 
 }  // namespace nufft45
+
+// Test hook (not part of the public header): one kernel whose bounded wait
+// on a barrier phase that never completes gives up after about a second; the
+// next nufft_stream_check reports NUFFT_ERR_TIMEOUT.  Asynchronous on `stream`.
+extern "C" nufft_status nufft_debug_wait_expiry(nufft_stream_t stream) {
+    using namespace nufft45;
+    k_debug_wait_expiry<<<1, 32, 0, (cudaStream_t)stream>>>();
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}

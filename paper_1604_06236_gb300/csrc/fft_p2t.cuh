@@ -14,8 +14,9 @@
 // each thread loads W^{jm k2} and one entry of the per-tile [k1][c] table of
 // W^{jm R2 k1}, so a tile of C R elements needs 2 C R / R1 table loads instead
 // of C R.  The inner twiddles W_R^{m1 k2} sit in shared memory for the
-// lifetime of the CTA.  Every wait is bounded: on expiry the kernel counts the
-// event in g_wait_expired, drains its copies in flight and returns.
+// lifetime of the CTA.  Every wait is bounded (a poll count and one second):
+// on expiry the kernel counts the event in g_wait_expired, drains its copies in
+// flight (again with bounded waits) and returns.
 //
 // FUSE (radix 16 x 16, two-pass length n = R^2 only): the last pass of one
 // transform, a pointwise product and the first pass of a second transform of
@@ -47,7 +48,8 @@ template <int R1, int R2> struct TCfg {
 
 constexpr int kStages = 2;      // ring depth
 constexpr int kMinBlocks = 3;   // resident CTAs per SM the register budget allows
-constexpr int kPollLimit = 1 << 22;
+constexpr int kPollLimit = 1 << 22;                 // polls of one wait, at most
+constexpr unsigned long long kWaitNs = 1000000000;  // and at most one second
 
 struct TArgs {
     int n_log, R_log, Ns_log, C_log;
@@ -84,9 +86,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// true once the phase with this parity completed; false after kPollLimit
+// polls or kWaitNs nanoseconds, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-    for (int i = 0; i < kPollLimit; ++i)
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kPollLimit; ++i) {
         if (mbar_try_wait(b, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1, int c2,
