@@ -465,9 +465,11 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         }
         __syncthreads();
 
-        // ---- the float32 inverse
+        // ---- the float32 inverse (its scalings rho^{+-k} in float32: |k log rho|
+        // <= log gamma, so expf is accurate to a few float32 ulp)
         const float tow_s = 2.0f / kWSolve;
         const float beta_s = (float)a.beta_solve;
+        const float lr = (float)log_rho, invN = 1.0f / (float)N;
         if (d.kind == 5) {
             // a_p = s_p w_p e^{-j 2 pi K0 t_p}: type-1 (gather), FFT, deconvolve x rho^k
             for (int g = tid; g < ns; g += nt) {
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             float2* B = cta_fft<float>(g32, gw32, d.log_ns, -1, a.tw32, a.max_rl);
             for (int64_t k = tid; k < N; k += nt) {
                 const int64_t kc = k - K0;
-                const float f = (float)exp((double)k * log_rho) * dec_s[kc + ns / 2];
+                const float f = expf((float)k * lr) * dec_s[kc + ns / 2];
                 vec32[k] = cscale(B[kc < 0 ? kc + ns : kc], f);
             }
             __syncthreads();
@@ -498,10 +500,10 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             __syncthreads();
             cta_dft<float>(vec32, vw32, d, -1, bf, a.tw32, a.max_rl);
             for (int64_t m = tid; m < N; m += nt)
-                d.out[m] = cscale(vec32[m], (float)(exp(-(double)m * log_rho) / (double)N));
+                d.out[m] = cscale(vec32[m], expf(-(float)m * lr) * invN);
             __syncthreads();
         } else {
-            for (int64_t k = tid; k < N; k += nt) vec32[k] = cscale(d.in[k], (float)exp((double)k * log_rho));
+            for (int64_t k = tid; k < N; k += nt) vec32[k] = cscale(d.in[k], expf((float)k * lr));
             __syncthreads();
             cta_dft<float>(vec32, vw32, d, +1, bf, a.tw32, a.max_rl);
             for (int64_t q = tid; q < N; q += nt) vec32[q] = cmul(vec32[q], K32[q]);
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 const int64_t m = kc + K0;
                 float2 v = make_float2(0.f, 0.f);
                 if (m >= 0 && m < N)
-                    v = cscale(vec32[m], (float)(exp(-(double)m * log_rho) / (double)N) * dec_s[kc + ns / 2]);
+                    v = cscale(vec32[m], expf(-(float)m * lr) * invN * dec_s[kc + ns / 2]);
                 g32[g] = v;
             }
             __syncthreads();
