@@ -44,6 +44,23 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest(dist, value, device):
+    """The largest `value` over the ranks (a replica job takes as long as its
+    slowest rank); `value` itself without a process group."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons, time-stamped, so
@@ -316,13 +333,8 @@ def run_gpu(args):
     pkg.check(L.nufft_profile_read(entries, 16, ctypes.byref(cnt)))
     prof = {e.name.decode(): {"launches": e.launches, "ms": e.ms, "bytes": e.bytes} for e in entries[:cnt.value]}
 
-    t_max = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    transforms = 2 * B * args.steps * ws
-    value = transforms / (t_max / 1e3)
+    t_max = slowest(dist, total_ms, dev)
+    value = job_rate(2 * B * args.steps, ws, t_max / 1e3)
 
     # ---- roofline of the dominant kernel (per-launch events, traced pass) --
     peak, peak_src = measured_peaks()
@@ -405,14 +417,10 @@ def run_gpu(args):
         for i in range(args.steps):
             e2e_step(3 + i)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = slowest(dist, time.perf_counter() - t0, dev)
         h2d = N * 8 + 2 * B * N * 8
         d2h = 2 * B * N * 8
-        result["e2e"] = {"value": 2 * B * args.steps * ws / e2e_s, "unit": "transforms/s",
+        result["e2e"] = {"value": job_rate(2 * B * args.steps, ws, e2e_s), "unit": "transforms/s",
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                          "how": "nufft_plan/nufft_inv5/nufft_inv4 given pinned host buffers (nodes, data, "
                                 "results); the library stages them through device memory on its copy streams, "
