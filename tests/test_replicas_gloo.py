@@ -34,7 +34,8 @@ def _rank(rank, world, port, times, out):
 def test_two_replicas_take_the_slowest_rank():
     world, port = 2, _free_port()
     times = [0.75, 1.25]
-    with mp.Manager() as m:
+    # spawned, never forked: a fork after a CUDA call can hang the child
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, times, out), nprocs=world, join=True)
         res = dict(out)
