@@ -162,17 +162,23 @@ nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch
  *   Scratch is a fixed 8 MiB array inside the library image, present on
  *   every GPU that loads the library until the process exits; right-hand
  *   sides are processed one at a time through it.
+ * Refined plans (NUFFT_REFINE) get the refinement of Sec. V as in
+ *   nufft_inv5, also inside the static array: the float64 forward transform
+ *   of the first solution, the residual and the correction take extra room.
  * Limits.  A plan whose scratch per right-hand side exceeds 8 MiB is rejected
- *   with NUFFT_ERR_ARG (power-of-two N up to 131072 in NUFFT_FP32 and up to
- *   65536 in NUFFT_FP64 fit).  f and c must be device buffers (host buffers
- *   would need staging memory): NUFFT_ERR_ARG otherwise.
+ *   with NUFFT_ERR_ARG.  Power-of-two N that fit: up to 131072 in NUFFT_FP32
+ *   and up to 65536 in NUFFT_FP64; with NUFFT_REFINE up to 65536 in
+ *   NUFFT_FP32 and up to 32768 in NUFFT_FP64.  f and c must be device
+ *   buffers (host buffers would need staging memory): NUFFT_ERR_ARG otherwise.
  * Set-up.  The first call on each device resolves the scratch array's
  *   device address (cudaGetSymbolAddress) with that device current; make
  *   that first call before any stream capture.
- * Concurrency.  All calls share the one scratch array.  Nothing in it needs
- *   to start at zero (every stage overwrites what it reads), but calls whose
- *   work overlaps on the GPU (other streams, other threads) race on it:
- *   order them on one stream or serialise them.
+ * Concurrency.  All calls share the one scratch array, which keeps what the
+ *   last call left in it.  Nothing in it needs to start at zero: every stage
+ *   overwrites what it later reads, and the one stage that relies on zeros
+ *   (the zero-padded grid of NUFFT_TOEPLITZ plans) clears them itself.  Calls
+ *   whose work overlaps on the GPU (other streams, other threads) race on the
+ *   array: order them on one stream or serialise them.
  * Arguments, layout and results as for nufft_inv5.
  */
 nufft_status nufft_inv5_noalloc(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream);

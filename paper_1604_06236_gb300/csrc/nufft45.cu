@@ -1362,19 +1362,78 @@ nufft_status noalloc_scratch(void** out) {
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Offsets into the static scratch for one right-hand side.  The inverse uses
+// the grid, its FFT work vector and the two length-N vectors (region U).  A
+// refined plan (Sec. V, Eqs. 44-46) also needs the float64 copy of the first
+// solution, the float64 forward transform of it, the residual and the
+// correction; the float64 forward's grid and work vector are only live
+// between the two inverses, so they share region U with the inverse's
+// buffers, and the correction reuses the float64 copy's slot once the
+// forward transform has read it.
+struct NoAllocLayout {
+    size_t gA = 0, gW = 0, vA = 0, vW = 0;      // inverse (region U)
+    size_t g64 = 0, gw64 = 0;                   // float64 forward (region U)
+    size_t x64 = 0, y64 = 0, r = 0;             // refinement
+    size_t corr = 0;                            // = x64
+    size_t need = 0;
+};
+
+NoAllocLayout noalloc_layout(const nufft_plan_s* pl) {
+    const Params& prm = pl->prm;
+    const Tables& tab = *pl->tab;
+    const size_t es = solve_elem(prm);
+    NoAllocLayout L;
+    size_t u = 0;
+    L.gA = u; u += round256(es * prm.ns);
+    L.gW = u; u += round256(es * fft_work_elems(tab.fft_ns));
+    L.vA = u; u += round256(es * prm.N);
+    L.vW = u; u += round256(es * fft_work_elems(tab.fft_P));
+    if (!prm.refine) {
+        L.need = u;
+        return L;
+    }
+    size_t f = 0;
+    L.g64 = f; f += round256(sizeof(double2) * prm.ns);
+    L.gw64 = f; f += round256(sizeof(double2) * fft_work_elems(tab.fft_ns64));
+    size_t q = std::max(u, f);
+    L.x64 = q; q += round256(sizeof(double2) * prm.N);
+    L.y64 = q; q += round256(sizeof(double2) * prm.N);
+    L.r = q; q += round256(es * prm.N);
+    L.corr = L.x64;
+    L.need = q;
+    return L;
+}
+
 template <typename T>
 nufft_status inv5_noalloc_impl(nufft_plan_s* pl, const c2<T>* in, c2<T>* out, int64_t batch, char* scratch,
                                cudaStream_t s) {
     const Params& prm = pl->prm;
-    const Tables& tab = *pl->tab;
-    char* p = scratch;
-    c2<T>* gA = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * prm.ns);
-    c2<T>* gW = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * fft_work_elems(tab.fft_ns));
-    c2<T>* vA = reinterpret_cast<c2<T>*>(p); p += round256(sizeof(c2<T>) * prm.N);
-    c2<T>* vW = reinterpret_cast<c2<T>*>(p);
+    const int64_t N = prm.N;
+    const NoAllocLayout L = noalloc_layout(pl);
+    c2<T>* gA = reinterpret_cast<c2<T>*>(scratch + L.gA);
+    c2<T>* gW = reinterpret_cast<c2<T>*>(scratch + L.gW);
+    c2<T>* vA = reinterpret_cast<c2<T>*>(scratch + L.vA);
+    c2<T>* vW = reinterpret_cast<c2<T>*>(scratch + L.vW);
     for (int64_t b = 0; b < batch; ++b) {
-        const nufft_status st = run_chunk<T>(pl, OP_INV5, in + b * prm.N, out + b * prm.N, 1, gA, gW, vA, vW, s);
+        const c2<T>* bin = in + b * N;
+        c2<T>* bout = out + b * N;
+        nufft_status st = run_chunk<T>(pl, OP_INV5, bin, bout, 1, gA, gW, vA, vW, s);
         if (st != NUFFT_OK) return st;
+        if (!prm.refine) continue;
+        // Sec. V refinement as in nufft_inv5: x2 = x1 + inv(b - G x1), the
+        // residual from a float64 type-2 transform with the plan's float64 data
+        double2* x64 = reinterpret_cast<double2*>(scratch + L.x64);
+        double2* y64 = reinterpret_cast<double2*>(scratch + L.y64);
+        c2<T>* r = reinterpret_cast<c2<T>*>(scratch + L.r);
+        c2<T>* corr = reinterpret_cast<c2<T>*>(scratch + L.corr);
+        launch_widen<T>(bout, x64, N, s);
+        st = forward64(pl, true, x64, y64, 1, reinterpret_cast<double2*>(scratch + L.g64),
+                       reinterpret_cast<double2*>(scratch + L.gw64), s);
+        if (st != NUFFT_OK) return st;
+        launch_residual<T>(bin, y64, r, N, s);
+        if ((st = run_chunk<T>(pl, OP_INV5, r, corr, 1, gA, gW, vA, vW, s)) != NUFFT_OK) return st;
+        launch_accumulate<T>(bout, corr, N, s);
+        NUFFT_CUDA_TRY(cudaGetLastError());
     }
     return NUFFT_OK;
 }
@@ -1388,14 +1447,13 @@ extern "C" nufft_status nufft_inv5_noalloc(nufft_plan_t plan, const void* f, voi
     if (batch == 0) return NUFFT_OK;
     if (!f || !c) return fail(NUFFT_ERR_ARG, "null data pointer");
     const Params& prm = plan->prm;
-    const Tables& tab = *plan->tab;
     const size_t es = solve_elem(prm);
-    const size_t need = round256(es * prm.ns) + round256(es * fft_work_elems(tab.fft_ns)) + round256(es * prm.N) +
-                        round256(es * fft_work_elems(tab.fft_P));
+    const size_t need = noalloc_layout(plan).need;
     if (need > kNoAllocScratchBytes)
         return fail(NUFFT_ERR_ARG,
-                    "nufft_inv5_noalloc: N = %lld needs %zu bytes of scratch per right-hand side, more than the "
-                    "%zu-byte static scratch; use nufft_inv5", (long long)prm.N, need, kNoAllocScratchBytes);
+                    "nufft_inv5_noalloc: N = %lld%s needs %zu bytes of scratch per right-hand side, more than the "
+                    "%zu-byte static scratch; use nufft_inv5", (long long)prm.N, prm.refine ? " (refined)" : "",
+                    need, kNoAllocScratchBytes);
     const size_t bytes = es * (size_t)prm.N * (size_t)batch;
     const char* ib = (const char*)f;
     const char* ob = (const char*)c;
