@@ -10,6 +10,7 @@ What it computes (the plain definitions, no fast algorithm):
 * ``type1(x, a)``     A_k = sum_p a_p e^{-j2pi k t_p}, k = 0..P-1        (Sec. II, Eq. 32)
 * ``type1_at(x,a,ks)`` the same sum at a list of integer frequencies
 * ``type2(x, S)``     s_p = sum_m S_m e^{+j2pi m t_p}, m = 0..P-1        (Sec. II, Eq. 34)
+* ``type2_at(x,S,ms)`` the same sum with the coefficients at a list of integer frequencies
 * ``inv5(x, s)``      solves Eq. 48 for S by Gaussian elimination (LU with
                       partial pivoting, the paper's GE benchmark of Sec. VI)
 * ``inv4(x, A)``      solves Eq. 47 for a by the same LU on G^H
@@ -68,8 +69,10 @@ def _load():
         lib.oracle_deriv_samples.argtypes = [i64, P, P]
         lib.oracle_weights.argtypes = [i64, P, d, P, P]
         lib.oracle_type1_at.argtypes = [i64, P, P, i64, P, P]
+        lib.oracle_type2_at.argtypes = [i64, P, P, i64, P, P]
         for f in (lib.oracle_canon, lib.oracle_type1, lib.oracle_type2, lib.oracle_matrix,
-                  lib.oracle_kernel_samples, lib.oracle_deriv_samples, lib.oracle_weights, lib.oracle_type1_at):
+                  lib.oracle_kernel_samples, lib.oracle_deriv_samples, lib.oracle_weights, lib.oracle_type1_at,
+                  lib.oracle_type2_at):
             f.restype = None
         _lib = lib
     return _lib
@@ -118,6 +121,18 @@ def type2(x, S, m0=0):
     S = _c128(S)
     s = np.empty(T.size, dtype=np.complex128)
     _load().oracle_type2(S.size, m0, _ptr(S), T.size, _ptr(T), _ptr(s))
+    return s
+
+
+def type2_at(x, S, ms):
+    """Eq. 34 with coefficient S_i at the integer frequency ms[i]:
+    s_q = sum_i S_i e^{+j 2 pi ms[i] t_q} at every node."""
+    T, _ = canon(x)
+    S = _c128(S)
+    ms = np.ascontiguousarray(np.asarray(ms, dtype=np.int64))
+    assert ms.size == S.size
+    s = np.empty(T.size, dtype=np.complex128)
+    _load().oracle_type2_at(ms.size, _ptr(ms), _ptr(S), T.size, _ptr(T), _ptr(s))
     return s
 
 

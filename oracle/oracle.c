@@ -208,3 +208,22 @@ void oracle_type1_at(int64_t P, const uint64_t* T, const double* a, int64_t nk, 
         A[2 * i + 1] = si;
     }
 }
+
+/* Type-2, Eq. 34, with the coefficients at an arbitrary list of integer
+   frequencies ms[0..nm-1]: s_q = sum_i S_i e^{+j 2 pi ms[i] t_q} at Q nodes. */
+void oracle_type2_at(int64_t nm, const int64_t* ms, const double* S, int64_t Q, const uint64_t* T, double* s)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < Q; ++q) {
+        double sr = 0.0, si = 0.0;
+        for (int64_t i = 0; i < nm; ++i) {
+            double cr, ci;
+            cis_turns((uint64_t)ms[i] * T[q], 1.0, &cr, &ci);
+            double br = S[2 * i], bi = S[2 * i + 1];
+            sr += br * cr - bi * ci;
+            si += br * ci + bi * cr;
+        }
+        s[2 * q] = sr;
+        s[2 * q + 1] = si;
+    }
+}

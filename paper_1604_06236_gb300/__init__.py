@@ -328,11 +328,6 @@ class Batch:
         check(lib().nufft_batch_status(self._h, ctypes.c_void_p(st.data_ptr()), _stream_handle(stream)))
         return st
 
-    def check(self):
-        """Wait for the plan; raise NufftError(NUFFT_ERR_DUP_NODES) if two nodes
-        coincide (the way a DEFER_CHECK plan reports it)."""
-        check(lib().nufft_plan_check(self._h))
-
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().nufft_batch_destroy(self._h)

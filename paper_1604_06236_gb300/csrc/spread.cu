@@ -860,3 +860,36 @@ INST(double)
 #undef INST
 
 }  // namespace nufft45
+
+namespace nufft45 {
+namespace {
+__global__ void k_debug_dd_exp(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float2 s_exp[64];
+    if (threadIdx.x < 64) s_exp[threadIdx.x] = c_exp2_64[threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = x[i];
+        const float hi = (float)v;
+        const dd e = dd_exp_nonpos(dd(hi, (float)(v - (double)hi)), s_exp);
+        out[i] = (double)e.hi + (double)e.lo;
+    }
+}
+}  // namespace
+}  // namespace nufft45
+
+// Test hook (not part of the public header): out[i] = e^{x[i]} by the
+// double-float exponential of the plan's spreading kernels (dd_exp_nonpos,
+// valid for -87 < x <= 0); device arrays of n float64 values.
+extern "C" nufft_status nufft_debug_dd_exp(int64_t n, const double* x, double* out, nufft_stream_t stream) {
+    using namespace nufft45;
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(NUFFT_ERR_ARG, "bad exp test arguments");
+    if (n == 0) return NUFFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_k(k_debug_dd_exp, nblk(n), kTB, 0, s, x, n, out);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}

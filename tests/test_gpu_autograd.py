@@ -162,3 +162,51 @@ def test_full_size_finite_differences():
             vt = torch.from_numpy(v).cuda()
             fd = (loss(x0 + h * vt) - loss(x0 - h * vt)) / (2 * h)
             assert abs(fd - (gx * v).sum()) <= 1e-3 * np.linalg.norm(gx[b])
+
+
+@pytest.mark.parametrize("kind", [5, 4])
+def test_fp32_gradients_vs_dense_oracle_n1024(kind):
+    """The differentiable workload's node law (u ~ U(-0.45, 0.45)) and data
+    type (complex64) at the largest size the dense oracle handles quickly:
+    gradients with respect to the data and the nodes against the oracle's LU
+    and exact-phase gradient, for 2 instances with their own nodes."""
+    N, B = 1024, 2
+    x, d, ct = _setup(N, B, seed=91 + kind, shared=False)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    dt = torch.from_numpy(d).to(torch.complex64).cuda().requires_grad_(True)
+    ctt = torch.from_numpy(ct).to(torch.complex64).cuda()
+    fn = ag.inv5 if kind == 5 else ag.inv4
+    (fn(dt, xt, prec=pkg.FP32) - ctt).abs().pow(2).sum().backward()
+    solve = oracle.inv5 if kind == 5 else oracle.inv4
+    vjp = oracle.inv5_vjp if kind == 5 else oracle.inv4_vjp
+    dr = d.astype(np.complex64).astype(np.complex128)
+    cr = ct.astype(np.complex64).astype(np.complex128)
+    for b in range(B):
+        g_d, g_x = vjp(x[b], dr[b], 2 * (solve(x[b], dr[b]) - cr[b]))
+        assert _rel(dt.grad[b].cpu().numpy().astype(np.complex128), g_d) <= TOL_GRAD[pkg.FP32]
+        assert _rel(xt.grad[b].cpu().numpy(), g_x) <= TOL_GRAD[pkg.FP32]
+
+
+def test_full_size_fp32_gradients_vs_fp64():
+    """The N = 262144 differentiable workload in its own precision: complex64
+    samples, the float32-split path, instances with their own nodes (seeds
+    4 + i, 4 of the 64), loss ||c_hat - c_target||^2.  Gradients with respect
+    to the samples and the nodes against the float64 GPU path on the same
+    (complex64-rounded) inputs, whose gradients the central-difference test
+    above pins at this size."""
+    N, B = 262144, 4
+    x = np.stack([synth.jittered_nodes(N, 0.45, seed=4 + i) for i in range(B)])
+    f = synth.cn01((B, N), seed=50).astype(np.complex64)
+    ct = synth.cn01((B, N), seed=51).astype(np.complex64)
+    grads = {}
+    for prec, dt in ((pkg.FP32, torch.complex64), (pkg.FP64, torch.complex128)):
+        xt = torch.from_numpy(x).cuda().requires_grad_(True)
+        ft = torch.from_numpy(f).to(dt).cuda().requires_grad_(True)
+        ctt = torch.from_numpy(ct).to(dt).cuda()
+        (ag.inv5(ft, xt, prec=prec) - ctt).abs().pow(2).sum().backward()
+        grads[prec] = (ft.grad.cpu().numpy().astype(np.complex128), xt.grad.cpu().numpy())
+    gf32, gx32 = grads[pkg.FP32]
+    gf64, gx64 = grads[pkg.FP64]
+    for b in range(B):
+        assert _rel(gf32[b], gf64[b]) <= TOL_GRAD[pkg.FP32], (b, _rel(gf32[b], gf64[b]))
+        assert _rel(gx32[b], gx64[b]) <= TOL_GRAD[pkg.FP32], (b, _rel(gx32[b], gx64[b]))

@@ -4,14 +4,20 @@ Nodes x_k = 2 pi (k + u_k)/N, u_k ~ U(-0.45, 0.45), then 1% of the even
 indices get t_i = t_{i+1} - d_i/N with d_i ~ U(0.01, 0.05) (seed 2).  A dense
 O(N^3) solve is out of reach, so parity uses what the oracle can compute at
 this size:
-  * sparse known truth: 64 nonzero coefficients (resp. node amplitudes), the
-    inputs built by exact-phase direct sums over the support only, and the
-    full recovered vector compared element by element;
+  * known truth on 2048 coefficients (resp. node amplitudes) spread over the
+    whole index range: the inputs are exact-phase direct sums over that
+    support (2^31 terms), and the full recovered vector is compared with the
+    truth in rel-L2 and element by element;
   * the residual of dense CN(0,1) data at 1024 sampled nodes (resp. 1024
-    sampled frequencies), by exact-phase direct sums over all N terms.
-The clusters make L'(z_p) small for the paired nodes and the weights lose
-accuracy to cancellation, so these plans use the refined method of Sec. V
-(NUFFT_REFINE: one correction from a float64 residual).
+    sampled frequencies), by exact-phase direct sums over all N terms;
+  * the dense float32 solution against the float64 one (itself pinned by the
+    known truth above to ~1e-13).
+The clusters make L'(z_p) small for the paired nodes; the weights of a pair
+are large and nearly opposite, and the cancellation between them amplifies
+the round-off of the inverse.  The refined method of Sec. V (NUFFT_REFINE:
+one correction from a float64 residual, Eqs. 44-46) is what meets the
+tolerances here; the plain method's error is measured and bounded as well,
+so that the need for refinement stays visible.
 """
 import numpy as np
 import pytest
@@ -25,8 +31,12 @@ pytestmark = pytest.mark.gpu
 import paper_1604_06236_gb300 as pkg  # noqa: E402
 
 N = 1 << 20
+M = 2048
 CDT = {pkg.FP32: torch.complex64, pkg.FP64: torch.complex128}
 TOL = {pkg.FP32: 1e-5, pkg.FP64: 1e-10}
+# plain-method errors measured on this node set (float32 inv5 3.2e-4, inv4
+# 2.8e-5; float64 inv5 1.4e-7, inv4 5.1e-10): a regression bound, not a tolerance
+PLAIN_BOUND = {pkg.FP32: 3e-3, pkg.FP64: 3e-6}
 
 
 @pytest.fixture(scope="module")
@@ -36,50 +46,95 @@ def nodes():
     return synth.clustered_nodes(N, 0.45, 0.01, 0.01, 0.05, seed=2)
 
 
-def _sparse_coeffs(seed, k=64):
-    g = synth.rng(seed)
-    idx = np.sort(g.choice(N, k, replace=False))
-    vals = synth.cn01(k, generator=g)
-    return idx, vals
-
-
-@pytest.mark.parametrize("prec", [pkg.FP32, pkg.FP64])
-def test_inv5_sparse_known_truth(nodes, prec):
-    idx, vals = _sparse_coeffs(5)
-    f = np.zeros(N, complex)
-    for m, v in zip(idx, vals):
-        f += oracle.type2(nodes, np.array([v]), m0=int(m))
+@pytest.fixture(scope="module")
+def truth5(nodes):
+    g = synth.rng(5)
+    ms = np.sort(g.choice(N, M, replace=False))
+    vals = synth.cn01(M, generator=g)
     c = np.zeros(N, complex)
-    c[idx] = vals
-    plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | pkg.REFINE)
-    S = plan.inv5(torch.from_numpy(f).to(CDT[prec]).cuda()).cpu().numpy().astype(complex)
-    assert oracle.rel_l2(S, c) <= TOL[prec]
+    c[ms] = vals
+    return oracle.type2_at(nodes, vals, ms), c
 
 
-@pytest.mark.parametrize("prec", [pkg.FP32, pkg.FP64])
-def test_inv4_sparse_known_truth(nodes, prec):
-    idx, vals = _sparse_coeffs(6)
-    A = oracle.type1(nodes[idx], vals, M=N)
+@pytest.fixture(scope="module")
+def truth4(nodes):
+    g = synth.rng(6)
+    idx = np.sort(g.choice(N, M, replace=False))
+    vals = synth.cn01(M, generator=g)
     a = np.zeros(N, complex)
     a[idx] = vals
-    plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | pkg.REFINE)
-    got = plan.inv4(torch.from_numpy(A).to(CDT[prec]).cuda()).cpu().numpy().astype(complex)
-    assert oracle.rel_l2(got, a) <= TOL[prec]
+    return oracle.type1(nodes[idx], vals, M=N), a
+
+
+def _elementwise(got, ref, tol):
+    """max |error| over the vector against its RMS value: a bound that a few
+    wrong entries inside a passing rel-L2 would break"""
+    rms = np.linalg.norm(ref) / np.sqrt(ref.size)
+    return np.abs(got - ref).max() / rms <= 30 * tol
 
 
 @pytest.mark.parametrize("prec", [pkg.FP32, pkg.FP64])
-def test_dense_residual_at_sampled_points(nodes, prec):
-    """||G S - f|| over 1024 sampled nodes relative to ||f|| there (type-5),
-    and the same for type-4 at 1024 sampled frequencies; bounded by the
-    tolerance (the residual is the backward error, at most the forward error
-    times ||G|| ||S|| / ||f||, of order one here)."""
-    f = synth.cn01(N, seed=7)
-    plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | pkg.REFINE)
-    fr = f.astype(np.complex64).astype(complex) if prec == pkg.FP32 else f
+@pytest.mark.parametrize("refine", [True, False])
+def test_inv5_known_truth(nodes, truth5, prec, refine):
+    f, c = truth5
+    plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | (pkg.REFINE if refine else 0))
     S = plan.inv5(torch.from_numpy(f).to(CDT[prec]).cuda()).cpu().numpy().astype(complex)
+    e = oracle.rel_l2(S, c)
+    print("N=2^20 clustered inv5 prec %d refine %d: rel-L2 %.3e" % (prec, refine, e))
+    if refine:
+        assert e <= TOL[prec]
+        assert _elementwise(S, c, TOL[prec])
+    else:
+        assert e <= PLAIN_BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", [pkg.FP32, pkg.FP64])
+@pytest.mark.parametrize("refine", [True, False])
+def test_inv4_known_truth(nodes, truth4, prec, refine):
+    A, a = truth4
+    plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | (pkg.REFINE if refine else 0))
+    got = plan.inv4(torch.from_numpy(A).to(CDT[prec]).cuda()).cpu().numpy().astype(complex)
+    e = oracle.rel_l2(got, a)
+    print("N=2^20 clustered inv4 prec %d refine %d: rel-L2 %.3e" % (prec, refine, e))
+    if refine:
+        assert e <= TOL[prec]
+        assert _elementwise(got, a, TOL[prec])
+    else:
+        assert e <= PLAIN_BOUND[prec]
+
+
+@pytest.fixture(scope="module")
+def dense(nodes):
+    """Refined solutions of dense CN(0,1) data in both precisions (type-5 and type-4)."""
+    f = synth.cn01(N, seed=7)
+    out = {}
+    for prec in (pkg.FP32, pkg.FP64):
+        plan = pkg.Plan(torch.from_numpy(nodes).cuda(), prec=prec | pkg.REFINE)
+        ft = torch.from_numpy(f).to(CDT[prec]).cuda()
+        out[prec] = (plan.inv5(ft).cpu().numpy().astype(complex), plan.inv4(ft).cpu().numpy().astype(complex))
+        plan.close()
+    return f, out
+
+
+@pytest.mark.parametrize("prec", [pkg.FP32, pkg.FP64])
+def test_dense_residual_at_sampled_points(nodes, dense, prec):
+    """||G S - f|| over 1024 sampled nodes relative to ||f|| there (type-5),
+    and the same for type-4 at 1024 sampled frequencies, within the tolerance.
+    (The float32 result's own rounding to complex64 already leaves a residual
+    of 2.7e-7 here, measured from the float64 solution rounded to complex64.)"""
+    f, out = dense
+    S, a = out[prec]
+    fr = f.astype(np.complex64).astype(complex) if prec == pkg.FP32 else f
     q = np.sort(synth.rng(8).choice(N, 1024, replace=False))
-    assert oracle.rel_l2(oracle.type2(nodes[q], S), fr[q]) <= 10 * TOL[prec]
-    a = plan.inv4(torch.from_numpy(f).to(CDT[prec]).cuda()).cpu().numpy().astype(complex)
+    assert oracle.rel_l2(oracle.type2(nodes[q], S), fr[q]) <= TOL[prec]
     k = np.sort(synth.rng(9).choice(N, 1024, replace=False))
-    Ak = oracle.type1_at(nodes, a, k)
-    assert oracle.rel_l2(Ak, fr[k]) <= 10 * TOL[prec]
+    assert oracle.rel_l2(oracle.type1_at(nodes, a, k), fr[k]) <= TOL[prec]
+
+
+def test_dense_float32_against_float64(dense):
+    """Dense data: the refined float32 solution (complex64 samples, float64
+    plan) against the refined float64 one, element by element."""
+    _, out = dense
+    for got, ref in zip(out[pkg.FP32], out[pkg.FP64]):
+        assert oracle.rel_l2(got, ref) <= TOL[pkg.FP32]
+        assert _elementwise(got, ref, TOL[pkg.FP32])

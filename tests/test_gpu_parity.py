@@ -46,6 +46,16 @@ def _np(t):
     return t.detach().cpu().numpy().astype(np.complex128)
 
 
+def _close(got, ref, tol):
+    """rel-L2 within tol, and no single element off by more than 30 tol times
+    the reference's RMS value (a few wrong entries inside a passing rel-L2
+    would break this)."""
+    e = oracle.rel_l2(got, ref)
+    rms = np.linalg.norm(ref) / np.sqrt(max(1, ref.size))
+    m = np.abs(np.asarray(got) - ref).max() / rms if ref.size else 0.0
+    return e <= tol and m <= 30 * tol
+
+
 def _rounded(a, prec):
     """The input as the GPU sees it (complex64 rounding for FP32), in float64."""
     return a.astype(np.complex64).astype(np.complex128) if prec == FP32 else a
@@ -90,8 +100,8 @@ def test_inverses_vs_lu(N, prec):
     sr = _rounded(s, prec)
     S_ref = oracle.inv5(x, sr)
     a_ref = oracle.inv4(x, sr)
-    assert oracle.rel_l2(_np(plan.inv5(_dev(s, prec))), S_ref) <= TOL_INV[prec]
-    assert oracle.rel_l2(_np(plan.inv4(_dev(s, prec))), a_ref) <= TOL_INV[prec]
+    assert _close(_np(plan.inv5(_dev(s, prec))), S_ref, TOL_INV[prec])
+    assert _close(_np(plan.inv4(_dev(s, prec))), a_ref, TOL_INV[prec])
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
@@ -105,8 +115,8 @@ def test_cfg_n256_known_truth(prec):
     plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
     f = oracle.type2(x, c)
     A = oracle.type1(x, c)
-    assert oracle.rel_l2(_np(plan.inv5(_dev(f, prec))), c) <= TOL_INV[prec]
-    assert oracle.rel_l2(_np(plan.inv4(_dev(A, prec))), c) <= TOL_INV[prec]
+    assert _close(_np(plan.inv5(_dev(f, prec))), c, TOL_INV[prec])
+    assert _close(_np(plan.inv4(_dev(A, prec))), c, TOL_INV[prec])
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
@@ -260,8 +270,8 @@ def test_n65536_known_truth(prec):
     f = oracle.type2(x, c)
     A = oracle.type1(x, c)
     plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
-    assert oracle.rel_l2(_np(plan.inv5(_dev(f, prec))), c) <= TOL_INV[prec]
-    assert oracle.rel_l2(_np(plan.inv4(_dev(A, prec))), c) <= TOL_INV[prec]
+    assert _close(_np(plan.inv5(_dev(f, prec))), c, TOL_INV[prec])
+    assert _close(_np(plan.inv4(_dev(A, prec))), c, TOL_INV[prec])
     # batched right-hand sides as timed by the benchmark
     fb = np.stack([f, 1j * f, -f, 0.5 * f])
     Sb = _np(plan.inv5(_dev(fb, prec)))
@@ -290,9 +300,9 @@ def test_n131072_known_truth_float32():
     Sb = _np(plan.inv5(_dev(fb, FP32)))
     ab = _np(plan.inv4(_dev(Ab, FP32)))
     for b, sc in enumerate([1, -1j]):
-        assert oracle.rel_l2(Sb[b], sc * c) <= TOL_INV[FP32]
+        assert _close(Sb[b], sc * c, TOL_INV[FP32])
     for b, sc in enumerate([1, 2]):
-        assert oracle.rel_l2(ab[b], sc * c) <= TOL_INV[FP32]
+        assert _close(ab[b], sc * c, TOL_INV[FP32])
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])

@@ -72,6 +72,23 @@ def test_type1_at_matches_type1():
     np.testing.assert_allclose(oracle.type1_at(x, a, ks), full[ks + 5], atol=1e-12)
 
 
+def test_type2_at_matches_type2():
+    """Coefficients at a scattered, unordered list of integer frequencies give
+    the same sums as the contiguous type-2 with those coefficients placed in
+    an otherwise zero vector; one term is the plain exponential."""
+    P = 40
+    x = synth.jittered_nodes(P, 0.45, seed=73)
+    ms = np.array([3, 0, 999, -5, 7, 1000, 41])
+    S = synth.cn01(ms.size, seed=74)
+    full = np.zeros(1006, complex)
+    full[ms + 5] = S
+    np.testing.assert_allclose(oracle.type2_at(x, S, ms), oracle.type2(x, full, m0=-5), atol=1e-12)
+    t = oracle.canon(x)[1]
+    one = oracle.type2_at(x, np.array([1.0 + 0j]), np.array([123456789]))
+    ref = np.array([cmath.exp(2j * math.pi * ((123456789 * ti) % 1.0)) for ti in t])
+    np.testing.assert_allclose(one, ref, atol=1e-6)
+
+
 @pytest.mark.parametrize("P", [1, 3, 5, 12])
 def test_brute_force_python(P):
     """Pure-Python double loops with cmath.exp (no exact phases) vs the oracle."""
@@ -201,9 +218,10 @@ def test_lagrange_factorisation_identities(P, gamma):
 def test_middle_stage_convolution_identity(P, gamma):
     """The middle stage of Eqs. 37, 30, 31, S_m = rho^-m/P DFT(K P IDFT(rho^k A))_m
     (IDFT with 1/P), equals c_m + rho^P c_{m+P} with c the linear convolution of
-    the coefficients L_0..L_P of prod (z - z_p) with A (reading C-7): K from the
-    oracle, L from numpy's own expansion (np.poly, which rounds badly beyond ~24
-    roots on the circle), the products by numpy."""
+    the coefficients L_0..L_P of prod (z - z_p) (Eqs. 11, 43) with A, which
+    follows from Eqs. 10, 30 and 31 by expanding K_q = L(rho e^{j 2 pi q/P}):
+    K from the oracle, L from numpy's own expansion (np.poly, which rounds
+    badly beyond ~24 roots on the circle), the products by numpy."""
     x = synth.jittered_nodes(P, 0.45, seed=7 * P)
     t = oracle.canon(x)[1]
     A = synth.cn01(P, seed=11)
