@@ -314,6 +314,31 @@ nufft_status nufft_plan_set_batch_chunk(nufft_plan_t plan, int64_t chunk);
 nufft_status nufft_plan_export(nufft_plan_t plan, int which, void* dst, nufft_stream_t stream);
 
 /*
+ * nufft_plan_save / nufft_plan_restore -- no counterpart in the paper.  For
+ * reverse-mode differentiation, which needs the plan again in the backward
+ * pass: keep the two node-dependent quantities that cost the plan its FFTs,
+ * K_q = L(e^{j 2 pi (q/N + j a)}) (Eqs. 10, 29) and L'(z_p) (Sec. III-D), 32
+ * bytes per node, instead of the whole plan, and recompute the rest.
+ * nufft_plan_save copies them, as N complex128 values each (K in q order,
+ *   D in node order), into the device buffers K and D, asynchronously on
+ *   `stream`.  NUFFT_ERR_ARG for null or host pointers.
+ * nufft_plan_restore makes a plan for the nodes x from them: arguments as for
+ *   nufft_plan_ex, which must be those of the saved plan (same node values,
+ *   N, tol, precision and method parameters; pass the saved plan's gamma,
+ *   eta and widths from nufft_plan_info to be independent of the tuner's
+ *   cache), plus the saved K and D (device, read in stream order: they must
+ *   stay valid until the call's work on `stream` has run).  Only the node
+ *   geometry (exact turns, cell sort, extended node list, coincident-node
+ *   check), the node phases and the weights w_p of Eqs. 27/40 are computed;
+ *   the log-kernel type-1, the FFTs and the type-2 of the plan are skipped.
+ *   NUFFT_REFINE and NUFFT_DEFER_CHECK are accepted; NUFFT_TOEPLITZ is not
+ *   (NUFFT_ERR_ARG).  Results are those of the saved plan.
+ */
+nufft_status nufft_plan_save(nufft_plan_t plan, void* K, void* D, nufft_stream_t stream);
+nufft_status nufft_plan_restore(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                                const void* K, const void* D, nufft_stream_t stream, nufft_plan_t* plan);
+
+/*
  * nufft_plan_check -- no counterpart in the paper.  Waits for the plan's
  * kernels on its stream and returns NUFFT_ERR_DUP_NODES if two nodes coincide
  * modulo 2 pi (the inverse does not exist; results of the plan are not to be

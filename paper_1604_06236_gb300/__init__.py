@@ -83,6 +83,10 @@ def lib():
         L.nufft_plan_ex.restype = i32
         L.nufft_plan_tune.argtypes = [i64, vp, dbl, i32, i64, vp, ctypes.POINTER(Params), ctypes.POINTER(dbl)]
         L.nufft_plan_tune.restype = i32
+        L.nufft_plan_save.argtypes = [vp, vp, vp, vp]
+        L.nufft_plan_save.restype = i32
+        L.nufft_plan_restore.argtypes = [i64, vp, dbl, i32, ctypes.POINTER(Params), vp, vp, vp, ctypes.POINTER(vp)]
+        L.nufft_plan_restore.restype = i32
         for name in ("nufft_inv5", "nufft_inv4", "nufft_fwd1", "nufft_fwd2", "nufft_fwd2_deriv"):
             getattr(L, name).argtypes = [vp, vp, vp, i64, vp]
         L.nufft_destroy.argtypes = [vp]
@@ -179,7 +183,12 @@ class Plan:
     prec FP32: complex64 data, float64 node weights; prec FP64: complex128.
     """
 
-    def __init__(self, x, tol=None, prec=FP32, stream=None, gamma=None, eta=None, w_plan=None, w_solve=None):
+    def __init__(self, x, tol=None, prec=FP32, stream=None, gamma=None, eta=None, w_plan=None, w_solve=None,
+                 saved=None):
+        """saved: (K, D, params) from Plan.save() of a plan on the same node
+        values, tol and precision; the plan is then restored from them
+        (nufft_plan_restore: only the node geometry, phases and weights are
+        computed)."""
         import torch
         if not isinstance(x, torch.Tensor):
             x = torch.as_tensor(x)
@@ -193,7 +202,13 @@ class Plan:
         self.device = x.device if x.is_cuda else torch.device("cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
         self._x_keep = x
-        if gamma is None and eta is None and w_plan is None and w_solve is None:
+        if saved is not None:
+            K, D, prm = saved
+            self._saved_keep = (K, D)
+            q = Params(float(prm["gamma"]), int(prm["eta"]), int(prm["w_plan"]), int(prm["w_solve"]))
+            check(lib().nufft_plan_restore(self.N, _ptr(x), float(tol), int(prec), ctypes.byref(q), _ptr(K), _ptr(D),
+                                           _stream_handle(stream), ctypes.byref(self._h)))
+        elif gamma is None and eta is None and w_plan is None and w_solve is None:
             check(lib().nufft_plan(self.N, _ptr(x), float(tol), int(prec), _stream_handle(stream),
                                    ctypes.byref(self._h)))
         else:
@@ -225,6 +240,17 @@ class Plan:
         inf = PlanInfo()
         check(lib().nufft_plan_info(self._h, ctypes.byref(inf)))
         return inf.as_dict()
+
+    def save(self, stream=None):
+        """(K, D, params): the kernel samples K_q and the derivative samples
+        L'(z_p) as complex128 device tensors (nufft_plan_save, stream
+        ordered) and the method parameters, enough to restore the plan."""
+        import torch
+        K = torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        D = torch.empty_like(K)
+        check(lib().nufft_plan_save(self._h, _ptr(K), _ptr(D), _stream_handle(stream)))
+        inf = self.info()
+        return K, D, {k: inf[k] for k in ("gamma", "eta", "w_plan", "w_solve")}
 
     def export(self, which, stream=None):
         import torch

@@ -7,24 +7,29 @@ Backward, with G_{q,m} = e^{j 2 pi m t_q} (Eq. 48) and the type-4 matrix G^H
     inverse; grad_x from the derivative type-2 of S (library kernels);
   * type-4, a = G^{-H} A:  grad_A = G^{-1} grad_a, computed by the type-5
     inverse; grad_x from the derivative type-2 of grad_A.
-The plan (node geometry, kernel samples, weights) is rebuilt from the saved
-nodes in the backward pass instead of being kept alive between the passes.
+Between the passes only the kernel samples K_q (Eq. 29) and the derivative
+samples L'(z_p) (Sec. III-D) are kept, 32 bytes per node (Plan.save); the
+backward pass restores each plan from them and the saved nodes, recomputing
+the spreading geometry (exact turns, cell sort, extended node list), the
+node phases and the weights instead of storing them, and skipping the plan's
+log-kernel type-1, FFTs and type-2.
+
+Plans are made with the deferred coincident-node check: all of a pass's
+plans and transforms are queued before the host waits for the checks.
 
 Nodes x: float64 tensor of shape (N,) shared by every right-hand side, or
 (B, N) with one node set per instance (data then (B, N)).
 """
 import torch
 
-from . import FP32, FP64, Plan
+from . import DEFER_CHECK, FP32, FP64, Plan
 
 __all__ = ["inv5", "inv4"]
 
 
-def _plans(x, tol, prec):
+def _node_sets(x):
     xd = x.detach()
-    if xd.dim() == 1:
-        return [Plan(xd, tol=tol, prec=prec)]
-    return [Plan(xd[i], tol=tol, prec=prec) for i in range(xd.shape[0])]
+    return [xd] if xd.dim() == 1 else [xd[i] for i in range(xd.shape[0])]
 
 
 def _split(t, x):
@@ -34,33 +39,52 @@ def _split(t, x):
     return [t[i] for i in range(x.shape[0])]
 
 
+def _finish(plans):
+    """Wait for the plans' coincident-node checks, then release them."""
+    try:
+        for pl in plans:
+            pl.check()
+    finally:
+        for pl in plans:
+            pl.close()
+
+
 class _Inverse(torch.autograd.Function):
     @staticmethod
     def forward(ctx, data, x, kind, tol, prec):
-        plans = _plans(x, tol, prec)
-        outs = []
-        for pl, d in zip(plans, _split(data, x)):
-            outs.append(pl.inv5(d) if kind == 5 else pl.inv4(d))
-            pl.close()
+        plans, outs, saved = [], [], []
+        try:
+            for xi, d in zip(_node_sets(x), _split(data, x)):
+                pl = Plan(xi, tol=tol, prec=prec | DEFER_CHECK)
+                plans.append(pl)
+                outs.append(pl.inv5(d) if kind == 5 else pl.inv4(d))
+                saved.append(pl.save())
+        finally:
+            _finish(plans)
         out = outs[0] if x.dim() == 1 else torch.stack(outs)
-        ctx.save_for_backward(x, out)
-        ctx.kind, ctx.tol, ctx.prec = kind, tol, prec
+        ctx.save_for_backward(x, out, *[t for K, D, _ in saved for t in (K, D)])
+        ctx.params = [p for _, _, p in saved]
+        ctx.kind, ctx.tol, ctx.prec = kind, plans[0].tol, prec
         return out
 
     @staticmethod
     def backward(ctx, g):
-        x, out = ctx.saved_tensors
+        x, out, *kd = ctx.saved_tensors
         need_data, need_x = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        plans = _plans(x, ctx.tol, ctx.prec)
         g = g.contiguous().to(out.dtype)
-        gd, gx = [], []
-        for pl, gi, oi in zip(plans, _split(g, x), _split(out, x)):
-            # the dual inverse carries the gradient back to the data
-            gdi = pl.inv4(gi) if ctx.kind == 5 else pl.inv5(gi)
-            gd.append(gdi)
-            if need_x:
-                gx.append(pl.inv5_grad_nodes(gdi, oi) if ctx.kind == 5 else pl.inv4_grad_nodes(gdi, oi))
-            pl.close()
+        gd, gx, plans = [], [], []
+        try:
+            for i, (xi, gi, oi) in enumerate(zip(_node_sets(x), _split(g, x), _split(out, x))):
+                pl = Plan(xi, tol=ctx.tol, prec=ctx.prec | DEFER_CHECK,
+                          saved=(kd[2 * i], kd[2 * i + 1], ctx.params[i]))
+                plans.append(pl)
+                # the dual inverse carries the gradient back to the data
+                gdi = pl.inv4(gi) if ctx.kind == 5 else pl.inv5(gi)
+                gd.append(gdi)
+                if need_x:
+                    gx.append(pl.inv5_grad_nodes(gdi, oi) if ctx.kind == 5 else pl.inv4_grad_nodes(gdi, oi))
+        finally:
+            _finish(plans)
         grad_data = (gd[0] if x.dim() == 1 else torch.stack(gd)) if need_data else None
         grad_x = None
         if need_x:

@@ -415,7 +415,11 @@ int64_t per_item_elems(const nufft_plan_s* pl) {
     return pl->prm.ns + fft_work_elems(t.fft_ns) + pl->prm.N + fft_work_elems(t.fft_P);
 }
 
-nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
+// Ksv, Dsv: K_q and L'(z_p) saved from an earlier plan of the same nodes and
+// parameters (nufft_plan_restore): only the geometry, the node phases and the
+// weights are then computed
+nufft_status run_plan(nufft_plan_s* pl, const double* x_dev, const double2* Ksv = nullptr,
+                      const double2* Dsv = nullptr) {
     const Params& prm = pl->prm;
     const Tables& tab = *pl->tab;
     cudaStream_t s = pl->stream;
@@ -455,6 +459,42 @@ nufft_status run_plan(nufft_plan_s* pl, const double* x_dev) {
     pl->modm64_ext = m.take<double2>(2 * N);
     pl->modp64_srt = m.take<double2>(N);
     if (prm.toeplitz) pl->FL = m.take<char>(es * prm.ns);
+
+    if (Ksv) {
+        // restored plan: the saved K_q and L'(z_p), then the per-node work
+        Sizer zr;
+        const int64_t geo_ints = geometry_scratch_ints(N, prm.ns);
+        zr.add<int>(geo_ints);
+        zr.add<double2>((size_t)N);
+        zr.add<unsigned long long>(1);
+        Arena tmp;
+        if ((st = tmp.reserve(zr.used, s)) != NUFFT_OK) return st;
+        int* geo = tmp.take<int>(geo_ints);
+        double2* beta64 = tmp.take<double2>((size_t)N);
+        unsigned long long* sumT = tmp.take<unsigned long long>(1);
+        if ((st = build_geometry(gs, x_dev, pl->T, N, prm.ns, prm.halo, f32, geo, sumT, s)) != NUFFT_OK) {
+            tmp.release();
+            return st;
+        }
+        launch_node_phases(pl->T, gs, (uint64_t)prm.K0s, (uint64_t)P, 0, pl->modm64_ext, pl->modp64_srt, beta64,
+                           nullptr, s);
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->K64, Ksv, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->D64, Dsv, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+        if (f32) launch_to_solve<float>(pl->K64, P, 1.0, (float2*)pl->Ks, s);
+        else NUFFT_CUDA_TRY(cudaMemcpyAsync(pl->Ks, Ksv, sizeof(double2) * P, cudaMemcpyDeviceToDevice, s));
+        if (f32) {
+            launch_weights<float>(pl->T, gs, pl->D64, pl->modp64_srt, beta64, prm.rhoP, pl->w64,
+                                  (float2*)pl->wt2_srt, (float2*)pl->wt4_srt, (float2*)pl->wt1_ext,
+                                  (float2*)pl->wt5_ext, s);
+        } else {
+            launch_weights<double>(pl->T, gs, pl->D64, pl->modp64_srt, beta64, prm.rhoP, pl->w64,
+                                   (double2*)pl->wt2_srt, (double2*)pl->wt4_srt, (double2*)pl->wt1_ext,
+                                   (double2*)pl->wt5_ext, s);
+        }
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        tmp.release();
+        return NUFFT_OK;
+    }
 
     // temporaries of the plan
     const int eta = prm.eta;
@@ -978,8 +1018,34 @@ nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_
     return nufft_plan_ex(N, x, tol, prec, nullptr, stream, plan);
 }
 
+static nufft_status plan_impl(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                              nufft_stream_t stream, nufft_plan_t* plan, const double2* Ksv, const double2* Dsv);
+
 nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
                            nufft_stream_t stream, nufft_plan_t* plan) {
+    return plan_impl(N, x, tol, prec, params, stream, plan, nullptr, nullptr);
+}
+
+nufft_status nufft_plan_save(nufft_plan_t plan, void* K, void* D, nufft_stream_t stream) {
+    if (!plan || !K || !D) return fail(NUFFT_ERR_ARG, "null argument");
+    if (!is_device_ptr(K) || !is_device_ptr(D)) return fail(NUFFT_ERR_ARG, "nufft_plan_save needs device buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b = sizeof(double2) * (size_t)plan->prm.N;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(K, plan->K64, b, cudaMemcpyDeviceToDevice, s));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(D, plan->D64, b, cudaMemcpyDeviceToDevice, s));
+    return NUFFT_OK;
+}
+
+nufft_status nufft_plan_restore(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                                const void* K, const void* D, nufft_stream_t stream, nufft_plan_t* plan) {
+    if (!K || !D) return fail(NUFFT_ERR_ARG, "null saved-quantity pointer");
+    if (prec & NUFFT_TOEPLITZ) return fail(NUFFT_ERR_ARG, "nufft_plan_restore: NUFFT_TOEPLITZ plans cannot be restored");
+    if (!is_device_ptr(K) || !is_device_ptr(D)) return fail(NUFFT_ERR_ARG, "nufft_plan_restore needs device buffers");
+    return plan_impl(N, x, tol, prec, params, stream, plan, (const double2*)K, (const double2*)D);
+}
+
+static nufft_status plan_impl(int64_t N, const double* x, double tol, int prec, const nufft_params_t* params,
+                              nufft_stream_t stream, nufft_plan_t* plan, const double2* Ksv, const double2* Dsv) {
     if (!plan) return fail(NUFFT_ERR_ARG, "null plan output pointer");
     *plan = nullptr;
     if (N < 1 || N > ((int64_t)1 << 28)) return fail(NUFFT_ERR_ARG, "N = %lld out of range [1, 2^28]", (long long)N);
@@ -1039,7 +1105,7 @@ nufft_status nufft_plan_ex(int64_t N, const double* x, double tol, int prec, con
         if (cp != s && (st = order_after(s, cp)) != NUFFT_OK) { xs.release(); delete pl; return st; }
         xd = d;
     }
-    st = run_plan(pl, xd);
+    st = run_plan(pl, xd, Ksv, Dsv);
     xs.release_on(s);
     if (st == NUFFT_OK) st = plan_dup_queue(pl);
     if (st == NUFFT_OK && !defer) st = plan_dup_check(pl);

@@ -71,3 +71,20 @@ def test_argument_errors_without_device(L):
     r = ctypes.c_double()
     assert L.nufft_measure_fma(3, ctypes.byref(r), None) == 1
     assert L.nufft_measure_fma(1, None, None) == 1
+
+
+def test_save_restore_argument_errors_without_device(L):
+    x = (ctypes.c_double * 4)(0.0, 1.0, 2.0, 3.0)
+    xp = ctypes.cast(x, ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    L.nufft_plan_save.argtypes = [ctypes.c_void_p] * 4
+    L.nufft_plan_restore.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+    assert L.nufft_plan_save(None, xp, xp, None) == 1
+    # saved quantities missing
+    assert L.nufft_plan_restore(4, xp, 1e-5, 1, None, None, xp, None, ctypes.byref(h)) == 1
+    assert L.nufft_plan_restore(4, xp, 1e-5, 1, None, xp, None, None, ctypes.byref(h)) == 1
+    # convolution-form plans are not restorable
+    assert L.nufft_plan_restore(4, xp, 1e-5, 1 | 0x400, None, xp, xp, None, ctypes.byref(h)) == 1
+    assert b"TOEPLITZ" in L.nufft_last_error_message()

@@ -356,3 +356,31 @@ def test_toeplitz_avoids_rho_amplification():
     print(errs)
     assert errs["toeplitz"] <= TOL_INV[FP32]
     assert errs["toeplitz"] < errs["scaled"] / 3
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64, FP32 | pkg.REFINE])
+def test_restored_plan_matches_plan(prec):
+    """nufft_plan_restore from nufft_plan_save's K_q and L'(z_p): the node
+    geometry, phases and weights are recomputed, the rest is taken over; every
+    transform gives bit-identical results to the original plan, and a
+    restored plan of duplicate nodes still reports them."""
+    N = 3000
+    x = torch.from_numpy(synth.jittered_nodes(N, 0.45, seed=24)).cuda()
+    p0 = pkg.Plan(x, prec=prec)
+    K, D, prm = p0.save()
+    p1 = pkg.Plan(x, prec=prec, saved=(K, D, prm))
+    base = prec & 0xFF
+    data = synth.cn01((3, N), seed=25)
+    for op in ("inv5", "inv4", "fwd1", "fwd2"):
+        a = _np(getattr(p0, op)(_dev(data, base)))
+        b = _np(getattr(p1, op)(_dev(data, base)))
+        np.testing.assert_array_equal(a, b)
+    for which in (0, 1, 2):
+        np.testing.assert_array_equal(_np(p0.export(which)), _np(p1.export(which)))
+    xd = synth.jittered_nodes(100, 0.45, seed=15)
+    pd = pkg.Plan(torch.from_numpy(xd).cuda(), prec=FP64)
+    Kd, Dd, pr = pd.save()
+    xd[40] = xd[41]
+    with pytest.raises(pkg.NufftError) as e:
+        pkg.Plan(torch.from_numpy(xd).cuda(), prec=FP64, saved=(Kd, Dd, pr))
+    assert e.value.status == "NUFFT_ERR_DUP_NODES"
