@@ -15,7 +15,11 @@ node phases and the weights instead of storing them, and skipping the plan's
 log-kernel type-1, FFTs and type-2.
 
 Plans are made with the deferred coincident-node check: all of a pass's
-plans and transforms are queued before the host waits for the checks.
+plans and transforms are queued before the host waits for the checks.  With
+one node set per instance the instances are spread over a few CUDA streams
+(each instance's plan and transforms stay on one stream, ordered after the
+caller's stream and joined back into it), so that the plans, whose stages
+are latency-bound at one right-hand side, overlap.
 
 Nodes x: float64 tensor of shape (N,) shared by every right-hand side, or
 (B, N) with one node set per instance (data then (B, N)).
@@ -39,6 +43,35 @@ def _split(t, x):
     return [t[i] for i in range(x.shape[0])]
 
 
+_STREAMS = {}
+_NSTREAMS = 8
+
+
+def _lanes(device, count):
+    """The caller's stream alone for one instance, else a pool of side
+    streams of this device, each ordered after the caller's stream."""
+    main = torch.cuda.current_stream(device)
+    if count <= 1:
+        return main, [main]
+    pool = _STREAMS.get(device.index)
+    if pool is None:
+        pool = _STREAMS[device.index] = [torch.cuda.Stream(device) for _ in range(_NSTREAMS)]
+    lanes = pool[:min(count, len(pool))]
+    for s in lanes:
+        s.wait_stream(main)
+    return main, lanes
+
+
+def _join(main, lanes, tensors):
+    """Order the caller's stream after the side streams; tensors made on a
+    side stream are marked as used by the caller's stream."""
+    for s in lanes:
+        if s is not main:
+            main.wait_stream(s)
+    for t in tensors:
+        t.record_stream(main)
+
+
 def _finish(plans):
     """Wait for the plans' coincident-node checks, then release them."""
     try:
@@ -53,13 +86,18 @@ class _Inverse(torch.autograd.Function):
     @staticmethod
     def forward(ctx, data, x, kind, tol, prec):
         plans, outs, saved = [], [], []
+        sets = _node_sets(x)
+        main, lanes = _lanes(x.device, len(sets))
         try:
-            for xi, d in zip(_node_sets(x), _split(data, x)):
-                pl = Plan(xi, tol=tol, prec=prec | DEFER_CHECK)
-                plans.append(pl)
-                outs.append(pl.inv5(d) if kind == 5 else pl.inv4(d))
-                saved.append(pl.save())
+            for i, (xi, d) in enumerate(zip(sets, _split(data, x))):
+                s = lanes[i % len(lanes)]
+                with torch.cuda.stream(s):
+                    pl = Plan(xi, tol=tol, prec=prec | DEFER_CHECK, stream=s)
+                    plans.append(pl)
+                    outs.append(pl.inv5(d, stream=s) if kind == 5 else pl.inv4(d, stream=s))
+                    saved.append(pl.save(stream=s))
         finally:
+            _join(main, lanes, outs + [t for K, D, _ in saved for t in (K, D)])
             _finish(plans)
         out = outs[0] if x.dim() == 1 else torch.stack(outs)
         ctx.save_for_backward(x, out, *[t for K, D, _ in saved for t in (K, D)])
@@ -73,17 +111,23 @@ class _Inverse(torch.autograd.Function):
         need_data, need_x = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         g = g.contiguous().to(out.dtype)
         gd, gx, plans = [], [], []
+        sets = _node_sets(x)
+        main, lanes = _lanes(x.device, len(sets))
         try:
-            for i, (xi, gi, oi) in enumerate(zip(_node_sets(x), _split(g, x), _split(out, x))):
-                pl = Plan(xi, tol=ctx.tol, prec=ctx.prec | DEFER_CHECK,
-                          saved=(kd[2 * i], kd[2 * i + 1], ctx.params[i]))
-                plans.append(pl)
-                # the dual inverse carries the gradient back to the data
-                gdi = pl.inv4(gi) if ctx.kind == 5 else pl.inv5(gi)
-                gd.append(gdi)
-                if need_x:
-                    gx.append(pl.inv5_grad_nodes(gdi, oi) if ctx.kind == 5 else pl.inv4_grad_nodes(gdi, oi))
+            for i, (xi, gi, oi) in enumerate(zip(sets, _split(g, x), _split(out, x))):
+                s = lanes[i % len(lanes)]
+                with torch.cuda.stream(s):
+                    pl = Plan(xi, tol=ctx.tol, prec=ctx.prec | DEFER_CHECK, stream=s,
+                              saved=(kd[2 * i], kd[2 * i + 1], ctx.params[i]))
+                    plans.append(pl)
+                    # the dual inverse carries the gradient back to the data
+                    gdi = pl.inv4(gi, stream=s) if ctx.kind == 5 else pl.inv5(gi, stream=s)
+                    gd.append(gdi)
+                    if need_x:
+                        gx.append(pl.inv5_grad_nodes(gdi, oi, stream=s) if ctx.kind == 5
+                                  else pl.inv4_grad_nodes(gdi, oi, stream=s))
         finally:
+            _join(main, lanes, gd + gx)
             _finish(plans)
         grad_data = (gd[0] if x.dim() == 1 else torch.stack(gd)) if need_data else None
         grad_x = None

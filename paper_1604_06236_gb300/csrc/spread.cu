@@ -291,6 +291,337 @@ __global__ void __launch_bounds__(kTB) k_spread(int64_t n, int w, T two_over_w, 
     }
 }
 
+// ---- float32 spread for many right-hand sides (tiled, pipelined) ----------
+// One CTA per tile of kTB grid points, all right-hand sides.  The nodes of
+// the tile's window (extended slots t0 .. t1, at most one per thread) are
+// read once: each thread tabulates the w kernel values of its node,
+// ph[e][m] = phi(m + 1 - w/2 - frac_e) (grid point cell_e + 1 - w/2 + m).
+// The samples of a chunk of BC right-hand sides at those nodes are gathered
+// into a two-stage ring by cp.async while the previous chunk is summed; once
+// a chunk has landed, its node's thread multiplies it by the slot weight, and
+// each grid point then sums ph x strength over the nodes of its window in
+// registers and is written once per right-hand side.  Tiles whose window
+// holds more than kTB nodes (dense clusters) take the window in pieces,
+// without the ring.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+struct TileSmem {
+    float* ph;      // [kTB][w]
+    float2* ring;   // [2][BC][kTB]
+    float2* wt;     // [kTB]
+    int* cell;      // [kTB]
+};
+
+// node e = threadIdx.x of the piece [c0, c0 + cnt): cell, slot weight and the
+// w kernel values; returns its node index (the sample column), -1 if none
+__device__ __forceinline__ int tile_tabulate(const TileSmem& sm, int c0, int cnt, int w, float two_over_w, float beta,
+                                             const int* __restrict__ eperm, const int* __restrict__ ecell,
+                                             const float* __restrict__ efrac, const float2* __restrict__ wt) {
+    const int e = threadIdx.x;
+    if (e >= cnt) return -1;
+    const int h = w / 2;
+    sm.cell[e] = ecell[c0 + e];
+    sm.wt[e] = wt[c0 + e];
+    const float f = efrac[c0 + e];
+    float* ph = sm.ph + e * w;
+    for (int m = 0; m < w; ++m) ph[m] = es_kernel<float>((float)(m + 1 - h) - f, two_over_w, beta);
+    return eperm[c0 + e];
+}
+
+// this thread's node's samples of right-hand sides [bc BC, bc BC + BC) into
+// ring stage st (one commit group per thread, possibly empty)
+template <int BC>
+__device__ __forceinline__ void tile_gather(const TileSmem& sm, int bc, int st, int p,
+                                            const float2* __restrict__ src, int64_t src_bs, int64_t batch) {
+    if (p >= 0) {
+        float2* dst = sm.ring + st * BC * kTB + threadIdx.x;
+        const int64_t b0 = (int64_t)bc * BC;
+        const float2* sp = src + b0 * src_bs + p;
+        const int nb = (int)min((int64_t)BC, batch - b0);
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+            if (b < nb) cp_async8(dst + b * kTB, sp + b * src_bs);
+    }
+    cp_async_commit();
+}
+
+// x slot weight, in place (the thread's own node column)
+template <int BC>
+__device__ __forceinline__ void tile_weight(const TileSmem& sm, int st, int p) {
+    if (p < 0) return;
+    float2* col = sm.ring + st * BC * kTB + threadIdx.x;
+    const float2 wv = sm.wt[threadIdx.x];
+#pragma unroll
+    for (int b = 0; b < BC; ++b) col[b * kTB] = cmul(col[b * kTB], wv);
+}
+
+template <int BC>
+__device__ __forceinline__ void tile_accumulate(const TileSmem& sm, float2* acc, int st, int c0, int a, int z,
+                                                int64_t g, int w) {
+    const float2* sv = sm.ring + st * BC * kTB;
+    const int h = w / 2;
+    for (int i = a; i < z; ++i) {
+        const int e = i - c0;
+        const float k = sm.ph[e * w + (int)(g - sm.cell[e]) - 1 + h];
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            const float2 v = sv[b * kTB + e];
+            acc[b].x = fmaf(k, v.x, acc[b].x);
+            acc[b].y = fmaf(k, v.y, acc[b].y);
+        }
+    }
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two_over_w, float beta,
+                                                     const int* __restrict__ cstart, const int* __restrict__ eperm,
+                                                     const int* __restrict__ ecell, const float* __restrict__ efrac,
+                                                     const float2* __restrict__ src, int64_t src_bs,
+                                                     const float2* __restrict__ wt, float2* __restrict__ grid,
+                                                     int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem sm;
+    sm.ring = reinterpret_cast<float2*>(smem_raw);
+    sm.wt = sm.ring + 2 * BC * kTB;
+    sm.ph = reinterpret_cast<float*>(sm.wt + kTB);
+    sm.cell = reinterpret_cast<int*>(sm.ph + kTB * w);
+    const int64_t g0 = (int64_t)blockIdx.x * kTB;
+    const int64_t g = g0 + threadIdx.x;
+    const int64_t glast = min(g0 + (int64_t)kTB, n) - 1;
+    const int t0 = cstart[g0], t1 = cstart[glast + w];
+    int lo = 0, hi = 0;
+    if (g < n) { lo = cstart[g]; hi = cstart[g + w]; }
+    const int nchunks = (int)((batch + BC - 1) / BC);
+    const int cnt_all = t1 - t0;
+    float2* out = grid + g;
+    float2 acc[BC];
+    if (cnt_all <= kTB) {
+        const int p = tile_tabulate(sm, t0, cnt_all, w, two_over_w, beta, eperm, ecell, efrac, wt);
+        tile_gather<BC>(sm, 0, 0, p, src, src_bs, batch);
+        for (int bc = 0; bc < nchunks; ++bc) {
+            const int st = bc & 1;
+            if (bc + 1 < nchunks) {
+                tile_gather<BC>(sm, bc + 1, st ^ 1, p, src, src_bs, batch);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            tile_weight<BC>(sm, st, p);   // the thread's own copies: no barrier needed before
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < BC; ++b) acc[b] = make_float2(0.f, 0.f);
+            tile_accumulate<BC>(sm, acc, st, t0, lo, hi, g, w);
+            if (g < n) {
+                const int nb = (int)min((int64_t)BC, batch - (int64_t)bc * BC);
+                float2* o = out + (int64_t)bc * BC * n;
+#pragma unroll
+                for (int b = 0; b < BC; ++b)
+                    if (b < nb) o[b * n] = acc[b];
+            }
+            __syncthreads();   // stage st is refilled by the next iteration's gather
+        }
+        return;
+    }
+    // dense window: pieces of kTB nodes, one chunk of right-hand sides at a time
+    for (int bc = 0; bc < nchunks; ++bc) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b) acc[b] = make_float2(0.f, 0.f);
+        for (int c0 = t0; c0 < t1; c0 += kTB) {
+            const int cnt = min(kTB, t1 - c0);
+            __syncthreads();
+            const int p = tile_tabulate(sm, c0, cnt, w, two_over_w, beta, eperm, ecell, efrac, wt);
+            tile_gather<BC>(sm, bc, 0, p, src, src_bs, batch);
+            cp_async_wait<0>();
+            tile_weight<BC>(sm, 0, p);
+            __syncthreads();
+            tile_accumulate<BC>(sm, acc, 0, c0, max(lo, c0), min(hi, c0 + cnt), g, w);
+        }
+        if (g < n) {
+            const int nb = (int)min((int64_t)BC, batch - (int64_t)bc * BC);
+            float2* o = out + (int64_t)bc * BC * n;
+#pragma unroll
+            for (int b = 0; b < BC; ++b)
+                if (b < nb) o[b * n] = acc[b];
+        }
+    }
+}
+
+inline size_t spread_tile_smem(int w, int BC) {
+    return 2 * (size_t)BC * kTB * sizeof(float2) + (size_t)kTB * sizeof(float2) + (size_t)kTB * w * sizeof(float) +
+           (size_t)kTB * sizeof(int);
+}
+
+// ---- float32 interpolation for many right-hand sides (tiled, pipelined) ---
+// One CTA per tile of kInterpNodes sorted slots, all right-hand sides, two
+// threads per node (each sums half of a chunk's right-hand sides).  Each
+// thread forms the w kernel values of its node once.  The tile's nodes read
+// the grid window [cell_first + 1 - w/2, cell_last + w/2] (periodic); for a
+// chunk of BC right-hand sides that window is copied into a two-stage ring
+// by cp.async while the previous chunk is summed, then every node sums its w
+// taps from shared memory and writes dst[b][perm] = sum x wt.  Windows
+// longer than kInterpWin points (tiles spanning a sparse stretch of nodes)
+// are read from global memory directly.
+constexpr int kInterpNodes = 128;
+constexpr int kInterpTB = 2 * kInterpNodes;
+constexpr int kInterpWin = 384;   // window points per right-hand side
+constexpr int kInterpRow = kInterpWin + 2;   // (+2 of slack for the pair alignment)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+// the window of right-hand sides [bc BC, bc BC + BC) into ring stage st: pairs
+// (grid indices wsa + 2k, +1, modulo n: n even, so a pair never straddles the
+// wrap) or single points (ws + k mod n)
+template <int BC>
+__device__ __forceinline__ void gather_window(float2* ring, int bc, int st, bool pairs, int npair, int Li, int64_t wsa,
+                                              int64_t ws, int64_t n, const float2* __restrict__ grid, int64_t batch) {
+    float2* d = ring + st * BC * kInterpRow;
+    const int64_t b0 = (int64_t)bc * BC;
+    const int nb = (int)min((int64_t)BC, batch - b0);
+    const float2* gb = grid + b0 * n;
+    if (pairs) {
+        for (int k = threadIdx.x; k < npair; k += kInterpTB) {
+            int64_t gi = wsa + 2 * k;
+            if (gi >= n) gi -= n;
+#pragma unroll
+            for (int b = 0; b < BC; ++b)
+                if (b < nb) cp_async16(&d[b * kInterpRow + 2 * k], gb + b * n + gi);
+        }
+    } else {
+        for (int k = threadIdx.x; k < Li; k += kInterpTB) {
+            int64_t gi = ws + k;
+            if (gi >= n) gi -= n;
+#pragma unroll
+            for (int b = 0; b < BC; ++b)
+                if (b < nb) cp_async8(&d[b * kInterpRow + k], gb + b * n + gi);
+        }
+    }
+    cp_async_commit();
+}
+
+template <int BC>
+__global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n, int w, float two_over_w,
+                                                           float beta, const int* __restrict__ sperm,
+                                                           const int* __restrict__ scell,
+                                                           const float* __restrict__ sfrac,
+                                                           const float2* __restrict__ grid,
+                                                           const float2* __restrict__ wt, float2* __restrict__ dst,
+                                                           int64_t dst_bs, int64_t batch) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int HB = BC / 2;   // right-hand sides per thread and chunk
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* ring = reinterpret_cast<float2*>(smem_raw);   // [2][BC][kInterpRow]
+    const int node = threadIdx.x % kInterpNodes, half = threadIdx.x / kInterpNodes;
+    const int64_t i0 = (int64_t)blockIdx.x * kInterpNodes;
+    const int64_t i = i0 + node;
+    const int64_t ilast = min(i0 + (int64_t)kInterpNodes, N) - 1;
+    const int h = w / 2;
+    const int64_t wa = (int64_t)scell[i0] + 1 - h;            // window start (may be < 0: periodic)
+    const int64_t L = (int64_t)scell[ilast] + h - wa + 1;     // window length
+    const bool live = i < N;
+    float ker[16];
+    int base = 0;
+    int c = 0;
+    if (live) {
+        c = scell[i];
+        const float f = sfrac[i];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<float>((float)(m + 1 - h) - f, two_over_w, beta) : 0.f;
+        base = (int)(c + 1 - h - wa);
+    }
+    const int p = live ? sperm[i] : 0;
+    const float2 wv = live ? wt[i] : make_float2(0.f, 0.f);
+    const int nchunks = (int)((batch + BC - 1) / BC);
+    float2 acc[HB];
+    if (L <= kInterpWin) {
+        int64_t ws = wa % n;
+        if (ws < 0) ws += n;
+        const bool pairs = (n & 1) == 0;
+        const int s0 = pairs ? (int)(ws & 1) : 0;
+        const int64_t wsa = ws - s0;
+        const int npair = (int)((L + s0 + 1) / 2);
+        const int Li = (int)L;
+        gather_window<BC>(ring, 0, 0, pairs, npair, Li, wsa, ws, n, grid, batch);
+        for (int bc = 0; bc < nchunks; ++bc) {
+            const int st = bc & 1;
+            if (bc + 1 < nchunks) {
+                gather_window<BC>(ring, bc + 1, st ^ 1, pairs, npair, Li, wsa, ws, n, grid, batch);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float2* win = ring + st * BC * kInterpRow + half * HB * kInterpRow + s0 + base;
+#pragma unroll
+            for (int b = 0; b < HB; ++b) acc[b] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                if (m < w) {
+#pragma unroll
+                    for (int b = 0; b < HB; ++b) {
+                        const float2 v = win[b * kInterpRow + m];
+                        acc[b].x = fmaf(ker[m], v.x, acc[b].x);
+                        acc[b].y = fmaf(ker[m], v.y, acc[b].y);
+                    }
+                }
+            }
+            if (live) {
+                const int64_t b0 = (int64_t)bc * BC + half * HB;
+                float2* o = dst + b0 * dst_bs + p;
+#pragma unroll
+                for (int b = 0; b < HB; ++b)
+                    if (b0 + b < batch) o[b * dst_bs] = cmul(acc[b], wv);
+            }
+            __syncthreads();   // stage st is refilled by the next iteration's gather
+        }
+        return;
+    }
+    // long window: direct gathers
+    if (!live) return;
+    int64_t g_first = (int64_t)c + 1 - h;
+    if (g_first < 0) g_first += n;
+    for (int bc = 0; bc < nchunks; ++bc) {
+        const int64_t b0 = (int64_t)bc * BC + half * HB;
+#pragma unroll
+        for (int b = 0; b < HB; ++b) acc[b] = make_float2(0.f, 0.f);
+        int64_t gi = g_first;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            if (m < w) {
+#pragma unroll
+                for (int b = 0; b < HB; ++b) {
+                    if (b0 + b < batch) {
+                        const float2 v = grid[(b0 + b) * n + gi];
+                        acc[b].x = fmaf(ker[m], v.x, acc[b].x);
+                        acc[b].y = fmaf(ker[m], v.y, acc[b].y);
+                    }
+                }
+                if (++gi == n) gi = 0;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < HB; ++b)
+            if (b0 + b < batch) dst[(b0 + b) * dst_bs + p] = cmul(acc[b], wv);
+    }
+}
+
+inline size_t interp_tile_smem(int BC) { return 2 * (size_t)BC * kInterpRow * sizeof(float2); }
+
+
 __constant__ float2 c_exp2_64[64] = NUFFT_EXP2_64_TABLE;
 
 // The float64 spread with the kernel values and the accumulation in
@@ -749,6 +1080,16 @@ void launch_spread(const Geometry& g, KernelShape ks, const c2<T>* src, int64_t 
         dim3 gr(nblk(g.n), (unsigned)((batch + 7) / 8));
         launch_k(k_spread<T, 8>, gr, kTB, 0, s, g.n, ks.w, tow, beta, cs, g.ext_perm, g.ext_cell, ef, src, src_bs,
                                           wt_ext, grid, batch);
+    } else if (src) {
+        // one CTA per tile of grid points for every right-hand side: the
+        // kernel values are formed once per tile and the sample gathers of
+        // the next chunk of right-hand sides overlap this chunk's sums
+        constexpr int BC = 8;
+        const size_t sm = spread_tile_smem(ks.w, BC);
+        cudaFuncSetAttribute(k_spread_tile<BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        launch_k(k_spread_tile<BC>, dim3(nblk(g.n)), kTB, sm, s, g.n, ks.w, (float)tow, (float)beta, cs, g.ext_perm,
+                 g.ext_cell, (const float*)ef, (const float2*)src, src_bs, (const float2*)wt_ext, (float2*)grid,
+                 batch);
     } else {
         // 16 right-hand sides per block row: each kernel value serves twice as many
         dim3 gr(nblk(g.n), (unsigned)((batch + 15) / 16));
@@ -773,10 +1114,15 @@ void launch_interp(const Geometry& g, KernelShape ks, const c2<T>* grid, const c
         launch_k(k_interp<T, 4>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
                                           dst_bs, batch);
     } else {
-        // 8 right-hand sides per block row: each kernel value serves twice as many
-        dim3 gr(nblk(g.N), (unsigned)((batch + 7) / 8));
-        launch_k(k_interp<T, 8>, gr, kTB, 0, s, g.N, g.n, ks.w, tow, beta, g.srt_perm, g.srt_cell, sf, grid, wt_srt, dst,
-                                          dst_bs, batch);
+        // one CTA per tile of sorted nodes for every right-hand side: kernel
+        // values once per node, the grid window of the next chunk of
+        // right-hand sides copied while this chunk is summed
+        constexpr int BC = 8;
+        const size_t sm = interp_tile_smem(BC);
+        cudaFuncSetAttribute(k_interp_tile<BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        launch_k(k_interp_tile<BC>, dim3(nblk(g.N, kInterpNodes)), kInterpTB, sm, s, g.N, g.n, ks.w, (float)tow,
+                 (float)beta, g.srt_perm, g.srt_cell, (const float*)sf, (const float2*)grid, (const float2*)wt_srt,
+                 (float2*)dst, dst_bs, batch);
     }
 }
 

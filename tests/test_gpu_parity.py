@@ -272,14 +272,16 @@ def test_n65536_known_truth(prec):
     plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
     assert _close(_np(plan.inv5(_dev(f, prec))), c, TOL_INV[prec])
     assert _close(_np(plan.inv4(_dev(A, prec))), c, TOL_INV[prec])
-    # batched right-hand sides as timed by the benchmark
-    fb = np.stack([f, 1j * f, -f, 0.5 * f])
+    # batched right-hand sides as timed by the benchmark (more than one chunk
+    # of the many-right-hand-side kernels, ragged)
+    scales = [1, 1j, -1, 0.5, 2j, -0.25, 1 + 1j, 3, -2j, 0.125, 1 - 1j, -4, 0.75]
+    fb = np.stack([sc * f for sc in scales])
     Sb = _np(plan.inv5(_dev(fb, prec)))
-    for b, sc in enumerate([1, 1j, -1, 0.5]):
+    for b, sc in enumerate(scales):
         assert oracle.rel_l2(Sb[b], sc * c) <= TOL_INV[prec]
-    Ab = np.stack([A, -1j * A, 2 * A])
+    Ab = np.stack([sc * A for sc in scales[:11]])
     ab = _np(plan.inv4(_dev(Ab, prec)))
-    for b, sc in enumerate([1, -1j, 2]):
+    for b, sc in enumerate(scales[:11]):
         assert oracle.rel_l2(ab[b], sc * c) <= TOL_INV[prec]
 
 
@@ -384,3 +386,41 @@ def test_restored_plan_matches_plan(prec):
     with pytest.raises(pkg.NufftError) as e:
         pkg.Plan(torch.from_numpy(xd).cuda(), prec=FP64, saved=(Kd, Dd, pr))
     assert e.value.status == "NUFFT_ERR_DUP_NODES"
+
+
+def _mixed_density_nodes(N, seed):
+    """Half of the nodes packed into [0, 0.05) turns (about 5 per grid cell of
+    the transforms' grid), the other half spread over [0.05, 1) (about 0.28
+    per cell): the packed stretch overflows the node window of a spreading
+    tile, the sparse one the grid window of an interpolation tile."""
+    g = synth.rng(seed)
+    t = np.concatenate([g.uniform(0.0, 0.05, N // 2), g.uniform(0.05, 1.0, N - N // 2)])
+    return 2 * np.pi * g.permutation(t)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("nodes", ["jittered", "mixed"])
+def test_many_right_hand_sides(prec, nodes):
+    """20 right-hand sides (several chunks of the many-right-hand-side spread
+    and interpolation kernels, the last one ragged): the forward transforms
+    against exact-phase direct sums, element by element; on the jittered nodes
+    also the inverses against Gaussian elimination."""
+    N, B = 4096, 20
+    x = synth.jittered_nodes(N, 0.45, seed=26) if nodes == "jittered" else _mixed_density_nodes(N, 27)
+    data = synth.cn01((B, N), seed=28)
+    plan = pkg.Plan(torch.from_numpy(x).cuda(), prec=prec)
+    dr = _rounded(data, prec)
+    A = _np(plan.fwd1(_dev(data, prec)))
+    f = _np(plan.fwd2(_dev(data, prec)))
+    for b in range(B):
+        assert _close(A[b], oracle.type1(x, dr[b]), TOL_FWD[prec]), b
+        assert _close(f[b], oracle.type2(x, dr[b]), TOL_FWD[prec]), b
+    if nodes == "jittered":
+        S = _np(plan.inv5(_dev(data, prec)))
+        a = _np(plan.inv4(_dev(data, prec)))
+        G = oracle.matrix(x)
+        Sref = np.linalg.solve(G, dr.T).T
+        aref = np.linalg.solve(G.conj().T, dr.T).T
+        for b in range(B):
+            assert _close(S[b], Sref[b], TOL_INV[prec]), b
+            assert _close(a[b], aref[b], TOL_INV[prec]), b
