@@ -1,8 +1,9 @@
 """Error of the type-4 method against the attenuation mu of Eq. 49 (Sec. VI,
 Figs. 1 and 2), with the method's parameters set explicitly (nufft_plan_ex).
 
-Setup of Sec. VI: P = 1024 nodes t_p = (p + u)/P with one shift u ~ U[0, 0.6)
-per trial, complex Gaussian amplitudes of variance one, spectra A(k) by
+Setup of Sec. VI: P = 1024 nodes t_p = (p + u_p)/P, a regular grid whose
+elements are shifted independently by u_p ~ U[0, 0.6), complex Gaussian
+amplitudes of variance one, spectra A(k) by
 exact-phase direct sums (oracle), the float64 path (widths 16).  For each
 eta the attenuation is swept through gamma = e^{2 pi P a} and the lowest
 mean error over the sweep is compared with the levels the paper quotes: about
@@ -12,8 +13,10 @@ eta = 1.  The figures' data are not given, so these are loose checks: the
 lowest error must not be more than 10 dB above the quoted level (this
 implementation, with exact-phase arithmetic, measures about 20 dB below it),
 and in the truncation regime the error must follow mu with the slope of Eq.
-49 (error ~ P mu, i.e. 60 dB above mu at P = 1024).  The full curves come
-from `bench.py --workload error_model`."""
+49 (error ~ P mu, i.e. 60 dB above mu at P = 1024).  Fig. 3: the refined
+method at eta = 1, with mu chosen per P to minimise the error, against
+Gaussian elimination for P from 64 to 4096.  The full curves come from
+`bench.py --workload error_model`."""
 import numpy as np
 import pytest
 
@@ -33,16 +36,18 @@ def _db(e):
     return 20.0 * np.log10(e)
 
 
-def _mu(gamma, eta):
+def _mu(gamma, eta, P=P):
     a = np.log(gamma) / (2 * np.pi * P)
     return np.exp(-2 * np.pi * (eta * P - 1) * a) / (eta * P - 1)
 
 
-def _cases():
+def _cases(P=P, trials=TRIALS, seed0=500):
+    """Sec. VI Monte Carlo trials: every node of the regular grid of spacing
+    1/P shifted by its own U[0, 0.6/P], CN(0,1) amplitudes, exact spectra."""
     out = []
-    for t in range(TRIALS):
-        g = synth.rng(500 + t)
-        u = g.uniform(0.0, 0.6)
+    for t in range(trials):
+        g = synth.rng(seed0 + t)
+        u = g.uniform(0.0, 0.6, size=P)
         x = 2 * np.pi * (np.arange(P) + u) / P
         a = synth.cn01(P, generator=g)
         out.append((x, a, oracle.type1(x, a, M=P)))
@@ -99,3 +104,19 @@ def test_refined_eta1_reaches_elimination_level(cases):
     x, a, A = cases[0]
     ge = np.linalg.norm(oracle.inv4(x, A) - a) / np.linalg.norm(a)
     assert _db(errs.min()) <= _db(ge) + 20.0, (_db(errs.min()), _db(ge))
+
+
+@pytest.mark.parametrize("Pn", [64, 256, 1024, 4096])
+def test_refined_eta1_error_vs_P(Pn):
+    """Fig. 3: the refined method (R-NFFT, Eqs. 44-46) at eta = 1 with mu
+    chosen per P to minimise the round-off error reaches the Gaussian
+    elimination level (here: within 20 dB of the oracle's LU on the same
+    trials) for every P."""
+    cs = _cases(Pn, TRIALS, 700 + Pn)
+    gammas = 10.0 ** np.arange(1.0, 9.01, 0.5)
+    errs = _curve(cs, 1, gammas, pkg.FP64 | pkg.REFINE)
+    ge = float(np.mean([np.linalg.norm(oracle.inv4(x, A) - a) / np.linalg.norm(a) for x, a, A in cs]))
+    i = int(np.argmin(errs))
+    print("P=%d refined eta=1: lowest %.1f dB at mu %.1f dB; GE %.1f dB"
+          % (Pn, _db(errs[i]), _db(_mu(gammas[i], 1, Pn)), _db(ge)))
+    assert _db(errs[i]) <= _db(ge) + 20.0, (_db(errs[i]), _db(ge))
