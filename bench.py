@@ -668,7 +668,8 @@ def measure_batched(args, dev, clocks):
         "workload": "batched: %d independent type-5/type-4 instances, N log-uniform in [64,16384] (sum N = %d), "
                     "own nodes u~U(-0.4,0.4), complex64, plan + inverse per instance per step, one persistent "
                     "launch replayed from a CUDA graph" % (count, n_pts),
-        "autotuned": {"ctas": ctas, "threads": threads, "max_fft_radix": radix, "tune_ms": tune_ms},
+        "autotuned": {"ctas": ctas, "threads": threads, "max_fft_radix": radix, "tune_ms": tune_ms,
+                      "method_params": b.params()},
         "gpu_launches": int(per_replay) * steps, "instances_flagged": int((st != 0).sum()),
         "rel_l2_vs_oracle": {"instances_checked": len(checked), "max": max(e[0] for e in errs),
                              "median": float(np.median([e[0] for e in errs])),

@@ -246,11 +246,14 @@ nufft_status nufft_destroy(nufft_plan_t plan);
  * persistent kernel launch (the paper has no counterpart: each instance is
  * the method of Secs. III/IV, Figs. 1 and 2).  Each instance has its own
  * nodes, size N (2 <= N <= 16384) and kind; data are complex64 and the
- * node-dependent part is computed in float64 as in NUFFT_FP32 plans
- * (gamma = 60, eta = 4, spreading widths 14 (plan) and 8 (transforms);
- * relative L2 error ~1e-6 on well-conditioned nodes).  The whole pipeline
- * (plan and inverse) runs on every nufft_batch_run, so new node values in the
- * same buffers are picked up.
+ * node-dependent part is computed to float64 accuracy as in NUFFT_FP32 plans.
+ * The method's parameters follow tol (Sec. V): gamma = 60, the smallest eta
+ * (at most 4) whose truncation 0.4 gamma^-eta is below tol/10, spreading
+ * widths 14 (plan; 12 for tol >= 1e-4) and 8 (transforms; 6 for tol >= 1e-3);
+ * at tol 1e-5 that is eta = 4 (relative L2 error ~1e-6 on well-conditioned
+ * nodes).  nufft_batch_tune may replace them by a faster set it validated.
+ * The whole pipeline (plan and inverse) runs on every nufft_batch_run, so new
+ * node values in the same buffers are picked up.
  * nufft_batch_create: `inst` is a host array of `count` descriptors of device
  *   buffers; the buffers must stay valid while the batch is used.  Allocates
  *   the descriptors, per-CTA scratch and deconvolution tables (synchronises
@@ -274,12 +277,21 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
 nufft_status nufft_batch_run(nufft_batch_t batch, nufft_stream_t stream);
 nufft_status nufft_batch_status(nufft_batch_t batch, int* status, nufft_stream_t stream);
 /* Autotuner: runs the batch under every launch shape (1-3 CTAs per SM, 256 or
- * 512 threads, largest FFT radix 4 or 8), keeps the fastest (reported in
- * *best_ms when not NULL) and caches it per (count, sum of N, largest N) for
- * later batches of the same shape.  Synchronises; run it before capturing. */
+ * 512 threads, largest FFT radix 4 or 8) and keeps the fastest; then runs it
+ * with candidate method parameters (gamma, eta, plan width, transforms'
+ * width; Sec. V leaves the choice open) whose a-priori error fits tol --
+ * truncation 0.4 gamma^-eta within tol/10, the transforms' round-off
+ * 0.5 gamma 2^-24 within tol/2 -- and accepts a set only if every instance's
+ * result stays within tol/2 (relative L2) of the result with the tightest set
+ * (gamma 60, eta 4, widths 14 and 8); the fastest accepted set is kept.  The
+ * best time goes to *best_ms when not NULL; choices are cached per (count,
+ * sum of N, largest N, tol) for later batches of the same shape.  Overwrites
+ * the outputs; synchronises; run it before capturing. */
 nufft_status nufft_batch_tune(nufft_batch_t batch, nufft_stream_t stream, double* best_ms);
 /* The launch shape in use: CTAs, threads per CTA, largest FFT radix. */
 nufft_status nufft_batch_config(nufft_batch_t batch, int* ctas, int* threads, int* max_radix);
+/* The method's parameters in use (gamma, eta, plan width, transforms' width). */
+nufft_status nufft_batch_params(nufft_batch_t batch, nufft_params_t* params);
 nufft_status nufft_batch_destroy(nufft_batch_t batch);
 
 /* Parameters a plan chose (Sec. V).  rho = e^{-2 pi a}; gamma = rho^{-N}. */

@@ -98,6 +98,8 @@ def lib():
         L.nufft_batch_destroy.argtypes = [vp]
         L.nufft_batch_tune.argtypes = [vp, vp, ctypes.POINTER(dbl)]
         L.nufft_batch_config.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.nufft_batch_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.nufft_batch_params.restype = i32
         for name in ("nufft_batch_create", "nufft_batch_run", "nufft_batch_status", "nufft_batch_destroy",
                      "nufft_batch_tune", "nufft_batch_config"):
             getattr(L, name).restype = i32
@@ -347,6 +349,12 @@ class Batch:
         c, t, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(lib().nufft_batch_config(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(r)))
         return ms.value, c.value, t.value, r.value
+
+    def params(self):
+        """The method's parameters in use: gamma, eta, w_plan, w_solve (Sec. V)."""
+        q = Params()
+        check(lib().nufft_batch_params(self._h, ctypes.byref(q)))
+        return {"gamma": q.gamma, "eta": q.eta, "w_plan": q.w_plan, "w_solve": q.w_solve}
 
     def status(self, stream=None):
         import torch

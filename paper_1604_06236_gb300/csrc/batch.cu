@@ -21,6 +21,7 @@
 #include "fft_p2.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -31,9 +32,8 @@ namespace nufft45 {
 namespace {
 
 constexpr int kMaxLog = 16;                 // largest power-of-two FFT inside: 2^16
-constexpr int kEta = 4;                     // log-kernel oversampling (Sec. V)
-constexpr double kGamma = 60.0;             // rho^-N (Sec. V, float32 transforms)
-constexpr int kWPlan = 14, kWSolve = 8;     // spreading widths (float64 plan, float32 transforms)
+constexpr int kMaxEta = 4;                  // largest log-kernel oversampling (Sec. V)
+constexpr int kMaxW = 16;                   // largest spreading width
 
 struct Desc {
     int64_t N;
@@ -61,6 +61,10 @@ struct Args {
     const float* dec_solve;  // 1/phihat (transforms' width)
     double beta_plan, beta_solve;
     int max_rl;              // largest FFT radix inside: 2^max_rl (2 or 3)
+    // the method's parameters (Sec. V): gamma = rho^-N, eta <= kMaxEta, the
+    // spreading widths of the float64-class plan and of the float32 transforms
+    double gamma;
+    int eta, w_plan, w_solve;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -218,8 +222,9 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         const int ns = 1 << d.log_ns;
         const int64_t M = (int64_t)1 << d.log_m;
         const int64_t K0 = N / 2;
-        const double log_rho = -log(kGamma) / (double)N;
-        const double rhoN = 1.0 / kGamma;
+        const int eta = a.eta, w_plan = a.w_plan, w_solve = a.w_solve;
+        const double log_rho = -log(a.gamma) / (double)N;
+        const double rhoN = 1.0 / a.gamma;
         const double* dec_p = a.dec_plan + d.tab;
         const float* dec_s = a.dec_solve + d.tab;
         // ---- scratch layout
@@ -232,8 +237,8 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
         int* start = carve<int>(p, ns + 1);
         double2* modm = carve<double2>(p, N);
         double2* modp = carve<double2>(p, N);
-        cdd* str = carve<cdd>(p, (size_t)kEta * N);    // log-kernel strengths (double-float)
-        cdd* G = carve<cdd>(p, (size_t)kEta * ns);
+        cdd* str = carve<cdd>(p, (size_t)eta * N);    // log-kernel strengths (double-float)
+        cdd* G = carve<cdd>(p, (size_t)eta * ns);
         cdd* GW = carve<cdd>(p, (size_t)ns);
         cdd* v64 = carve<cdd>(p, M);
         cdd* w64v = carve<cdd>(p, M);
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             // beta = e^{-j 2 pi N t}, in double-float
             cdd sv = to_cdd(mm);
             const cdd bt = to_cdd(cis_turns_t((uint64_t)N * t, -1));
-            for (int r = 0; r < kEta; ++r) {
+            for (int r = 0; r < eta; ++r) {
                 str[(int64_t)r * N + i] = sv;
                 sv = cmul(sv, bt);
             }
@@ -349,31 +354,34 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
 
         // ---- log-kernel spectrum: eta type-1s of length N on the grid
         // (double-float kernel values and sums)
-        const float hp = 0.5f * (float)kWPlan;
+        const float hp = 0.5f * (float)w_plan;
         const dd beta_p(a.beta_plan);
         for (int g = tid; g < ns; g += nt) {
-            cdd acc[kEta];
+            cdd acc[kMaxEta];
 #pragma unroll
-            for (int r = 0; r < kEta; ++r) acc[r] = mk<dd>(0, 0);
-            for (int j = 0; j < kWPlan; ++j) {
-                const int cu = g - kWPlan / 2 + j;                  // unwrapped cell
+            for (int r = 0; r < kMaxEta; ++r) acc[r] = mk<dd>(0, 0);
+            for (int j = 0; j < w_plan; ++j) {
+                const int cu = g - w_plan / 2 + j;                  // unwrapped cell
                 const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
                 for (int i = start[cw]; i < start[cw + 1]; ++i) {
                     const int q = perm[i];
                     const dd ph = es_kernel_dd(dd((float)(g - cu), 0.f) - fracd[q], hp, beta_p, s_exp);
 #pragma unroll
-                    for (int r = 0; r < kEta; ++r) {
-                        const cdd sv = str[(int64_t)r * N + q];
-                        acc[r].x += ph * sv.x;
-                        acc[r].y += ph * sv.y;
+                    for (int r = 0; r < kMaxEta; ++r) {
+                        if (r < eta) {
+                            const cdd sv = str[(int64_t)r * N + q];
+                            acc[r].x += ph * sv.x;
+                            acc[r].y += ph * sv.y;
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int r = 0; r < kEta; ++r) G[(int64_t)r * ns + g] = acc[r];
+            for (int r = 0; r < kMaxEta; ++r)
+                if (r < eta) G[(int64_t)r * ns + g] = acc[r];
         }
         __syncthreads();
-        for (int r = 0; r < kEta; ++r) {
+        for (int r = 0; r < eta; ++r) {
             cdd* res = cta_fft<dd>(G + (int64_t)r * ns, GW, d.log_ns, -1, a.twdd, a.max_rl);
             if (res != G + (int64_t)r * ns)
                 for (int g = tid; g < ns; g += nt) G[(int64_t)r * ns + g] = res[g];
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
             const double rm = exp((double)m * log_rho);
             cdd acc = mk<dd>(0, 0);
             double gr = 1.0;
-            for (int r = 0; r < kEta; ++r, gr *= rhoN) {
+            for (int r = 0; r < eta; ++r, gr *= rhoN) {
                 const int64_t k = N * r + m;
                 if (k == 0) continue;
                 const dd lam = dd_from_double(-gr * rm / (double)k * dec);
@@ -442,10 +450,10 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 const int c = cell[i];
                 const dd fdd = fracd[i];
                 cdd acc = mk<dd>(0, 0);
-                for (int m = 0; m < kWPlan; ++m) {
-                    int gi = c + 1 - kWPlan / 2 + m;
+                for (int m = 0; m < w_plan; ++m) {
+                    int gi = c + 1 - w_plan / 2 + m;
                     gi = gi < 0 ? gi + ns : (gi >= ns ? gi - ns : gi);
-                    const dd ph = es_kernel_dd(dd((float)(m + 1 - kWPlan / 2), 0.f) - fdd, hp, beta_p, s_exp);
+                    const dd ph = es_kernel_dd(dd((float)(m + 1 - w_plan / 2), 0.f) - fdd, hp, beta_p, s_exp);
                     const cdd gv = gsp[gi];
                     acc.x += ph * gv.x;
                     acc.y += ph * gv.y;
@@ -467,15 +475,15 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
 
         // ---- the float32 inverse (its scalings rho^{+-k} in float32: |k log rho|
         // <= log gamma, so expf is accurate to a few float32 ulp)
-        const float tow_s = 2.0f / kWSolve;
+        const float tow_s = 2.0f / (float)w_solve;
         const float beta_s = (float)a.beta_solve;
         const float lr = (float)log_rho, invN = 1.0f / (float)N;
         if (d.kind == 5) {
             // a_p = s_p w_p e^{-j 2 pi K0 t_p}: type-1 (gather), FFT, deconvolve x rho^k
             for (int g = tid; g < ns; g += nt) {
                 float2 acc = make_float2(0.f, 0.f);
-                for (int j = 0; j < kWSolve; ++j) {
-                    const int cu = g - kWSolve / 2 + j;
+                for (int j = 0; j < w_solve; ++j) {
+                    const int cu = g - w_solve / 2 + j;
                     const int cw = cu < 0 ? cu + ns : (cu >= ns ? cu - ns : cu);
                     for (int i = start[cw]; i < start[cw + 1]; ++i) {
                         const int q = perm[i];
@@ -523,10 +531,10 @@ __global__ void __launch_bounds__(512) k_batch(Args a) {
                 const int c = cell[i];
                 const float f = fracf[i];
                 float2 acc = make_float2(0.f, 0.f);
-                for (int m = 0; m < kWSolve; ++m) {
-                    int gi = c + 1 - kWSolve / 2 + m;
+                for (int m = 0; m < w_solve; ++m) {
+                    int gi = c + 1 - w_solve / 2 + m;
                     gi = gi < 0 ? gi + ns : (gi >= ns ? gi - ns : gi);
-                    const float ph = es_kernel<float>((float)(m + 1 - kWSolve / 2) - f, tow_s, beta_s);
+                    const float ph = es_kernel<float>((float)(m + 1 - w_solve / 2) - f, tow_s, beta_s);
                     acc.x = fmaf(ph, gsp[gi].x, acc.x);
                     acc.y = fmaf(ph, gsp[gi].y, acc.y);
                 }
@@ -546,12 +554,49 @@ __global__ void k_twiddle_table(int logn, cdd* tdd, float2* t32) {
     t32[i] = make_float2((float)c, (float)s);
 }
 
+// the tuner's accuracy check: copy every instance's output into one buffer
+// (ref[off[i] ..]) or compare it with that copy, recording the largest
+// per-instance relative L2 difference (a positive float's bits order like it)
+__global__ void k_batch_outputs(const Desc* __restrict__ desc, int count, const int64_t* __restrict__ off,
+                                float2* __restrict__ ref, int compare, unsigned* __restrict__ worst) {
+    __shared__ double s_num[32], s_den[32];
+    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+        const Desc d = desc[it];
+        float2* r = ref + off[it];
+        double num = 0.0, den = 0.0;
+        for (int64_t i = threadIdx.x; i < d.N; i += blockDim.x) {
+            const float2 o = d.out[i];
+            if (!compare) {
+                r[i] = o;
+            } else {
+                const double dx = (double)o.x - r[i].x, dy = (double)o.y - r[i].y;
+                num += dx * dx + dy * dy;
+                den += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
+            }
+        }
+        if (!compare) continue;
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_down_sync(0xffffffffu, num, o);
+            den += __shfl_down_sync(0xffffffffu, den, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_num[threadIdx.x >> 5] = num; s_den[threadIdx.x >> 5] = den; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_num[w]; b += s_den[w]; }
+            const float rel = b > 0.0 ? (float)sqrt(a / b) : (a > 0.0 ? 1e30f : 0.f);
+            atomicMax(worst, __float_as_uint(rel));
+        }
+        __syncthreads();
+    }
+}
+
 size_t scratch_bytes(int64_t N, int log_ns, int log_m) {
     const size_t ns = (size_t)1 << log_ns, M = (size_t)1 << log_m;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     size_t s = 0;
     s += al(8 * N) + al(4 * N) + al(8 * N) + al(4 * N) + 2 * al(4 * (ns + 1));
-    s += 2 * al(16 * N) + al(16 * kEta * N) + al(16 * kEta * ns) + al(16 * ns);
+    s += 2 * al(16 * N) + al(16 * kMaxEta * N) + al(16 * kMaxEta * ns) + al(16 * ns);
     s += 2 * al(16 * M) + 2 * al(16 * N) + al(16 * N) + 3 * al(16 * M);
     s += al(8 * N) + 3 * al(8 * M) + 2 * al(8 * N) + 2 * al(8 * ns) + 2 * al(8 * M);
     s += al(8 * N) + al(4 * N);   // node fractions in double-float and float32
@@ -585,12 +630,62 @@ struct nufft_batch_s {
     size_t scratch_cap = 0;          // CTAs the scratch slab can hold
     double tol = 0;
     int64_t key_total = 0, key_max = 0;
+    // the method's parameters (Sec. V) and the deconvolution tables of the widths
+    double gamma = 60.0;
+    int eta = 4, w_plan = 14, w_solve = 8;
+    std::map<int, int64_t> tab_off;  // log2 grid -> offset in the tables
+    int64_t tab_total = 0;
+    int tab_w_plan = 0, tab_w_solve = 0;
+    int64_t* out_off = nullptr;      // device: first output slot of each descriptor in a packed copy
+    int64_t total_n = 0;
 };
 
 namespace {
-// autotuner cache: (count, sum N, max N) -> (CTAs, threads, radix)
+// autotuner cache: (count, sum N, max N, tol) -> (CTAs, threads, radix, gamma, eta, w_plan, w_solve)
+struct TuneChoice {
+    int grid, threads, max_rl;
+    double gamma;
+    int eta, w_plan, w_solve;
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int64_t, int64_t>, std::tuple<int, int, int>> g_tune;
+std::map<std::tuple<int64_t, int64_t, int64_t, double>, TuneChoice> g_tune;
+
+// Sec. V, Eq. 49: the truncation of the log-kernel series leaves about
+// 0.4 gamma^-eta (measured law); the float32 transforms' round-off grows with
+// gamma (their rho^{+-k} scalings), about 0.5 gamma 2^-24.
+double batch_trunc(double gamma, int eta) { return 0.4 * std::pow(gamma, -eta); }
+double batch_roundoff(double gamma) { return 0.5 * gamma * 5.96e-8; }
+
+// default parameters for tol: gamma = 60 with the smallest eta that puts the
+// truncation below tol/10, plan width 14 below tol 1e-4 (12 above), width 8
+// for the transforms below tol 1e-3 (6 above)
+void batch_default_params(double tol, nufft_batch_s* b) {
+    b->gamma = 60.0;
+    int eta = 1;
+    while (eta < kMaxEta && batch_trunc(b->gamma, eta) > tol / 10) ++eta;
+    b->eta = eta;
+    b->w_plan = tol < 1e-4 ? 14 : 12;
+    b->w_solve = tol < 1e-3 ? 8 : 6;
+}
+
+// deconvolution tables (1/phihat per grid, centred index) for the current widths
+nufft_status batch_tables(nufft_batch_s* b, cudaStream_t s) {
+    if (b->tab_w_plan == b->w_plan && b->tab_w_solve == b->w_solve) return NUFFT_OK;
+    GLRule glp, gls;
+    gauss_legendre_half(2 + (3 * b->w_plan) / 2 + 4, glp);
+    gauss_legendre_half(2 + (3 * b->w_solve) / 2 + 4, gls);
+    for (auto& kv : b->tab_off) {
+        const int64_t ns = (int64_t)1 << kv.first;
+        launch_table(KernelShape{b->w_plan, 2.30 * b->w_plan}, glp, ns, ns / 2, ns, 0.0, 0, ns,
+                     b->dec_plan + kv.second, nullptr, s);
+        launch_table(KernelShape{b->w_solve, 2.30 * b->w_solve}, gls, ns, ns / 2, ns, 0.0, 0, ns, nullptr,
+                     b->dec_solve + kv.second, s);
+    }
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    b->tab_w_plan = b->w_plan;
+    b->tab_w_solve = b->w_solve;
+    return NUFFT_OK;
+}
 }
 
 extern "C" {
@@ -623,6 +718,8 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     std::map<int, int64_t> tab_off;   // log_ns -> table offset
     int64_t tab_total = 0;
     size_t scratch = 0;
+    std::vector<int64_t> off(count);   // packed output offsets, descriptor order
+    int64_t total_n = 0;
     for (int64_t i = 0; i < count; ++i) {
         const nufft_instance_t& q = inst[order[i]];
         Desc& d = h[i];
@@ -631,13 +728,15 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
         d.in = (const float2*)q.in;
         d.out = (float2*)q.out;
         d.kind = q.kind;
-        d.log_ns = std::max(ceil_log2(2 * q.N), ceil_log2(2 * kWPlan));
+        d.log_ns = std::max(ceil_log2(2 * q.N), ceil_log2(2 * kMaxW));
         d.pow2 = (q.N & (q.N - 1)) == 0;
         d.log_m = d.pow2 ? ceil_log2(q.N) : ceil_log2(2 * q.N - 1);
         d.slot = order[i];
         if (!tab_off.count(d.log_ns)) { tab_off[d.log_ns] = tab_total; tab_total += (int64_t)1 << d.log_ns; }
         d.tab = tab_off[d.log_ns];
         scratch = std::max(scratch, scratch_bytes(d.N, d.log_ns, d.log_m));
+        off[i] = total_n;
+        total_n += q.N;
     }
     nufft_batch_s* b = new nufft_batch_s();
     b->count = (int)count;
@@ -654,10 +753,18 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     for (int64_t i = 0; i < count; ++i) { tot += inst[i].N; mx = std::max<int64_t>(mx, inst[i].N); }
     b->key_total = tot;
     b->key_max = mx;
+    b->total_n = total_n;
+    b->tab_off = tab_off;
+    b->tab_total = tab_total;
+    batch_default_params(tol, b);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune.find(std::make_tuple((int64_t)count, tot, mx));
-        if (it != g_tune.end()) std::tie(b->grid, b->threads, b->max_rl) = it->second;
+        auto it = g_tune.find(std::make_tuple((int64_t)count, tot, mx, tol));
+        if (it != g_tune.end()) {
+            const TuneChoice& c = it->second;
+            b->grid = c.grid; b->threads = c.threads; b->max_rl = c.max_rl;
+            b->gamma = c.gamma; b->eta = c.eta; b->w_plan = c.w_plan; b->w_solve = c.w_solve;
+        }
     }
     auto cleanup = [&](nufft_status st) { nufft_batch_destroy(b); return st; };
     cudaError_t e;
@@ -669,22 +776,19 @@ nufft_status nufft_batch_create(int64_t count, const nufft_instance_t* inst, dou
     if ((e = cudaMalloc(&b->tw32, sizeof(float2) << kMaxLog)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->dec_plan, sizeof(double) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMalloc(&b->dec_solve, sizeof(float) * tab_total)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+    if ((e = cudaMalloc(&b->out_off, sizeof(int64_t) * count)) != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
     if ((e = cudaMemcpyAsync(b->desc, h.data(), sizeof(Desc) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
+    if ((e = cudaMemcpyAsync(b->out_off, off.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cleanup(cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__));
     {
         Launch L(s, K_PLAN_TABLE, 24.0 * (1 << kMaxLog));
         k_twiddle_table<<<(1 << kMaxLog) / 256, 256, 0, s>>>(kMaxLog, b->twdd, b->tw32);
     }
     // deconvolution tables per grid, indexed by the centred index k' + ns/2
-    GLRule glp, gls;
-    gauss_legendre_half(2 + (3 * kWPlan) / 2 + 4, glp);
-    gauss_legendre_half(2 + (3 * kWSolve) / 2 + 4, gls);
-    for (auto& kv : tab_off) {
-        const int64_t ns = (int64_t)1 << kv.first;
-        launch_table(KernelShape{kWPlan, 2.30 * kWPlan}, glp, ns, ns / 2, ns, 0.0, 0, ns, b->dec_plan + kv.second,
-                     nullptr, s);
-        launch_table(KernelShape{kWSolve, 2.30 * kWSolve}, gls, ns, ns / 2, ns, 0.0, 0, ns, nullptr,
-                     b->dec_solve + kv.second, s);
+    {
+        nufft_status ts = batch_tables(b, s);
+        if (ts != NUFFT_OK) return cleanup(ts);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(cuda_fail(e, "table launch", __FILE__, __LINE__));
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(cuda_fail(e, "batch set-up", __FILE__, __LINE__));
@@ -708,9 +812,15 @@ nufft_status nufft_batch_run(nufft_batch_t b, nufft_stream_t stream) {
     a.tw32 = b->tw32;
     a.dec_plan = b->dec_plan;
     a.dec_solve = b->dec_solve;
-    a.beta_plan = 2.30 * kWPlan;
-    a.beta_solve = 2.30 * kWSolve;
+    a.beta_plan = 2.30 * b->w_plan;
+    a.beta_solve = 2.30 * b->w_solve;
     a.max_rl = b->max_rl;
+    a.gamma = b->gamma;
+    a.eta = b->eta;
+    a.w_plan = b->w_plan;
+    a.w_solve = b->w_solve;
+    if (b->tab_w_plan != b->w_plan || b->tab_w_solve != b->w_solve)
+        return fail(NUFFT_ERR_ARG, "batch tables do not match its widths");
     {
         Launch L(s, K_PLAN_STAGE, 0.0);
         k_batch<<<b->grid, b->threads, 0, s>>>(a);
@@ -719,18 +829,34 @@ nufft_status nufft_batch_run(nufft_batch_t b, nufft_stream_t stream) {
     return NUFFT_OK;
 }
 
-// Autotuner: times every (CTAs per SM, threads per CTA, largest FFT radix)
-// candidate on this batch with CUDA events and keeps the fastest; the choice
-// is cached per (count, sum N, max N) for later batches of the same shape.
+// Autotuner.  First the launch shape: every (CTAs per SM, threads per CTA,
+// largest FFT radix) candidate is timed with CUDA events at the current
+// parameters.  Then the method's parameters (Sec. V): candidate sets
+// (gamma, eta, plan width, transforms' width) whose a-priori error --
+// truncation 0.4 gamma^-eta (Eq. 49's law) within tol/10 and round-off
+// 0.5 gamma 2^-24 within tol/2 -- qualifies are run on this batch; a set is
+// accepted when every instance's output stays within tol/2 (relative L2) of
+// the output of the tightest set (gamma 60, eta 4, widths 14 and 8), and the
+// fastest accepted set is kept.  Choices are cached per (count, sum N,
+// max N, tol).  The batch's outputs are overwritten.
 nufft_status nufft_batch_tune(nufft_batch_t b, nufft_stream_t stream, double* best_ms) {
     if (!b) return fail(NUFFT_ERR_ARG, "null batch");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     NUFFT_CUDA_TRY(cudaEventCreate(&e0));
     NUFFT_CUDA_TRY(cudaEventCreate(&e1));
-    const int keep_g = b->grid, keep_t = b->threads, keep_r = b->max_rl;
+    auto time_run = [&](float* ms) -> nufft_status {
+        nufft_status st = nufft_batch_run(b, stream);   // warm
+        if (st != NUFFT_OK) return st;
+        cudaEventRecord(e0, s);
+        if ((st = nufft_batch_run(b, stream)) != NUFFT_OK) return st;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tuner", __FILE__, __LINE__);
+        cudaEventElapsedTime(ms, e0, e1);
+        return NUFFT_OK;
+    };
     float best = 1e30f;
-    int bg = keep_g, bt = keep_t, br = keep_r;
+    int bg = b->grid, bt = b->threads, br = b->max_rl;
     nufft_status st = NUFFT_OK;
     for (int per_sm = 1; per_sm <= 3 && st == NUFFT_OK; ++per_sm)
         for (int th : {256, 512})
@@ -738,26 +864,78 @@ nufft_status nufft_batch_tune(nufft_batch_t b, nufft_stream_t stream, double* be
                 b->grid = b->sms * per_sm;
                 b->threads = th;
                 b->max_rl = rl;
-                if ((st = nufft_batch_run(b, stream)) != NUFFT_OK) break;   // warm
-                cudaEventRecord(e0, s);
-                if ((st = nufft_batch_run(b, stream)) != NUFFT_OK) break;
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
+                if ((st = time_run(&ms)) != NUFFT_OK) break;
                 if (ms < best) { best = ms; bg = b->grid; bt = th; br = rl; }
             }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->grid = bg;
     b->threads = bt;
     b->max_rl = br;
+    // the method's parameters, validated on this batch against the tightest set
+    struct Cand { double gamma; int eta, w_plan, w_solve; };
+    const Cand ref{60.0, 4, 14, 8};
+    const Cand cands[] = {{100.0, 3, 12, 8}, {100.0, 3, 10, 8}, {60.0, 4, 12, 8}, {30.0, 4, 12, 8},
+                          {60.0, 3, 12, 8}, {300.0, 2, 12, 8}, {100.0, 2, 12, 8}, {100.0, 3, 12, 6}};
+    const Cand keep{b->gamma, b->eta, b->w_plan, b->w_solve};
+    float2* refout = nullptr;
+    unsigned* worst = nullptr;
+    Cand bestc = keep;
+    if (st == NUFFT_OK) {
+        cudaError_t ce = cudaMalloc(&refout, sizeof(float2) * (size_t)b->total_n);
+        if (ce == cudaSuccess) ce = cudaMalloc(&worst, sizeof(unsigned));
+        if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMalloc", __FILE__, __LINE__);
+    }
+    auto set = [&](const Cand& c) -> nufft_status {
+        b->gamma = c.gamma; b->eta = c.eta; b->w_plan = c.w_plan; b->w_solve = c.w_solve;
+        return batch_tables(b, s);
+    };
+    if (st == NUFFT_OK && (st = set(ref)) == NUFFT_OK) {
+        float ms = 0.f;
+        if ((st = time_run(&ms)) == NUFFT_OK) {
+            k_batch_outputs<<<std::min(b->count, 4 * b->sms), 256, 0, s>>>(b->desc, b->count, b->out_off, refout, 0,
+                                                                           worst);
+            best = ms;
+            bestc = ref;
+        }
+    }
+    for (const Cand& c : cands) {
+        if (st != NUFFT_OK) break;
+        if (batch_trunc(c.gamma, c.eta) > b->tol / 10 || batch_roundoff(c.gamma) > b->tol / 2) continue;
+        if (c.w_solve < 8 && b->tol < 1e-3) continue;
+        if ((st = set(c)) != NUFFT_OK) break;
+        float ms = 0.f;
+        if ((st = time_run(&ms)) != NUFFT_OK) break;
+        unsigned w = 0;
+        cudaMemsetAsync(worst, 0, sizeof(unsigned), s);
+        k_batch_outputs<<<std::min(b->count, 4 * b->sms), 256, 0, s>>>(b->desc, b->count, b->out_off, refout, 1, worst);
+        cudaMemcpyAsync(&w, worst, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "tuner", __FILE__, __LINE__); break; }
+        float rel = 0.f;
+        std::memcpy(&rel, &w, sizeof(rel));
+        if (rel <= b->tol / 2 && ms < best) { best = ms; bestc = c; }
+    }
+    cudaFree(refout);
+    cudaFree(worst);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    nufft_status st2 = set(st == NUFFT_OK ? bestc : keep);
     if (st != NUFFT_OK) return st;
+    if (st2 != NUFFT_OK) return st2;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[std::make_tuple((int64_t)b->count, b->key_total, b->key_max)] = std::make_tuple(bg, bt, br);
+        g_tune[std::make_tuple((int64_t)b->count, b->key_total, b->key_max, b->tol)] =
+            TuneChoice{b->grid, b->threads, b->max_rl, b->gamma, b->eta, b->w_plan, b->w_solve};
     }
     if (best_ms) *best_ms = best;
+    return NUFFT_OK;
+}
+
+nufft_status nufft_batch_params(nufft_batch_t b, nufft_params_t* params) {
+    if (!b || !params) return fail(NUFFT_ERR_ARG, "null argument");
+    params->gamma = b->gamma;
+    params->eta = b->eta;
+    params->w_plan = b->w_plan;
+    params->w_solve = b->w_solve;
     return NUFFT_OK;
 }
 
@@ -787,6 +965,7 @@ nufft_status nufft_batch_destroy(nufft_batch_t b) {
     cudaFree(b->tw32);
     cudaFree(b->dec_plan);
     cudaFree(b->dec_solve);
+    cudaFree(b->out_off);
     delete b;
     return NUFFT_OK;
 }

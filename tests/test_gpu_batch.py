@@ -149,3 +149,35 @@ def test_benchmarked_4096_instance_workload():
             rms = np.linalg.norm(truth[i]) / np.sqrt(truth[i].size)
             assert np.abs(o - truth[i]).max() <= 30 * TOL * rms, (i, int(sizes[i]))
     print("4096-instance batch: worst rel-L2 over %d checked instances %.3e" % (len(truth), worst))
+
+
+def test_batch_parameters_follow_tol():
+    """The method's parameters follow tol (Sec. V): at 1e-5 the tightest set
+    (gamma 60, eta 4, widths 14 and 8); at 1e-3 a smaller eta and narrower
+    widths, and the results still meet that tolerance against the oracle."""
+    items, truth = _instances([300, 4096, 100, 2000, 777, 64], seed=13)
+    b = pkg.Batch(items, tol=1e-5)
+    assert b.params() == {"gamma": 60.0, "eta": 4, "w_plan": 14, "w_solve": 8}
+    b3 = pkg.Batch(items, tol=1e-3)
+    p3 = b3.params()
+    assert p3["eta"] < 4 and p3["w_plan"] == 12 and p3["w_solve"] == 6, p3
+    outs = b3.run()
+    torch.cuda.synchronize()
+    for o, c in zip(outs, truth):
+        assert oracle.rel_l2(o.cpu().numpy().astype(np.complex128), c) <= 1e-3
+
+
+def test_tuned_parameters_validated():
+    """nufft_batch_tune keeps a parameter set only after checking it against
+    the tightest set on the batch itself; the tuned batch meets tol against
+    the oracle."""
+    items, truth = _instances([5000, 300, 4096, 100, 2000, 777, 16384, 1000], seed=14)
+    b = pkg.Batch(items, tol=1e-5)
+    b.tune()
+    p = b.params()
+    assert 0.4 * p["gamma"] ** (-p["eta"]) <= 1e-6 and p["w_solve"] == 8, p
+    outs = b.run()
+    torch.cuda.synchronize()
+    for o, c in zip(outs, truth):
+        assert oracle.rel_l2(o.cpu().numpy().astype(np.complex128), c) <= TOL
+    print("tuned batch parameters:", p)
