@@ -21,9 +21,10 @@ path's (1e-5), the error of a benchmarked right-hand side of each kind against
 known truth from the oracle's exact-phase direct sums, end-to-end throughput
 from pinned host buffers, per-kernel-class times and the dominant kernel's
 roofline, and the other configurations, each with its own clock record and
-oracle error: 4096 uneven instances in one persistent launch under a CUDA
-graph, N = 2^20 with clustered nodes (plain and refined), and forward +
-backward at N = 262144 for 64 instances.  The CPU baseline is the float64
+oracle error: N = 256 in float64 with 1 and 1024 right-hand sides, 4096
+uneven instances in one persistent launch under a CUDA graph, N = 2^20 with
+clustered nodes (plain and refined), and forward + backward at N = 262144
+for 64 instances.  The CPU baseline is the float64
 oracle on this host's cores.
 
 `--impl reference` times the float64 CPU oracle (dense matrix by exact-phase
@@ -553,6 +554,7 @@ def run_gpu(args):
         # ---- the other configurations, each with its own clock record
         if not args.no_side:
             result["configs"] = {
+                "small_256_fp64": measure_small(args, dev, clocks),
                 "batched_4096": measure_batched(args, dev, clocks),
                 "clustered_2p20": measure_clustered(args, dev, clocks),
                 "autograd_262144": measure_autograd(args, dev, clocks),
@@ -791,6 +793,68 @@ def measure_autograd(args, dev, clocks):
     }
 
 
+def measure_small(args, dev, clocks):
+    """The N = 256 configuration: nodes x_k = 2 pi (k + u_k)/N, u_k ~ U(-0.3, 0.3)
+    (seed 0), float64 path at tol 1e-10, type-5 and type-4 inverses with 1 and
+    with 1024 right-hand sides, plan + solve (new plan every step) and solve
+    only; errors against Gaussian elimination (the oracle's LU) and known
+    truth."""
+    import torch
+    import oracle
+    import synth
+    import paper_1604_06236_gb300 as pkg
+    oracle.build()
+    stream = torch.cuda.current_stream()
+    N = 256
+    g = synth.rng(0)
+    xn = synth.jittered_nodes(N, 0.3, generator=g)
+    c = synth.cn01(N, generator=g)
+    f_true = oracle.type2(xn, c)
+    A_true = oracle.type1(xn, c)
+    x = torch.from_numpy(xn).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    t0 = time.perf_counter()
+    for B in (1, 1024):
+        f = torch.from_numpy(np.tile(f_true, (B, 1))).to(dev)
+        A = torch.from_numpy(np.tile(A_true, (B, 1))).to(dev)
+        S = torch.empty_like(f)
+        a = torch.empty_like(A)
+
+        def step(i):
+            p = pkg.Plan(x, prec=pkg.FP64 | pkg.DEFER_CHECK)
+            p.inv5(f, out=S)
+            p.inv4(A, out=a)
+            p.check()
+            p.close()
+        ms = _timed_steps(step, args.steps, args.warmup, stream, flush)
+        p = pkg.Plan(x, prec=pkg.FP64)
+
+        def solve(i):
+            p.inv5(f, out=S)
+            p.inv4(A, out=a)
+        ms_s = _timed_steps(solve, args.steps, args.warmup, stream, flush)
+        e5 = max(_rel_max(S[b].cpu().numpy(), c)[0] for b in (0, B - 1))
+        e4 = max(_rel_max(a[b].cpu().numpy(), c)[0] for b in (0, B - 1))
+        p.close()
+        out["batch_%d" % B] = {"plan_and_solve": {"value": 2 * B / (ms / args.steps / 1e3), "ms_per_step": ms / args.steps},
+                               "solve_only": {"value": 2 * B / (ms_s / args.steps / 1e3), "ms_per_step": ms_s / args.steps},
+                               "rel_l2_vs_oracle": {"inv5": e5, "inv4": e4}}
+    t1 = time.perf_counter()
+    lu5 = oracle.rel_l2(oracle.inv5(xn, f_true), c)
+    lu4 = oracle.rel_l2(oracle.inv4(xn, A_true), c)
+    return {
+        "value": out["batch_1024"]["plan_and_solve"]["value"], "unit": "transforms/s", "dtype": "f64",
+        "ms_per_step": out["batch_1024"]["plan_and_solve"]["ms_per_step"], "steps": args.steps,
+        "warmup": args.warmup, "tol": 1e-10, "paths": out,
+        "gaussian_elimination_rel_l2": {"inv5": lu5, "inv4": lu4},
+        "workload": "type-5 + type-4 inverses, N=256, u~U(-0.3,0.3) (seed 0), float64 path, tol 1e-10, "
+                    "1 and 1024 right-hand sides (known-truth inputs), plan per step and solve only",
+        "clocks": clocks.summary(t0, t1),
+        "l2": "512 MiB buffer written between timed steps (outside the events)",
+    }
+
+
 def _print_side(args, fn, metric_unit_note=None):
     import torch
     import paper_1604_06236_gb300 as pkg
@@ -802,7 +866,7 @@ def _print_side(args, fn, metric_unit_note=None):
     r = fn(args, dev, clocks)
     clocks.stop()
     line = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 transforms (complex64 data), f64 plan", "data": "synthetic",
+            "dtype": r.pop("dtype", "f32 transforms (complex64 data), f64 plan"), "data": "synthetic",
             "config": {"workload": r.pop("workload"), "l2": r.pop("l2")}}
     line.update(r)
     print(json.dumps(line), flush=True)
@@ -819,6 +883,10 @@ def run_clustered(args):
 
 def run_autograd(args):
     return _print_side(args, measure_autograd)
+
+
+def run_small(args):
+    return _print_side(args, measure_small)
 
 
 def run_error_model(args):
@@ -927,7 +995,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="n65536",
-                    choices=["n65536", "batched", "clustered", "autograd", "error_model"],
+                    choices=["n65536", "small", "batched", "clustered", "autograd", "error_model"],
                     help="n65536: the headline workload (default); batched: uneven-N instances; clustered: "
                          "N=2^20 with near-coincident nodes; autograd: forward+backward at N=262144; "
                          "error_model: error versus the attenuation mu of Eq. 49 (Sec. VI)")
@@ -941,6 +1009,8 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "small":
+        return run_small(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "clustered":

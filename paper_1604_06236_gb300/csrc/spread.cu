@@ -474,7 +474,7 @@ inline size_t spread_tile_smem(int w, int BC) {
 constexpr int kInterpNodes = 128;
 constexpr int kInterpTB = 2 * kInterpNodes;
 constexpr int kInterpWin = 384;   // window points per right-hand side
-constexpr int kInterpRow = kInterpWin + 2;   // (+2 of slack for the pair alignment)
+constexpr int kInterpRow = kInterpWin + 4;   // (+4: pair alignment and the pair read past a node's last tap)
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
@@ -513,7 +513,7 @@ __device__ __forceinline__ void gather_window(float2* ring, int bc, int st, bool
 }
 
 template <int BC>
-__global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n, int w, float two_over_w,
+__global__ void __launch_bounds__(kInterpTB, 4) k_interp_tile(int64_t N, int64_t n, int w, float two_over_w,
                                                            float beta, const int* __restrict__ sperm,
                                                            const int* __restrict__ scell,
                                                            const float* __restrict__ sfrac,
@@ -533,16 +533,24 @@ __global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n,
     const int64_t wa = (int64_t)scell[i0] + 1 - h;            // window start (may be < 0: periodic)
     const int64_t L = (int64_t)scell[ilast] + h - wa + 1;     // window length
     const bool live = i < N;
-    float ker[16];
+    // kernel values by tap, shifted by `par` positions: ker[k] = phi(k - par + 1 - h - frac)
+    // for 0 <= k - par < w, else 0
+    float ker[18];
     int base = 0;
     int c = 0;
+    float f = 0.f;
     if (live) {
         c = scell[i];
-        const float f = sfrac[i];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) ker[m] = (m < w) ? es_kernel<float>((float)(m + 1 - h) - f, two_over_w, beta) : 0.f;
+        f = sfrac[i];
         base = (int)(c + 1 - h - wa);
     }
+    auto kernel_values = [&](int par) {
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const int m = k - par;
+            ker[k] = (live && m >= 0 && m < w) ? es_kernel<float>((float)(m + 1 - h) - f, two_over_w, beta) : 0.f;
+        }
+    };
     const int p = live ? sperm[i] : 0;
     const float2 wv = live ? wt[i] : make_float2(0.f, 0.f);
     const int nchunks = (int)((batch + BC - 1) / BC);
@@ -553,8 +561,13 @@ __global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n,
         const bool pairs = (n & 1) == 0;
         const int s0 = pairs ? (int)(ws & 1) : 0;
         const int64_t wsa = ws - s0;
-        const int npair = (int)((L + s0 + 1) / 2);
+        // (one pair more than the window needs: a node whose taps start at an
+        // odd ring index reads w/2 + 1 pairs, the last one past its taps)
+        const int npair = (int)((L + s0 + 1) / 2) + 1;
         const int Li = (int)L;
+        // with pairs, the kernel values by position in the pairs read from
+        // (s0 + base) / 2 on: shifted by the parity of the first tap's ring index
+        kernel_values(pairs ? ((s0 + base) & 1) : 0);
         gather_window<BC>(ring, 0, 0, pairs, npair, Li, wsa, ws, n, grid, batch);
         for (int bc = 0; bc < nchunks; ++bc) {
             const int st = bc & 1;
@@ -565,17 +578,38 @@ __global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n,
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const float2* win = ring + st * BC * kInterpRow + half * HB * kInterpRow + s0 + base;
 #pragma unroll
             for (int b = 0; b < HB; ++b) acc[b] = make_float2(0.f, 0.f);
+            if (pairs) {
+                // 16-byte reads of whole pairs: nodes about two grid points
+                // apart read consecutive pairs (no bank conflicts); kp holds the
+                // kernel values shifted by the parity of the first tap
+                const float4* win4 = reinterpret_cast<const float4*>(ring + st * BC * kInterpRow +
+                                                                     half * HB * kInterpRow) + (s0 + base) / 2;
 #pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                if (m < w) {
+                for (int q = 0; q < 9; ++q) {
+                    if (q <= w / 2) {
 #pragma unroll
-                    for (int b = 0; b < HB; ++b) {
-                        const float2 v = win[b * kInterpRow + m];
-                        acc[b].x = fmaf(ker[m], v.x, acc[b].x);
-                        acc[b].y = fmaf(ker[m], v.y, acc[b].y);
+                        for (int b = 0; b < HB; ++b) {
+                            const float4 v = win4[b * (kInterpRow / 2) + q];
+                            // taps in order (the same sums as the per-node kernel
+                            // for few right-hand sides; zero weights add exact zeros)
+                            acc[b].x = fmaf(ker[2 * q + 1], v.z, fmaf(ker[2 * q], v.x, acc[b].x));
+                            acc[b].y = fmaf(ker[2 * q + 1], v.w, fmaf(ker[2 * q], v.y, acc[b].y));
+                        }
+                    }
+                }
+            } else {
+                const float2* win = ring + st * BC * kInterpRow + half * HB * kInterpRow + s0 + base;
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    if (m < w) {
+#pragma unroll
+                        for (int b = 0; b < HB; ++b) {
+                            const float2 v = win[b * kInterpRow + m];
+                            acc[b].x = fmaf(ker[m], v.x, acc[b].x);
+                            acc[b].y = fmaf(ker[m], v.y, acc[b].y);
+                        }
                     }
                 }
             }
@@ -592,6 +626,7 @@ __global__ void __launch_bounds__(kInterpTB) k_interp_tile(int64_t N, int64_t n,
     }
     // long window: direct gathers
     if (!live) return;
+    kernel_values(0);
     int64_t g_first = (int64_t)c + 1 - h;
     if (g_first < 0) g_first += n;
     for (int bc = 0; bc < nchunks; ++bc) {
