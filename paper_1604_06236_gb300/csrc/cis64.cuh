@@ -6,9 +6,10 @@
 // complex product joins them: about 2 ulp, against ~1 ulp for sincospi, at
 // less than half its cost.
 //
-// The table is a per-translation-unit __device__ array; cis_table_ensure()
-// fills it on the current device (once per device, from long double host
-// trigonometry) and must run before the first launch that reads it.
+// The tables (this one and exp_t's) are per-translation-unit __device__
+// arrays; cis_table_ensure() fills them on the current device (once per
+// device, from long double host trigonometry and exp2) and must run before
+// the first launch that reads them.
 #pragma once
 #include <atomic>
 #include <cmath>
@@ -20,6 +21,27 @@
 namespace nufft45 {
 
 static __device__ double2 g_cis_table[4096];
+static __device__ double g_exp2_table[64];   // 2^(j/64), j < 64
+
+// e^x for |x| < 700 in float64, by P. T. P. Tang's table-driven method
+// ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15(2), 1989): x = (64 m + j) ln2/64 + r,
+// |r| <= ln2/128, the reduction done with an FMA against ln2/64 split into a
+// float64 head and its (tiny) remainder, so that k ln2/64 enters without
+// rounding; e^x = 2^m 2^(j/64) (1 + p), p = e^r - 1 by its Taylor series to
+// r^6 (truncation below |r|^7/5040 < 3e-20).  About 3 ulp; 12 float64
+// operations against the ~2x more of a general-purpose exponential.
+__device__ __forceinline__ double exp_t(double x) {
+    const double kd = rint(x * 92.33248261689366);                  // 64 / ln2
+    double r = fma(-kd, 0x1.62e42fefa39efp-7, x);                    // ln2/64, head
+    r = fma(-kd, 0x1.abc9e3b39803fp-62, r);                          // ln2/64 - head
+    const double p =
+        r * fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+    const int k = (int)kd;
+    const double t = g_exp2_table[k & 63];
+    const double sc = __longlong_as_double((long long)((k >> 6) + 1023) << 52);   // 2^m
+    return fma(t, p, t) * sc;
+}
 
 __device__ __forceinline__ double2 cis_turns_t(uint64_t T, int sign) {
     const double2 t = g_cis_table[T >> 52];
@@ -51,6 +73,9 @@ __device__ __forceinline__ double2 cis_turns_t(uint64_t T, int sign) {
         h[i] = make_double2((double)cosl(a), (double)sinl(a));
     }
     NUFFT_CUDA_TRY(cudaMemcpyToSymbol(g_cis_table, h.data(), sizeof(double2) * h.size()));
+    std::vector<double> e2(64);
+    for (int j = 0; j < 64; ++j) e2[j] = (double)exp2l((long double)j / 64.0L);
+    NUFFT_CUDA_TRY(cudaMemcpyToSymbol(g_exp2_table, e2.data(), sizeof(double) * e2.size()));
     done[dev].store(true, std::memory_order_release);
     return NUFFT_OK;
 }

@@ -127,10 +127,13 @@ __global__ void k_kernel_samples(const double2* __restrict__ v, int64_t P, const
     if (q >= P) return;
     const uint64_t C = (uint64_t)*sumT + (uint64_t)P * 0x8000000000000000ull;
     const double2 vq = v[q];
-    double s, c;
-    sincospi(vq.y / 3.141592653589793238462643383279502884 + 2.0 * turns_of(C), &s, &c);
-    const double mag = exp(vq.x);
-    const double2 k = make_double2(mag * c, mag * s);
+    // the phase in exact 64-bit turns: v's argument taken mod 1 turn, plus C
+    double tv = vq.y * 0.15915494309189535;   // 1 / (2 pi)
+    tv -= floor(tv);
+    const uint64_t Tv = tv < 1.0 ? __double2ull_rz(tv * 18446744073709551616.0) : 0ull;
+    const double2 e = cis_turns_t(Tv + C, +1);
+    const double mag = exp_t(vq.x);
+    const double2 k = make_double2(mag * e.x, mag * e.y);
     K[q] = k;
     if (Kf) Kf[q] = make_float2((float)k.x, (float)k.y);
     if (Kd) Kd[q] = k;
@@ -345,6 +348,12 @@ __global__ void k_debug_cis(const uint64_t* __restrict__ T, int64_t n, double2* 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = cis_turns_t(T[i], +1);
 }
+__global__ void k_debug_exp_t(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = exp_t(x[i]);
+}
 }  // namespace
 
 }  // namespace nufft45
@@ -363,3 +372,17 @@ extern "C" nufft_status nufft_debug_cis(int64_t n, const uint64_t* T, void* out,
     return NUFFT_OK;
 }
 
+
+// Test hook (not part of the public header): out[i] = e^{x[i]} by the plan
+// kernels' table-driven float64 exponential (|x| < 700); device arrays of n.
+extern "C" nufft_status nufft_debug_exp64(int64_t n, const double* x, double* out, nufft_stream_t stream) {
+    using namespace nufft45;
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(NUFFT_ERR_ARG, "bad exp test arguments");
+    nufft_status st = plan_kernels_init();
+    if (st != NUFFT_OK || n == 0) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_k(k_debug_exp_t, nblk(n), kTB, 0, s, x, n, out);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
