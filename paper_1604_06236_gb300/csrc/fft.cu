@@ -9,6 +9,7 @@
 // buffers), and stores the results in Stockham order, so the final pass leaves
 // the transform in natural order.  Lengths with a larger prime factor use
 // Bluestein's chirp-z convolution on a smooth length m >= 2n - 1.
+#include <atomic>
 #include "internal.h"
 #include "df.cuh"
 #include "fft_p2.cuh"
@@ -492,6 +493,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
     return fn;
 }
 
+// the tile counter of the next TMA-fed pass: one sequence for every
+// instantiation of the pass, so consecutive launches never share a counter
+static int p2t_next_slot() {
+    static std::atomic<unsigned> next{0};
+    return (int)(next.fetch_add(1u, std::memory_order_relaxed) % (unsigned)p2t::kTileSlots);
+}
+
 template <int R1, int R2, bool FUSE = false>
 nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta, int64_t batch, const float2* tw,
                             int dir, cudaStream_t s) {
@@ -521,7 +529,9 @@ nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta,
     NUFFT_CUDA_TRY(cudaGetDevice(&dev));
     NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::min(ta.ntiles, per_sm * std::max(1, sms));
-    launch_k(kern, grid, G::TH, smem, s, tm, out, ta, tw, dir);
+    p2t::TArgs tl = ta;
+    tl.slot = p2t_next_slot();
+    launch_k(kern, grid, G::TH, smem, s, tm, out, tl, tw, dir);
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }

@@ -10,6 +10,21 @@
 // i+1 .. i+S-1 are in flight, and stage completion is tracked by mbarrier
 // transaction counts instead of per-thread loads.
 //
+// Each CTA's first tile is its block index; the later ones are handed out by
+// a per-launch atomic counter (tile = grid size + counter), not by block
+// index: when other work on the GPU (the next plan's kernels on another
+// stream) holds some of the slots the grid was sized for, the CTAs that
+// start late find fewer tiles left instead of running their share as a
+// second wave.
+// Launches take the kTileSlots counters in turn, and each launch sets the
+// counter kTileSlots/2 slots ahead of its own back to zero, ready for its
+// next user; this needs fewer than kTileSlots/2 of these launches in flight
+// at a time, which any stream-ordered use keeps far below.  The first tile's
+// load goes out before any atomic; a CTA takes its next S-1 tiles with one
+// atomic, and each later tile by an atomic issued just before the iteration's
+// twiddle loads and TMA wait, whose latency it shares (the result is parked
+// in shared memory for the refill at the end of the iteration).
+//
 // Inter-pass twiddles use W^{jm k} = W^{jm k2} W^{jm R2 k1} (k = k1 R2 + k2):
 // each thread loads W^{jm k2} and one entry of the per-tile [k1][c] table of
 // W^{jm R2 k1}, so a tile of C R elements needs 2 C R / R1 table loads instead
@@ -32,8 +47,12 @@
 
 namespace nufft45 {
 
+constexpr int p2t_tile_slots = 4096;   // tile counters of the TMA-fed passes (p2t::kTileSlots)
+
 // number of in-kernel waits that gave up (read and cleared by the host)
 __device__ int g_wait_expired;
+// per-launch tile counters of the TMA-fed passes (next tile to hand out)
+__device__ unsigned g_p2t_tiles[p2t_tile_slots];
 
 namespace p2t {
 
@@ -48,12 +67,14 @@ template <int R1, int R2> struct TCfg {
 
 constexpr int kStages = 2;      // ring depth
 constexpr int kMinBlocks = 3;   // resident CTAs per SM the register budget allows
+constexpr int kTileSlots = p2t_tile_slots;          // tile counters, used by launches in turn
 constexpr int kPollLimit = 1 << 22;                 // polls of one wait, at most
 constexpr unsigned long long kWaitNs = 1000000000;  // and at most one second
 
 struct TArgs {
     int n_log, R_log, Ns_log, C_log;
     int ntiles;
+    int slot;             // tile counter of this launch, < kTileSlots
     const float2* fmul;   // FUSE: the pointwise factor between the two transforms (length n)
     // lop 2: x = in[idx] * fac_in[idx]; lop 3 (first pass): the input is zero
     // outside rows k1 < R1/4 and k1 >= 3 R1/4 (a spectrum centred on the
@@ -147,6 +168,8 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     float2* wi = stage + S * TILE;                                 // W_R^e, e < R
     float2* btab = wi + R;                                         // [k1][c]: W^{jm R2 k1}
     uint64_t* bars = reinterpret_cast<uint64_t*>(btab + R1 * C);   // S barriers
+    int* tq = reinterpret_cast<int*>(bars + S);                      // tile in each stage, -1: none
+    unsigned* tnext = reinterpret_cast<unsigned*>(tq + S);           // counter value for the refill
     const int tid = threadIdx.x;
     const int nR_log = a.n_log - a.R_log;
     const uint32_t nR = 1u << nR_log;
@@ -154,9 +177,6 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     const int tw_shift = a.n_log - a.Ns_log - a.R_log;
     const int inner_shift = a.n_log - a.R_log;
     const int ntiles = a.ntiles;
-    const int step = gridDim.x;
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
 
     for (int e = tid; e < R; e += TH) {
         float2 w = __ldg(&tw[(uint32_t)e << inner_shift]);
@@ -166,17 +186,33 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int s = 0; s < S; ++s) {
-            const int t = tile + s * step;
-            if (t < ntiles) issue<R1, R2>(&tm, stage + s * TILE, &bars[s], t, nR_log, a.lop == 3);
+        // (the grid is at most ntiles CTAs)
+        tq[0] = (int)blockIdx.x;
+        issue<R1, R2>(&tm, stage, &bars[0], (int)blockIdx.x, nR_log, a.lop == 3);
+        if (blockIdx.x == 0) g_p2t_tiles[(a.slot + kTileSlots / 2) % kTileSlots] = 0u;
+        const unsigned first = gridDim.x + atomicAdd(&g_p2t_tiles[a.slot], (unsigned)(S - 1));
+        for (int s = 1; s < S; ++s) {
+            const unsigned u = first + (unsigned)(s - 1);
+            const int t = u < (unsigned)ntiles ? (int)u : -1;
+            tq[s] = t;
+            if (t >= 0) issue<R1, R2>(&tm, stage + s * TILE, &bars[s], t, nR_log, a.lop == 3);
         }
     }
     __syncthreads();
 
     const int ca = tid % C, k2 = tid / C;   // step-A thread: column ca, inputs k = k1 R2 + k2
     int it = 0;
-    for (; tile < ntiles; tile += step, ++it) {
+    bool expired = false;
+    // stages are consumed in the order their tiles were taken, so the first
+    // empty one ends the walk (tq[s] was written before a barrier every
+    // thread has passed since)
+    for (;; ++it) {
         const int s = it % S;
+        const int tile = tq[s];
+        if (tile < 0) break;
+        // the tile this stage loads next (thread 0; parked after the wait below)
+        unsigned nxt = 0u;
+        if (tid == 0) nxt = atomicAdd(&g_p2t_tiles[a.slot], 1u);
         float2* st = stage + s * TILE;
         const int g0 = tile * C;
         const uint32_t b = (uint32_t)g0 >> nR_log, j0 = (uint32_t)g0 & (nR - 1);
@@ -194,8 +230,10 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
             }
         }
         const bool ok = mbar_wait(&bars[s], (unsigned)((it / S) & 1));
+        if (tid == 0) *tnext = gridDim.x + nxt;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicAdd(&g_wait_expired, 1);
+            expired = true;
             break;
         }
         // step A: DFT over k1 of column ca, then the inner twiddle W_R^{m1 k2}
@@ -326,13 +364,18 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            const int t = tile + S * step;
-            if (t < ntiles) issue<R1, R2>(&tm, st, &bars[s], t, nR_log, a.lop == 3);
+            const unsigned u = *tnext;
+            const int t = u < (unsigned)ntiles ? (int)u : -1;
+            tq[s] = t;
+            if (t >= 0) issue<R1, R2>(&tm, st, &bars[s], t, nR_log, a.lop == 3);
         }
     }
     // after an expired wait, let the copies still in flight land before the CTA ends
-    if (tile < ntiles && tid == 0) {
-        for (int k = 0; k < S && tile < ntiles; ++k, tile += step, ++it) mbar_wait(&bars[it % S], (unsigned)((it / S) & 1));
+    if (expired && tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            const int ss = (it + k) % S;
+            if (tq[ss] >= 0) mbar_wait(&bars[ss], (unsigned)(((it + k) / S) & 1));
+        }
     }
 }
 
@@ -340,7 +383,7 @@ template <int R1, int R2>
 constexpr size_t smem_bytes() {
     using G = TCfg<R1, R2>;
     return (size_t)kStages * G::TILE * sizeof(float2) + (size_t)G::R * sizeof(float2) +
-           (size_t)R1 * G::C * sizeof(float2) + kStages * sizeof(uint64_t);
+           (size_t)R1 * G::C * sizeof(float2) + kStages * (sizeof(uint64_t) + sizeof(int)) + sizeof(unsigned);
 }
 
 }  // namespace p2t
