@@ -193,7 +193,9 @@ def oracle_sample(seconds_hint=15.0):
     import oracle
     import synth
     oracle.build()
-    n_s = 2048
+    # a bounded sample per step: N = 2048 (~0.2 s a step on 16 cores), or
+    # N = 1024 (~0.03 s) for long runs, so that the run ends within minutes
+    n_s = 2048 if args.steps <= 60 else 1024
     x = synth.jittered_nodes(n_s, 0.45, seed=123)
     s = synth.cn01(n_s, seed=124)
     t0 = time.perf_counter()
@@ -274,7 +276,9 @@ def run_reference(args):
     import oracle
     import synth
     oracle.build()
-    n_s = 2048
+    # a bounded sample per step: N = 2048 (~0.2 s a step on 16 cores), or
+    # N = 1024 (~0.03 s) for long runs, so that the run ends within minutes
+    n_s = 2048 if args.steps <= 60 else 1024
     x = synth.jittered_nodes(n_s, 0.45, seed=123)
     s = synth.cn01(n_s, seed=124)
     for _ in range(args.warmup):
@@ -1060,7 +1064,7 @@ def run_error_model(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nufft45", choices=["nufft45", "reference"])
     ap.add_argument("--N", type=int, default=65536)
