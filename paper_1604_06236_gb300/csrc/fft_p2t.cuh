@@ -11,15 +11,17 @@
 // transaction counts instead of per-thread loads.
 //
 // Each CTA's first tile is its block index; the later ones are handed out by
-// a per-launch atomic counter (tile = grid size + counter), not by block
-// index: when other work on the GPU (the next plan's kernels on another
-// stream) holds some of the slots the grid was sized for, the CTAs that
-// start late find fewer tiles left instead of running their share as a
-// second wave.
-// Launches take the kTileSlots counters in turn, and each launch sets the
-// counter kTileSlots/2 slots ahead of its own back to zero, ready for its
-// next user; this needs fewer than kTileSlots/2 of these launches in flight
-// at a time, which any stream-ordered use keeps far below.  The first tile's
+// per-launch atomic counters, not by block index: when other work on the GPU
+// (the next plan's kernels on another stream) holds some of the slots the
+// grid was sized for, the CTAs that start late find fewer tiles left instead
+// of running their share as a second wave.  The tiles are split into eight
+// shards by tile index mod 8, each with its own counter, served by the CTAs
+// of the same block index mod 8: one counter for all CTAs made its atomics
+// queue (0.5 us more per pass), and more shards balance less.
+// Launches take the kTileSlots counter sets in turn, and each launch sets the
+// set kTileSlots/2 slots ahead of its own back to zero, ready for its next
+// user; this needs fewer than kTileSlots/2 of these launches in flight at a
+// time, which any stream-ordered use keeps far below.  The first tile's
 // load goes out before any atomic; a CTA takes its next S-1 tiles with one
 // atomic, and each later tile by an atomic issued just before the iteration's
 // twiddle loads and TMA wait, whose latency it shares (the result is parked
@@ -47,12 +49,12 @@
 
 namespace nufft45 {
 
-constexpr int p2t_tile_slots = 4096;   // tile counters of the TMA-fed passes (p2t::kTileSlots)
+constexpr int p2t_tile_slots = 4096;   // tile counter sets of the TMA-fed passes (p2t::kTileSlots)
 
 // number of in-kernel waits that gave up (read and cleared by the host)
 __device__ int g_wait_expired;
 // per-launch tile counters of the TMA-fed passes (next tile to hand out)
-__device__ unsigned g_p2t_tiles[p2t_tile_slots];
+__device__ unsigned g_p2t_tiles[p2t_tile_slots * 8];   // [slot][shard]
 
 namespace p2t {
 
@@ -177,6 +179,11 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
     const int tw_shift = a.n_log - a.Ns_log - a.R_log;
     const int inner_shift = a.n_log - a.R_log;
     const int ntiles = a.ntiles;
+    // tiles t = h + nsh u of shard h = blockIdx mod nsh: u < shard_base are
+    // the shard's CTAs' first tiles, the later ones come from its counter
+    const unsigned nsh = gridDim.x < 8u ? gridDim.x : 8u;
+    const unsigned shard = blockIdx.x % nsh;
+    const unsigned shard_base = (gridDim.x - shard + nsh - 1u) / nsh;
 
     for (int e = tid; e < R; e += TH) {
         float2 w = __ldg(&tw[(uint32_t)e << inner_shift]);
@@ -189,10 +196,10 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         // (the grid is at most ntiles CTAs)
         tq[0] = (int)blockIdx.x;
         issue<R1, R2>(&tm, stage, &bars[0], (int)blockIdx.x, nR_log, a.lop == 3);
-        if (blockIdx.x == 0) g_p2t_tiles[(a.slot + kTileSlots / 2) % kTileSlots] = 0u;
-        const unsigned first = gridDim.x + atomicAdd(&g_p2t_tiles[a.slot], (unsigned)(S - 1));
+        if (blockIdx.x < 8) g_p2t_tiles[((a.slot + kTileSlots / 2) % kTileSlots) * 8 + blockIdx.x] = 0u;
+        const unsigned first = shard_base + atomicAdd(&g_p2t_tiles[a.slot * 8 + shard], (unsigned)(S - 1));
         for (int s = 1; s < S; ++s) {
-            const unsigned u = first + (unsigned)(s - 1);
+            const unsigned u = shard + nsh * (first + (unsigned)(s - 1));
             const int t = u < (unsigned)ntiles ? (int)u : -1;
             tq[s] = t;
             if (t >= 0) issue<R1, R2>(&tm, stage + s * TILE, &bars[s], t, nR_log, a.lop == 3);
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         if (tile < 0) break;
         // the tile this stage loads next (thread 0; parked after the wait below)
         unsigned nxt = 0u;
-        if (tid == 0) nxt = atomicAdd(&g_p2t_tiles[a.slot], 1u);
+        if (tid == 0) nxt = atomicAdd(&g_p2t_tiles[a.slot * 8 + shard], 1u);
         float2* st = stage + s * TILE;
         const int g0 = tile * C;
         const uint32_t b = (uint32_t)g0 >> nR_log, j0 = (uint32_t)g0 & (nR - 1);
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
             }
         }
         const bool ok = mbar_wait(&bars[s], (unsigned)((it / S) & 1));
-        if (tid == 0) *tnext = gridDim.x + nxt;
+        if (tid == 0) *tnext = shard + nsh * (shard_base + nxt);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicAdd(&g_wait_expired, 1);
             expired = true;
