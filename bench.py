@@ -11,7 +11,10 @@ Workload (one "step" = one pass of the whole hot path on one batch):
 The steps run as a pipeline: the plan of step i+1 is built on a
 high-priority stream while the transforms of step i run (a plan depends only
 on its nodes, not on transforms in flight; its kernels are latency-bound and
-take the SM slots that the transforms' passes leave between launches).  The
+take the SM slots that the transforms' passes leave between launches), and
+the type-5 and type-4 inverses of a step run side by side on two streams
+(both only read the plan; the FFT passes take their tiles from per-launch
+counters, so concurrent passes share the SMs without second waves).  The
 timed value is one pair of CUDA events around all K steps (inputs already in
 HBM, every step's plan and transforms inside the region), bracketed by a
 barrier and synchronisation.  Four sets of input and output vectors are
@@ -89,6 +92,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    PERIOD_MS = 25
 
     def __init__(self, index):
         self.index = index
@@ -100,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
@@ -141,7 +145,8 @@ class ClockSampler:
         if len(inside) < 3:
             mid = 0.5 * (t0 + t1)
             inside = sorted(self.samples, key=lambda s: abs(s[0] - mid))[:5]
-            window = "timed region shorter than the 100 ms sampling period: %d samples nearest to it" % len(inside)
+            window = "timed region shorter than three %d ms sampling periods: %d samples nearest to it" % (
+                self.PERIOD_MS, len(inside))
         if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         reasons = set()
@@ -350,14 +355,17 @@ def run_gpu(args):
         Ak = torch.from_numpy(synth.cn01((B, N), seed=8 + rank + 100 * k)).to(torch.complex64).to(dev)
         sets.append((fk, Ak, torch.empty_like(fk), torch.empty_like(Ak)))
     plan_stream = torch.cuda.Stream(priority=-1)   # the highest priority torch offers
+    inv4_stream = torch.cuda.Stream()
 
     def run_pipelined(first, count, nodes=xs, data=sets):
         """Steps first .. first+count-1: each step's plan is built on
-        plan_stream one step ahead of its transforms (on `stream`); a plan is
-        released on plan_stream once its transforms are done.  Step i plans
-        nodes[i mod len] and transforms data[i mod len]."""
-        ss, ps = stream, plan_stream
+        plan_stream one step ahead of its transforms; the type-5 inverse runs
+        on `stream`, the type-4 inverse beside it on inv4_stream (both only
+        read the plan); a plan is released on plan_stream once both are done.
+        Step i plans nodes[i mod len] and transforms data[i mod len]."""
+        ss, ps, s4 = stream, plan_stream, inv4_stream
         ps.wait_stream(ss)
+        s4.wait_stream(ss)
 
         def make(i):
             with torch.cuda.stream(ps):
@@ -372,9 +380,13 @@ def run_gpu(args):
             if k + 1 < count:
                 nxt = make(first + k + 1)
             ss.wait_event(ready)
+            s4.wait_event(ready)
             fi, Ai, Si, ai = data[(first + k) % len(data)]
             p.inv5(fi, out=Si, stream=ss)
-            p.inv4(Ai, out=ai, stream=ss)
+            p.inv4(Ai, out=ai, stream=s4)
+            d4 = torch.cuda.Event()
+            d4.record(s4)
+            ss.wait_event(d4)
             done = torch.cuda.Event()
             done.record(ss)
             live.append((p, done))
@@ -388,6 +400,7 @@ def run_gpu(args):
             q.check()
             q.close()
         ss.wait_stream(ps)
+        ss.wait_stream(s4)
 
     def timed(fn, steps, warm):
         for i in range(warm):
@@ -486,7 +499,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "N": N, "batch": B, "transforms_per_step": 2 * B,
                    "tol": 1e-5, "plan_per_step": True,
                    "schedule": "pipelined: the plan of step i+1 on a high-priority stream while step i's "
-                               "transforms run; one pair of CUDA events around all K steps",
+                               "transforms run, its type-5 and type-4 inverses on two streams side by side; "
+                               "one pair of CUDA events around all K steps",
                    "l2": "inputs larger than L2: %d rotating sets of input and output vectors (%d MB each), "
                          "a step reads data last touched %d steps earlier" % (NSETS, 4 * B * N * 8 // 10**6, NSETS),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},

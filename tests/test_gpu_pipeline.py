@@ -1,8 +1,9 @@
 """Plans built on a second, higher-priority stream while the previous plan's
-transforms run (the step schedule bench.py times) give the same results, bit
-for bit, as the same calls made one after another on one stream; and the
-results of that schedule at the benchmark's size stay within the FP32
-tolerance of the oracle's known truth on a sampled right-hand side."""
+transforms run, with a step's type-5 and type-4 inverses on two further
+streams side by side (the step schedule bench.py times), give the same
+results, bit for bit, as the same calls made one after another on one
+stream; and the results of that schedule stay within the FP32 tolerance of
+the oracle's known truth on a sampled right-hand side."""
 import numpy as np
 import pytest
 
@@ -14,11 +15,13 @@ pytestmark = pytest.mark.gpu
 import paper_1604_06236_gb300 as pkg  # noqa: E402
 
 
-def _pipelined(xs, fs, As, outs):
+def _pipelined(xs, fs, As, outs, two=False):
     ss = torch.cuda.Stream()
     ps = torch.cuda.Stream(priority=-1)
+    s4 = torch.cuda.Stream() if two else ss
     ss.wait_stream(torch.cuda.current_stream())
     ps.wait_stream(ss)
+    s4.wait_stream(ss)
 
     def make(i):
         with torch.cuda.stream(ps):
@@ -34,8 +37,13 @@ def _pipelined(xs, fs, As, outs):
         if i + 1 < len(xs):
             nxt = make(i + 1)
         ss.wait_event(ready)
+        s4.wait_event(ready)
         p.inv5(fs[i], out=outs[i][0], stream=ss)
-        p.inv4(As[i], out=outs[i][1], stream=ss)
+        p.inv4(As[i], out=outs[i][1], stream=s4)
+        if two:
+            d4 = torch.cuda.Event()
+            d4.record(s4)
+            ss.wait_event(d4)
         done = torch.cuda.Event()
         done.record(ss)
         live.append((p, done))
@@ -50,11 +58,13 @@ def _pipelined(xs, fs, As, outs):
         q.close()
     torch.cuda.current_stream().wait_stream(ss)
     torch.cuda.current_stream().wait_stream(ps)
+    torch.cuda.current_stream().wait_stream(s4)
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("N,B,K", [(8192, 8, 5), (65536, 16, 4)])
-def test_pipelined_plans_match_sequential(N, B, K):
+@pytest.mark.parametrize("two", [False, True], ids=["one_solve_stream", "inv5_inv4_side_by_side"])
+@pytest.mark.parametrize("N,B,K", [(8192, 8, 5), (65536, 16, 4), (65536, 64, 3)])
+def test_pipelined_plans_match_sequential(N, B, K, two):
     dev = torch.device("cuda", 0)
     xs = [torch.from_numpy(synth.jittered_nodes(N, 0.45, seed=500 + i)).to(dev) for i in range(K)]
     fs = [torch.from_numpy(synth.cn01((B, N), seed=600 + i)).to(torch.complex64).to(dev) for i in range(K)]
@@ -66,7 +76,7 @@ def test_pipelined_plans_match_sequential(N, B, K):
         p.close()
     torch.cuda.synchronize()
     outs = [(torch.empty_like(fs[i]), torch.empty_like(As[i])) for i in range(K)]
-    _pipelined(xs, fs, As, outs)
+    _pipelined(xs, fs, As, outs, two)
     for i in range(K):
         assert torch.equal(outs[i][0], ref[i][0]), i
         assert torch.equal(outs[i][1], ref[i][1]), i
@@ -93,7 +103,7 @@ def test_pipelined_known_truth():
         fs.append(torch.from_numpy(f).to(torch.complex64).to(dev))
         As.append(torch.from_numpy(A).to(torch.complex64).to(dev))
     outs = [(torch.empty_like(fs[i]), torch.empty_like(As[i])) for i in range(K)]
-    _pipelined(xs, fs, As, outs)
+    _pipelined(xs, fs, As, outs, two=True)
     for i in range(K):
         s = outs[i][0][0].cpu().numpy().astype(np.complex128)
         a = outs[i][1][0].cpu().numpy().astype(np.complex128)
