@@ -102,14 +102,18 @@ typedef enum {
  * nodes whose turns t differ by less than 2^-44 modulo 1 make the systems of
  * Eqs. 47/48 numerically singular and return NUFFT_ERR_DUP_NODES (no plan).
  * A plan depends on its nodes alone, not on transforms of other plans in
- * flight.  Its kernels are short and latency-bound, so a sequence of
- * (plan, transforms) steps runs fastest pipelined: plan step i+1 with
- * NUFFT_DEFER_CHECK on a stream of higher priority while the transforms of
- * step i run on another stream, which waits for an event recorded after the
- * plan call before it transforms with that plan (on GB300, N = 65536 with 64
- * right-hand sides of each kind: 0.44 against 0.51 ms per step, results bit
- * for bit the same).  Destroy a plan only once its creation stream has waited
- * for its transforms (see nufft_destroy).
+ * flight, and transforms only read their plan: calls with one plan may run
+ * on several streams at once.  A plan's kernels are short and latency-bound,
+ * so a sequence of (plan, transforms) steps runs fastest pipelined: plan step
+ * i+1 with NUFFT_DEFER_CHECK on a stream of higher priority while the
+ * transforms of step i run on other streams (each waiting for an event
+ * recorded after the plan call before it transforms with that plan; the FFT
+ * passes hand out their tiles by counters, so concurrent transforms share
+ * the SMs).  On GB300, N = 65536 with 64 right-hand sides of each kind: 0.51
+ * ms per step one call after another, 0.40 with the next plan pipelined, 0.35
+ * with the type-5 and type-4 inverses also on two streams; results bit for
+ * bit the same.  Destroy a plan only once its creation stream has waited for
+ * its transforms (see nufft_destroy).
  */
 nufft_status nufft_plan(int64_t N, const double* x, double tol, int prec, nufft_stream_t stream,
                         nufft_plan_t* plan);
