@@ -198,9 +198,7 @@ def oracle_sample(seconds_hint=15.0):
     import oracle
     import synth
     oracle.build()
-    # a bounded sample per step: N = 2048 (~0.2 s a step on 16 cores), or
-    # N = 1024 (~0.03 s) for long runs, so that the run ends within minutes
-    n_s = 2048 if args.steps <= 60 else 1024
+    n_s = 2048
     x = synth.jittered_nodes(n_s, 0.45, seed=123)
     s = synth.cn01(n_s, seed=124)
     t0 = time.perf_counter()
