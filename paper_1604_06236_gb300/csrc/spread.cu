@@ -313,11 +313,14 @@ template <int K> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
+constexpr int kTileList = 8;   // a grid point's nodes whose kernel values are listed once per tile
+
 struct TileSmem {
     float* ph;      // [kTB][w]
     float2* ring;   // [2][BC][kTB]
     float2* wt;     // [kTB]
     int* cell;      // [kTB]
+    float* kl;      // [kTileList][kTB]: the grid point's kernel values, node by node
 };
 
 // node e = threadIdx.x of the piece [c0, c0 + cnt): cell, slot weight and the
@@ -380,6 +383,24 @@ __device__ __forceinline__ void tile_accumulate(const TileSmem& sm, float2* acc,
     }
 }
 
+// as tile_accumulate for a grid point whose nl <= kTileList nodes (window
+// columns e0 .. e0 + nl - 1) have their kernel values listed in sm.kl: the
+// same sums in the same order, without the per-chunk cell and tap lookups
+template <int BC>
+__device__ __forceinline__ void tile_accumulate_list(const TileSmem& sm, float2* acc, int st, int e0, int nl) {
+    const float2* sv = sm.ring + st * BC * kTB + e0;
+    const float* kl = sm.kl + threadIdx.x;
+    for (int j = 0; j < nl; ++j) {
+        const float k = kl[j * kTB];
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+            const float2 v = sv[b * kTB + j];
+            acc[b].x = fmaf(k, v.x, acc[b].x);
+            acc[b].y = fmaf(k, v.y, acc[b].y);
+        }
+    }
+}
+
 template <int BC>
 __global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two_over_w, float beta,
                                                      const int* __restrict__ cstart, const int* __restrict__ eperm,
@@ -395,6 +416,7 @@ __global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two
     sm.wt = sm.ring + 2 * BC * kTB;
     sm.ph = reinterpret_cast<float*>(sm.wt + kTB);
     sm.cell = reinterpret_cast<int*>(sm.ph + kTB * w);
+    sm.kl = reinterpret_cast<float*>(sm.cell + kTB);
     const int64_t g0 = (int64_t)blockIdx.x * kTB;
     const int64_t g = g0 + threadIdx.x;
     const int64_t glast = min(g0 + (int64_t)kTB, n) - 1;
@@ -408,6 +430,7 @@ __global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two
     if (cnt_all <= kTB) {
         const int p = tile_tabulate(sm, t0, cnt_all, w, two_over_w, beta, eperm, ecell, efrac, wt);
         tile_gather<BC>(sm, 0, 0, p, src, src_bs, batch);
+        int nl = -1;   // this grid point's listed nodes (-1: too many, looked up per chunk)
         for (int bc = 0; bc < nchunks; ++bc) {
             const int st = bc & 1;
             if (bc + 1 < nchunks) {
@@ -418,9 +441,20 @@ __global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two
             }
             tile_weight<BC>(sm, st, p);   // the thread's own copies: no barrier needed before
             __syncthreads();
+            if (bc == 0 && hi - lo <= kTileList) {
+                // the kernel values of this grid point's nodes, once for all chunks
+                // (written and read by this thread only)
+                const int h = w / 2;
+                for (int j = 0; j < hi - lo; ++j) {
+                    const int e = lo - t0 + j;
+                    sm.kl[j * kTB + threadIdx.x] = sm.ph[e * w + (int)(g - sm.cell[e]) - 1 + h];
+                }
+                nl = hi - lo;
+            }
 #pragma unroll
             for (int b = 0; b < BC; ++b) acc[b] = make_float2(0.f, 0.f);
-            tile_accumulate<BC>(sm, acc, st, t0, lo, hi, g, w);
+            if (nl >= 0) tile_accumulate_list<BC>(sm, acc, st, lo - t0, nl);
+            else tile_accumulate<BC>(sm, acc, st, t0, lo, hi, g, w);
             if (g < n) {
                 const int nb = (int)min((int64_t)BC, batch - (int64_t)bc * BC);
                 float2* o = out + (int64_t)bc * BC * n;
@@ -458,7 +492,7 @@ __global__ void __launch_bounds__(kTB) k_spread_tile(int64_t n, int w, float two
 
 inline size_t spread_tile_smem(int w, int BC) {
     return 2 * (size_t)BC * kTB * sizeof(float2) + (size_t)kTB * sizeof(float2) + (size_t)kTB * w * sizeof(float) +
-           (size_t)kTB * sizeof(int);
+           (size_t)kTB * sizeof(int) + (size_t)kTileList * kTB * sizeof(float);
 }
 
 // ---- float32 interpolation for many right-hand sides (tiled, pipelined) ---
