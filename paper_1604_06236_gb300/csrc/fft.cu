@@ -493,11 +493,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
     return fn;
 }
 
-// the tile counter of the next TMA-fed pass: one sequence for every
-// instantiation of the pass, so consecutive launches never share a counter
-static int p2t_next_slot() {
-    static std::atomic<unsigned> next{0};
-    return (int)(next.fetch_add(1u, std::memory_order_relaxed) % (unsigned)p2t::kTileSlots);
+// the tile counter set of the next TMA-fed pass on device `dev`: one sequence
+// per device (the counters live in each device's memory, and a launch zeroes
+// the set it will reuse on its own device) shared by every instantiation of
+// the pass, so consecutive launches never share a set
+static int p2t_next_slot(int dev) {
+    static std::atomic<unsigned> next[128];
+    return (int)(next[(unsigned)dev & 127u].fetch_add(1u, std::memory_order_relaxed) % (unsigned)p2t::kTileSlots);
 }
 
 template <int R1, int R2, bool FUSE = false>
@@ -530,7 +532,7 @@ nufft_status launch_p2t_one(const float2* in, float2* out, const p2t::TArgs& ta,
     NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::min(ta.ntiles, per_sm * std::max(1, sms));
     p2t::TArgs tl = ta;
-    tl.slot = p2t_next_slot();
+    tl.slot = p2t_next_slot(dev);
     launch_k(kern, grid, G::TH, smem, s, tm, out, tl, tw, dir);
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
