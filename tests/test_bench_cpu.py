@@ -26,3 +26,45 @@ def test_cpu_baseline_sampler():
     import bench
     r = bench.oracle_sample(0.2)
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1 and "N=2048" in r["sample"]
+
+
+def _sampler(samples):
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.proc = object()   # stands for a running nvidia-smi; summary() only reads the samples
+    c.samples = samples
+    return c
+
+
+def test_clock_record_inside_the_timed_region():
+    s = [(0.05 * i, 2070.0 - (5.0 if i == 7 else 0.0), 2070.0, {"sw_power_cap"} if i == 8 else set())
+         for i in range(40)]
+    r = _sampler(s).summary(0.3, 0.5)            # samples 6 .. 10 inside
+    assert r["window"] == "timed region" and r["samples"] == 5
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_record_short_region_takes_the_nearest_samples():
+    s = [(0.1 * i, 1980.0 + i, 2070.0, {"hw_slowdown"} if i == 20 else set()) for i in range(40)]
+    r = _sampler(s).summary(1.001, 1.002)        # no sample inside
+    assert r["samples"] == 5 and "nearest" in r["window"]
+    assert r["reasons"] == []                    # sample 20 (t = 2.0) is not among the 5 nearest to 1.0015
+    # ... unless it is: a region at 2.0 picks it up
+    r = _sampler(s).summary(1.999, 2.001)
+    assert r["reasons"] == ["hw_slowdown"] and r["sm_mhz"] == 2000.0
+
+
+def test_clock_record_without_nvidia_smi():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.ClockSampler(0).summary(0.0, 1.0)
+    assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_job_rate_and_peaks():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.job_rate(128, 4, 0.5) == 1024.0
+    peak, src = bench.measured_peaks()
+    assert peak > 1000.0 and src in ("measured", "fallback")
