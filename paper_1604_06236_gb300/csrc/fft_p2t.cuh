@@ -18,10 +18,10 @@
 // shards by tile index mod 8, each with its own counter, served by the CTAs
 // of the same block index mod 8: one counter for all CTAs made its atomics
 // queue (0.5 us more per pass), and more shards balance less.
-// Launches take the kTileSlots counter sets in turn, and each launch sets the
-// set kTileSlots/2 slots ahead of its own back to zero, ready for its next
-// user; this needs fewer than kTileSlots/2 of these launches in flight at a
-// time, which any stream-ordered use keeps far below.  The first tile's
+// Launches take the kTileSlots counter sets in turn (one sequence per
+// device), and the last CTA of a launch to finish sets its set back to zero,
+// so a launch replayed from a CUDA graph finds it clean; launches kTileSlots
+// apart never run at the same time in any stream-ordered use.  The first tile's
 // load goes out before any atomic; a CTA takes its next S-1 tiles with one
 // atomic, and each later tile by an atomic issued just before the iteration's
 // twiddle loads and TMA wait, whose latency it shares (the result is parked
@@ -55,6 +55,7 @@ constexpr int p2t_tile_slots = 4096;   // tile counter sets of the TMA-fed passe
 __device__ int g_wait_expired;
 // per-launch tile counters of the TMA-fed passes (next tile to hand out)
 __device__ unsigned g_p2t_tiles[p2t_tile_slots * 8];   // [slot][shard]
+__device__ unsigned g_p2t_done[p2t_tile_slots];        // CTAs of the slot's launch that have finished
 
 namespace p2t {
 
@@ -196,7 +197,6 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
         // (the grid is at most ntiles CTAs)
         tq[0] = (int)blockIdx.x;
         issue<R1, R2>(&tm, stage, &bars[0], (int)blockIdx.x, nR_log, a.lop == 3);
-        if (blockIdx.x < 8) g_p2t_tiles[((a.slot + kTileSlots / 2) % kTileSlots) * 8 + blockIdx.x] = 0u;
         const unsigned first = shard_base + atomicAdd(&g_p2t_tiles[a.slot * 8 + shard], (unsigned)(S - 1));
         for (int s = 1; s < S; ++s) {
             const unsigned u = shard + nsh * (first + (unsigned)(s - 1));
@@ -377,11 +377,21 @@ __global__ void __launch_bounds__(TCfg<R1, R2>::TH, kMinBlocks)
             if (t >= 0) issue<R1, R2>(&tm, st, &bars[s], t, nR_log, a.lop == 3);
         }
     }
-    // after an expired wait, let the copies still in flight land before the CTA ends
-    if (expired && tid == 0) {
-        for (int k = 0; k < S; ++k) {
-            const int ss = (it + k) % S;
-            if (tq[ss] >= 0) mbar_wait(&bars[ss], (unsigned)(((it + k) / S) & 1));
+    if (tid == 0) {
+        // after an expired wait, let the copies still in flight land before the CTA ends
+        if (expired) {
+            for (int k = 0; k < S; ++k) {
+                const int ss = (it + k) % S;
+                if (tq[ss] >= 0) mbar_wait(&bars[ss], (unsigned)(((it + k) / S) & 1));
+            }
+        }
+        // the last CTA to finish leaves the launch's counters at zero (every
+        // CTA has taken its last tile before it counts itself done)
+        __threadfence();
+        if (atomicAdd(&g_p2t_done[a.slot], 1u) == gridDim.x - 1) {
+            for (unsigned h = 0; h < 8u; ++h) g_p2t_tiles[a.slot * 8 + h] = 0u;
+            g_p2t_done[a.slot] = 0u;
+            __threadfence();
         }
     }
 }
