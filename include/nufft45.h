@@ -162,6 +162,10 @@ nufft_status nufft_plan_tune(int64_t N, const double* x, double tol, int prec, i
  *   K_q (Eq. 30), length-N DFT and scaling by e^{2 pi m a} / N (Eq. 31).
  * f      batch x N samples at the plan's nodes (node order as given to nufft_plan).
  * c      batch x N coefficients S_0 .. S_{N-1}.
+ * With device buffers, nufft_inv5 and nufft_inv4 can be captured in a CUDA
+ * graph once a first call outside the capture has done the per-process
+ * set-up; replays on new data in the same buffers give the results of
+ * direct calls (the scratch then comes from the graph's own allocations).
  */
 nufft_status nufft_inv5(nufft_plan_t plan, const void* f, void* c, int64_t batch, nufft_stream_t stream);
 
